@@ -1,0 +1,311 @@
+"""Benchmark: 256^3 registration time to solution on one GB300.
+
+A step is one complete inexact Gauss-Newton-Krylov registration (every step
+of the path: semi-Lagrangian points, transports, spectral operators,
+gradient, Hessian matvecs, preconditioner, PCG, Armijo) of the synthetic
+256^3 brain-like phantom pair (nt = 8, H2, beta = 1e-3, FP32 interpolation
+and FFTs, FP64 reductions), from v = 0 to ||g|| <= 1e-2 ||g_0||.  Inputs are
+resident in HBM when the timed region starts; the working set (several GB)
+is far larger than the 129 MB L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line.  With --impl reference the FP64 CPU oracle is timed
+instead (see cpu_reference()).
+"""
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("256^3 time-to-solution (s), Hessian matvecs/s; interp+spectral GB/s vs HBM peak")
+UNIT = 's'
+SHAPE = (256, 256, 256)
+NT = 8
+BETA = 1e-3
+KIND = 'H2'
+SEED = 3000
+PHASE_NAMES = ('departure', 'state', 'adjoint', 'incstate', 'incadj', 'interp', 'fft',
+               'spectral', 'blas', 'other')
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, 'MEASURED_PEAKS.json')) as f:
+            p = json.load(f)
+        return float(p['hbm_gbs']), 'measured'
+    except Exception:
+        return 6800.0, 'fallback'
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, reasons) during the timed region."""
+
+    QUERY = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+             'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+             'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ['nvidia-smi', '-i', str(self.index), '--query-gpu=' + self.QUERY,
+                 '--format=csv,noheader,nounits', '-lms', '200'],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(',')])
+
+    def stop(self):
+        if self.proc is None:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['nvidia-smi unavailable']}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace('.', '').isdigit()]
+        smax = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace('.', '').isdigit()]
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9
+                          for i in range(4) if r[5 + i].lower().startswith('active')})
+        return {'sm_mhz': statistics.median(sm) if sm else None,
+                'sm_max_mhz': max(smax) if smax else None, 'reasons': reasons,
+                'samples': len(sm)}
+
+
+def make_inputs(shape=SHAPE, seed=SEED):
+    from paper_1608_03630_gb300 import synth
+    rho_T, rho_R, _ = synth.phantom_problem(shape, seed)
+    return rho_T.astype(np.float32), rho_R.astype(np.float32)
+
+
+def dist_env():
+    world = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return world, rank, local
+
+
+def cpu_oracle_sample(precision_note, counts):
+    """Oracle timing on the host cores: one gradient, one Hessian matvec and
+    one objective at 64^3 (nt = 8, same phantom recipe), scaled to 256^3 by
+    grid points (x64) and combined with the operation counts of the GPU solve."""
+    from oracle import problem as opr
+    from paper_1608_03630_gb300 import synth
+    shape = (64, 64, 64)
+    rho_T, rho_R, _ = synth.phantom_problem(shape, SEED)
+    P = opr.Problem(rho_T, rho_R, NT, BETA, KIND, False, presmooth=True)
+    v = np.zeros((3,) + shape)
+    w = synth.bandlimited(shape, 6, 1001)
+    t0 = time.perf_counter(); P.gradient(v); tg = time.perf_counter() - t0
+    t0 = time.perf_counter(); P.hessian_matvec(w); tm = time.perf_counter() - t0
+    t0 = time.perf_counter(); P.objective(0.1 * w); to = time.perf_counter() - t0
+    scale = (SHAPE[0] * SHAPE[1] * SHAPE[2]) / float(64 ** 3)
+    est = scale * (counts['gradient_evals'] * tg + counts['matvecs'] * tm +
+                   counts['objective_evals'] * to)
+    return {'value': est, 'unit': UNIT, 'cores': 1, 'kind': 'oracle',
+            'sample': ('FP64 NumPy oracle at 64^3 nt=8 (gradient %.2fs, matvec %.2fs, objective '
+                       '%.2fs on 1 host core), scaled x%d by grid points and by the GPU solve\'s '
+                       'counts (%d gradients, %d matvecs, %d objectives); %s'
+                       % (tg, tm, to, int(scale), counts['gradient_evals'], counts['matvecs'],
+                          counts['objective_evals'], precision_note))}
+
+
+def cpu_reference(args):
+    """--impl reference: the FP64 oracle as it stands, timed on the host
+    cores.  Each step is a bounded sample: the oracle's full Gauss-Newton solve
+    of the same phantom recipe at 32^3 (nt = 8, H2, beta = 1e-3, gtol 1e-2),
+    whose time is scaled to 256^3 by grid points (x512); the iteration counts
+    of the method do not depend on the mesh size for fixed beta (Sec. III-D)."""
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import problem as opr
+    from oracle import solver as oso
+    from paper_1608_03630_gb300 import synth
+    shape = (32, 32, 32)
+    rho_T, rho_R, _ = synth.phantom_problem(shape, SEED)
+    scale = (SHAPE[0] * SHAPE[1] * SHAPE[2]) / float(32 ** 3)
+    for _ in range(args.warmup):   # warm-up: one small gradient each (imports, caches)
+        opr.Problem(rho_T, rho_R, NT, BETA, KIND, False, presmooth=True).gradient(
+            np.zeros((3,) + shape))
+    times, last = [], None
+    for _ in range(args.steps):
+        P = opr.Problem(rho_T, rho_R, NT, BETA, KIND, False, presmooth=True)
+        t0 = time.perf_counter()
+        _, st = oso.gauss_newton(P, np.zeros((3,) + shape), gtol=1e-2, max_gn=50)
+        times.append(time.perf_counter() - t0)
+        last = st
+    value = scale * float(np.mean(times))
+    line = {
+        'impl': 'reference', 'metric': METRIC, 'value': value, 'unit': UNIT,
+        'n_gpus': args.gpus, 'steps': args.steps, 'warmup': args.warmup,
+        'ms_per_step': 1e3 * value, 'higher_is_better': False, 'scaling': 'weak',
+        'vs_baseline': None, 'dtype': 'f64', 'data': 'synthetic',
+        'config': {'workload': 'phantom 256^3 nt=8 H2 beta=1e-3 (sampled at 32^3)',
+                   'grid': list(SHAPE), 'nt': NT, 'beta': BETA},
+        'cpu_baseline': {'value': value, 'unit': UNIT, 'cores': 1, 'kind': 'oracle',
+                         'sample': 'oracle GN solve at 32^3 (%.1f s, %d GN, %d matvecs), x%d '
+                                   'by grid points' % (float(np.mean(times)), last['gn_iters'],
+                                                       last['matvecs'], int(scale))},
+        'e2e': {'value': value, 'unit': UNIT, 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def gpu_bench(args):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    world, rank, local = dist_env()
+    if world > 1:
+        dist.init_process_group('nccl')
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    from paper_1608_03630_gb300 import reg
+
+    rho_T, rho_R = make_inputs()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        dT = torch.from_numpy(rho_T).cuda()
+        dR = torch.from_numpy(rho_R).cuda()
+        v = torch.zeros((3,) + SHAPE, device='cuda')
+        R = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=args.precision,
+                             stream=stream)
+
+        def step():
+            v.zero_()
+            R.set_images(dT, dR, presmooth=True)
+            return R.solve(v, gtol=1e-2, max_gn=50, max_pcg=500)
+
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        clocks = ClockSampler(local)
+        clocks.start()
+        R.set_timing(True)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        stats = []
+        for _ in range(args.steps):
+            stats.append(step()[1])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        elapsed_ms = ev0.elapsed_time(ev1)
+        timing = R.get_timing()
+        R.set_timing(False)
+        clk = clocks.stop()
+        if world > 1:
+            t = torch.tensor([elapsed_ms], device='cuda')
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            elapsed_ms = float(t.item())
+            dist.barrier()
+
+        # end to end through the host-buffer entry point (H2D images + v, D2H v)
+        hT = torch.from_numpy(rho_T).pin_memory()
+        hR = torch.from_numpy(rho_R).pin_memory()
+        hv = torch.zeros((3,) + SHAPE).pin_memory()
+        e2e_steps = max(1, min(2, args.steps))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            hv.zero_()
+            R.solve_host(hT, hR, hv, presmooth=True, gtol=1e-2, max_gn=50, max_pcg=500)
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        R.close()
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    n = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    per_step_s = elapsed_ms / 1e3 / args.steps
+    value = per_step_s / world          # whole job: seconds per registration
+    last = stats[-1]
+    matvecs = sum(s['matvecs'] for s in stats)
+    peak, peak_kind = peaks()
+    # dominant hand-written kernel by device time
+    hand = {k: v for k, v in timing.items() if k not in ('fft',) and v['ms'] > 0}
+    dom = max(hand, key=lambda k: hand[k]['ms'])
+    d = timing[dom]
+    achieved = d['bytes'] / (d['ms'] / 1e3) / 1e9
+    interp_ph = ('state', 'adjoint', 'incstate', 'incadj', 'departure')
+    ib = sum(timing[p]['bytes'] for p in interp_ph)
+    ims = sum(timing[p]['ms'] for p in interp_ph)
+    sb = timing['spectral']['bytes']
+    sms = timing['spectral']['ms']
+    launches = sum(int(v['launches']) for k, v in timing.items() if k != 'fft')
+    counts = {'gradient_evals': last['gradient_evals'], 'matvecs': last['matvecs'],
+              'objective_evals': last['objective_evals']}
+    line = {
+        'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world,
+        'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': per_step_s * 1e3,
+        'higher_is_better': False, 'scaling': 'weak', 'vs_baseline': None,
+        'dtype': 'f32', 'data': 'synthetic',
+        'config': {'workload': 'phantom 256^3 nt=8 H2 beta=1e-3 %s' % args.precision,
+                   'grid': list(SHAPE), 'nt': NT, 'beta': BETA, 'regularisation': KIND,
+                   'gtol': 1e-2, 'precision': args.precision, 'parallelism': 'replicas',
+                   'l2': 'inputs larger than L2 (working set > 4 GB), no flush'},
+        'solve': {'gn_iters': last['gn_iters'], 'pcg_iters': last['pcg_iters'],
+                  'matvecs': last['matvecs'], 'gnorm_rel': last['gnorm_rel'],
+                  'mismatch_rel': last['mismatch_rel']},
+        'matvecs_per_s': matvecs / (elapsed_ms / 1e3),
+        'interp_gbs': ib / (ims / 1e3) / 1e9 if ims > 0 else None,
+        'spectral_gbs': sb / (sms / 1e3) / 1e9 if sms > 0 else None,
+        'phase_ms_per_step': {k: v['ms'] / args.steps for k, v in timing.items()},
+        'roofline': {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': peak,
+                     'unit': 'GB/s', 'frac': achieved / peak, 'peak_source': peak_kind,
+                     'traffic': None},
+        'gpu_launches': launches,
+        'clocks': clk,
+        'e2e': {'value': e2e_s, 'unit': UNIT, 'h2d_bytes_per_step': 4 * n * 2 + 12 * n,
+                'd2h_bytes_per_step': 12 * n},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line['cpu_baseline'] = cpu_oracle_sample(args.precision, counts)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument('--gpus', type=int, default=1)
+    ap.add_argument('--steps', type=int, default=3)
+    ap.add_argument('--warmup', type=int, default=3)
+    ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
+    ap.add_argument('--precision', default='fp32', choices=['fp32', 'mixed_bf16'])
+    ap.add_argument('--no-cpu-baseline', action='store_true')
+    args = ap.parse_args()
+    if args.impl == 'reference':
+        cpu_reference(args)
+    else:
+        gpu_bench(args)
+
+
+if __name__ == '__main__':
+    main()

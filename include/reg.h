@@ -1,0 +1,244 @@
+/*
+ * reg.h -- C-ABI of the GB300 spectral semi-Lagrangian Gauss-Newton-Krylov
+ * image-registration library (libreg.so).
+ *
+ * The method: Mang, Gholami, Biros, "Distributed-memory large deformation
+ * diffeomorphic 3D image registration", SC16.  Given a template image rho_T
+ * and a reference image rho_R on the periodic grid [0, 2 pi)^3, find the
+ * stationary velocity v minimising
+ *     J[v] = 1/2 ||rho(1) - rho_R||^2 + beta/2 <v, A v>            (Eq. varopt)
+ * where rho is transported by v from rho(0) = rho_T, with div v = 0 in the
+ * incompressible variant.  Every call below runs on one GPU, on the stream set
+ * by reg_set_stream (default: the legacy default stream).
+ *
+ * Conventions (all entry points):
+ *  - Grid: n1 x n2 x n3 points, x_j = 2 pi i_j / n_j, n = n1 n2 n3.  Scalar
+ *    fields are C-contiguous float arrays [n1][n2][n3] (x3 fastest); vector
+ *    fields are structure-of-arrays [3][n1][n2][n3].  Velocities are in
+ *    physical units (domain length 2 pi, unit time).
+ *  - Every float* / const float* argument is CALLER-OWNED DEVICE memory of the
+ *    stated size, 16-byte aligned, unless the name ends in _host.  Inputs and
+ *    outputs must not overlap unless a function says so.  The library never
+ *    keeps a caller pointer after a call returns.
+ *  - The library owns its workspaces (allocated once in reg_create), cuFFT
+ *    plans and CUDA events; all are released by reg_destroy.
+ *  - Return value: a reg_status.  No entry point aborts.  On an error the
+ *    message is available from reg_last_error(ctx); the context stays
+ *    destroyable.  A CUDA error inside a call is reported as REG_ECUDA and
+ *    the context refuses further work (REG_ECUDA) except reg_destroy.
+ *  - Scalars returned through double* are HOST pointers; such calls wait for
+ *    the stream to finish that value.  Calls without host outputs are
+ *    asynchronous on the stream.
+ *  - A context is not thread-safe; use one context per host thread / stream.
+ */
+#ifndef REG_H
+#define REG_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct reg_ctx reg_ctx;
+
+typedef enum {
+    REG_OK = 0,
+    REG_EINVAL = 1,       /* bad argument (size, null pointer, alignment, kind) */
+    REG_ENOMEM = 2,       /* device or host allocation failed */
+    REG_ECUDA = 3,        /* CUDA runtime error (context is now unusable) */
+    REG_ECUFFT = 4,       /* cuFFT plan or execution failure */
+    REG_ENOTREADY = 5,    /* call order: e.g. a matvec before any gradient */
+    REG_ENONFINITE = 6,   /* NaN/Inf in an objective, norm or inner product */
+    REG_EMAXITER = 7,     /* iteration cap reached before the tolerance */
+    REG_ENOTIMPL = 8
+} reg_status;
+
+/* Regularisation operator A(k) (Eq. varopt; Eq. gradient):
+ *  REG_H2    A = |k|^4, the biharmonic from ||Lap v||^2 (the paper's choice);
+ *  REG_H1    A = |k|^2, -Lap from ||grad v||^2;
+ *  REG_H1DIV A = |k|^2 on the Leray-projected velocity (with div v = 0 a
+ *            divergence penalty vanishes, so it acts as REG_H1). */
+enum { REG_H1 = 1, REG_H2 = 2, REG_H1DIV = 3 };
+
+/* Storage precision of the images and the cached state gradients.
+ *  REG_FP32        everything FP32 (reductions FP64);
+ *  REG_MIXED_BF16  rho_T, rho_R and the cached grad rho(t_j) stored in bfloat16;
+ *                  interpolation and FFTs in FP32; reductions in FP64. */
+enum { REG_FP32 = 0, REG_MIXED_BF16 = 1 };
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a registration context for an n1 x n2 x n3 grid with nt
+ * semi-Lagrangian time steps (dt = 1/nt, Sec. III-B2), regularisation weight
+ * beta > 0 and operator reg_kind; incompressible != 0 enforces div v = 0 by
+ * the Leray projection (Eq. gradient).  Allocates every workspace on the
+ * current CUDA device.  Sizes: 4 <= n_j, n <= 2^30, 1 <= nt <= 64.
+ * On success *out owns the context; on failure *out is NULL. */
+int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind,
+               int incompressible, reg_ctx** out);
+
+/* Release every resource of ctx (NULL is accepted).  Always REG_OK. */
+int reg_destroy(reg_ctx* ctx);
+
+/* Message of the last failing call on ctx ("" if none); valid until the next
+ * call on ctx.  With ctx == NULL: the last failure of reg_create on this
+ * thread. */
+const char* reg_last_error(const reg_ctx* ctx);
+
+/* Name of a status code. */
+const char* reg_status_string(int status);
+
+/* Set the CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream()
+ * .cuda_stream) for every later call; NULL = legacy default stream. */
+int reg_set_stream(reg_ctx* ctx, void* stream);
+
+/* Storage precision, REG_FP32 (default) or REG_MIXED_BF16.  Takes effect at
+ * the next reg_set_images. */
+int reg_set_precision(reg_ctx* ctx, int precision);
+
+/* Copy the template rho_T and reference rho_R ([n], device) into the context.
+ * presmooth != 0 applies the spectral Gaussian of one grid cell,
+ * exp(-sum_j h_j^2 k_j^2 / 2), h_j = 2 pi / n_j (Sec. III-B1).  Invalidates the
+ * linearisation point. */
+int reg_set_images(reg_ctx* ctx, const float* rho_T, const float* rho_R,
+                   int presmooth);
+
+/* ----------------------------------------------- objective, gradient, H */
+
+/* J[v] (Eq. varopt) for v [3n]: one forward state solve.  *J is host. */
+int reg_objective(reg_ctx* ctx, const float* v, double* J);
+
+/* Gradient g = beta A v + P b, b = int_0^1 lam grad rho dt (Eq. gradient;
+ * P -> I when compressible), for v [3n] -> g [3n]; *J (host, may be NULL)
+ * receives J[v].  Makes v the linearisation point of later Hessian matvecs:
+ * caches the semi-Lagrangian points of v and -v (Sec. III-C2), the state
+ * history rho(t_j) and its spectral gradients.  v and g may not overlap. */
+int reg_gradient(reg_ctx* ctx, const float* v, float* g, double* J);
+
+/* Gauss-Newton Hessian matvec Hvt = beta A vt + P b~ (Eq. hessian, without
+ * the lambda terms), b~ = int lam~ grad rho dt, at the last reg_gradient's v.
+ * vt, Hvt [3n], may not overlap.  REG_ENOTREADY before any reg_gradient. */
+int reg_hessian_matvec(reg_ctx* ctx, const float* vt, float* Hvt);
+
+/* Spectral preconditioner z = F^-1[ M(k) P(k) F r ], M = 1/(beta A(k)) for
+ * k != 0 and M(0) = 1/beta (Sec. III-A: the inverse regularisation
+ * operator).  r, z [3n]; r == z (in place) is allowed. */
+int reg_precond_apply(reg_ctx* ctx, const float* r, float* z);
+
+/* ------------------------------------------------------------- solver */
+
+typedef struct {
+    double gtol;          /* stop when ||g|| <= gtol ||g_0||            (1e-2) */
+    int max_gn;           /* Gauss-Newton iteration cap                   (50) */
+    int max_pcg;          /* PCG iterations per Newton step              (500) */
+    int forcing;          /* 0: eta = min(0.5, ||g||/||g0||) (quadratic)
+                             1: eta = min(0.5, sqrt(||g||/||g0||))         (0) */
+    double armijo_c;      /* sufficient-decrease constant               (1e-4) */
+    double armijo_shrink; /* step reduction factor                       (0.5) */
+    int armijo_max;       /* line-search trials                           (10) */
+    int use_graph;        /* capture the PCG iteration in a CUDA graph     (1) */
+    int verbose;          /* print one line per Newton iteration to stderr (0) */
+} reg_solve_opts;
+
+typedef struct {
+    int gn_iters, pcg_iters, matvecs, objective_evals, gradient_evals;
+    int line_search_failed;   /* 1 if Armijo found no acceptable step */
+    int negative_curvature;   /* PCG steps stopped by p.Hp <= 0 */
+    double J0, J, gnorm0, gnorm, gnorm_rel, mismatch_rel;
+    double ms_total;          /* wall time of the solve (host clock) */
+} reg_solve_stats;
+
+/* Fill *opts with the defaults listed above. */
+int reg_solve_opts_default(reg_solve_opts* opts);
+
+/* Inexact Gauss-Newton-Krylov solve with Armijo line search (Sec. III-A):
+ * v_inout [3n] is the initial guess on entry (zero, or a learned prediction)
+ * and the solution on exit.  opts NULL = defaults; stats may be NULL.
+ * Returns REG_OK when ||g|| <= gtol ||g_0||, REG_EMAXITER when max_gn was
+ * reached first (v_inout then holds the last accepted iterate). */
+int reg_solve(reg_ctx* ctx, float* v_inout, const reg_solve_opts* opts,
+              reg_solve_stats* stats);
+
+/* The same solve through HOST buffers: uploads rho_T_host, rho_R_host ([n]
+ * each, host memory; pinned memory makes the copies faster) and
+ * v_host_inout [3n], solves, and downloads v into v_host_inout. */
+int reg_solve_host(reg_ctx* ctx, const float* rho_T_host, const float* rho_R_host,
+                   int presmooth, float* v_host_inout, const reg_solve_opts* opts,
+                   reg_solve_stats* stats);
+
+/* ------------------------------------------- steps of the path, one each */
+
+/* RK2 semi-Lagrangian points (Eq. sml-trajectory) of v [3n] and of -v, as
+ * displacements X - x in GRID units: d_fwd, d_adj [3n]. */
+int reg_departure(reg_ctx* ctx, const float* v, float* d_fwd, float* d_adj);
+
+/* Tricubic Lagrange interpolation (Sec. III-C2) of nfields (1..3) scalar
+ * fields field [nfields][n] at the points x + disp (disp [3n], grid units,
+ * any magnitude; periodic wrap) -> out [nfields][n].  The 64 weights of a
+ * point are shared by its fields. */
+int reg_interp(reg_ctx* ctx, const float* field, int nfields, const float* disp,
+               float* out);
+
+/* Forward state transport (Eq. varopt:state): rho_hist [(nt+1)][n] receives
+ * rho(t_0) = rho0, ..., rho(t_nt), stepping with the points d_fwd [3n]. */
+int reg_state_transport(reg_ctx* ctx, const float* rho0, const float* d_fwd,
+                        float* rho_hist);
+
+/* Spectral first derivatives (Sec. III-B1): grad [3n] = grad f (f [n]);
+ * div [n] = div v (v [3n]).  Odd derivatives zero the Nyquist mode. */
+int reg_spectral_grad(reg_ctx* ctx, const float* f, float* grad);
+int reg_spectral_div(reg_ctx* ctx, const float* v, float* div);
+
+/* Leray projection pv = (I - grad Lap^-1 div) v (Eq. gradient); in place ok. */
+int reg_leray(reg_ctx* ctx, const float* v, float* pv);
+
+/* av = beta A v for the context's operator (Eq. gradient); in place ok. */
+int reg_apply_regularisation(reg_ctx* ctx, const float* v, float* av);
+
+/* Spectral Gaussian exp(-sum_j (s_j k_j)^2 / 2) of f [n] -> out [n]
+ * (s_j physical units; Sec. III-B1); in place ok. */
+int reg_gaussian_smooth(reg_ctx* ctx, const float* f, float* out,
+                        double s1, double s2, double s3);
+
+/* Discrete L2 inner product <a, b>_h = (2 pi)^3 / n * sum_i a_i b_i over
+ * count floats (count a multiple of n: scalar or vector fields), accumulated
+ * in FP64 (the Krylov inner products of Sec. III-A).  *out is host. */
+int reg_inner(reg_ctx* ctx, const float* a, const float* b, size_t count,
+              double* out);
+
+/* ------------------------------------------------------------- timing */
+
+enum {
+    REG_PH_DEPARTURE = 0,  /* semi-Lagrangian points */
+    REG_PH_STATE = 1,      /* forward state steps */
+    REG_PH_ADJOINT = 2,    /* adjoint steps + b accumulation */
+    REG_PH_INCSTATE = 3,   /* incremental state steps */
+    REG_PH_INCADJ = 4,     /* incremental adjoint steps + b~ accumulation */
+    REG_PH_INTERP = 5,     /* stand-alone interpolation (reg_interp) */
+    REG_PH_FFT = 6,        /* cuFFT executions */
+    REG_PH_SPECTRAL = 7,   /* spectral multiplier kernels */
+    REG_PH_BLAS = 8,       /* reductions and vector updates */
+    REG_PH_OTHER = 9,      /* pointwise set-up kernels */
+    REG_NPHASES = 10
+};
+
+typedef struct {
+    double ms[REG_NPHASES];         /* summed device time (CUDA events) */
+    long long launches[REG_NPHASES];
+    double bytes[REG_NPHASES];      /* algorithmic HBM bytes of those launches */
+} reg_timing;
+
+/* on != 0: bracket every kernel / FFT launch with CUDA events on the
+ * context's stream and accumulate per phase; on == 0 stops.  Resets the
+ * counters. */
+int reg_set_timing(reg_ctx* ctx, int on);
+
+/* Synchronise the stream and return the accumulated per-phase figures. */
+int reg_get_timing(reg_ctx* ctx, reg_timing* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REG_H */

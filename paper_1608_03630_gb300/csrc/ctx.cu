@@ -1,0 +1,795 @@
+// Context management, timing, the internal operations of the hot path and
+// their C-ABI entry points.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "ctx.h"
+
+namespace reg {
+
+static thread_local std::string g_create_error;
+
+static const double kTwoPi = 6.283185307179586476925286766559;
+
+int fail(reg_ctx* c, int status, const std::string& msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return status;
+}
+
+int fail_cuda(reg_ctx* c, cudaError_t e, const char* what, int line) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s [ctx.cu:%d]", (int)e,
+             cudaGetErrorString(e), what, line);
+    if (c) c->dead = true;
+    return fail(c, REG_ECUDA, buf);
+}
+
+static int fail_fft(reg_ctx* c, cufftResult r, const char* what) {
+    char buf[256];
+    snprintf(buf, sizeof buf, "cuFFT error %d in %s", (int)r, what);
+    return fail(c, REG_ECUFFT, buf);
+}
+
+// ----------------------------------------------------------------- timing
+
+void phase_begin(reg_ctx* c, cudaEvent_t* ev) {
+    *ev = nullptr;
+    if (!c->timing) return;
+    if (c->free_events.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return;
+        c->free_events.push_back(e);
+    }
+    *ev = c->free_events.back();
+    c->free_events.pop_back();
+    cudaEventRecord(*ev, c->stream);
+}
+
+void phase_end(reg_ctx* c, int phase, cudaEvent_t ev, double bytes) {
+    if (!c->timing || !ev) return;
+    if (c->free_events.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { c->free_events.push_back(ev); return; }
+        c->free_events.push_back(e);
+    }
+    cudaEvent_t b = c->free_events.back();
+    c->free_events.pop_back();
+    cudaEventRecord(b, c->stream);
+    c->pending.push_back({phase, ev, b, bytes});
+    // keep the number of outstanding event pairs bounded
+    if (c->pending.size() > 4096) {
+        cudaEventSynchronize(b);
+        for (auto& p : c->pending) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, p.a, p.b);
+            c->acc.ms[p.phase] += ms;
+            c->acc.launches[p.phase] += 1;
+            c->acc.bytes[p.phase] += p.bytes;
+            c->free_events.push_back(p.a);
+            c->free_events.push_back(p.b);
+        }
+        c->pending.clear();
+    }
+}
+
+// RAII helper around one launch.
+struct Phase {
+    reg_ctx* c; int ph; double bytes; cudaEvent_t ev;
+    Phase(reg_ctx* c_, int ph_, double bytes_) : c(c_), ph(ph_), bytes(bytes_) {
+        phase_begin(c, &ev);
+    }
+    ~Phase() { phase_end(c, ph, ev, bytes); }
+};
+
+// ------------------------------------------------------------- operations
+
+int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj) {
+    Phase p(c, REG_PH_DEPARTURE, (double)c->g.n * (d_adj ? 36.0 : 24.0));
+    REG_CK(c, launch_departure(c->g, v, (float)(1.0 / c->nt), d_fwd, d_adj, c->stream));
+    return REG_OK;
+}
+
+int op_fft_r2c(reg_ctx* c, const float* in, float2* out, int ncomp) {
+    Phase p(c, REG_PH_FFT, (double)ncomp * (4.0 * c->g.n + 8.0 * c->g.nc));
+    cufftHandle h = ncomp == 3 ? c->r2c3 : c->r2c1;
+    cufftResult r = cufftExecR2C(h, const_cast<cufftReal*>(in), reinterpret_cast<cufftComplex*>(out));
+    if (r != CUFFT_SUCCESS) return fail_fft(c, r, "cufftExecR2C");
+    return REG_OK;
+}
+
+int op_fft_c2r(reg_ctx* c, float2* in, float* out, int ncomp) {
+    Phase p(c, REG_PH_FFT, (double)ncomp * (4.0 * c->g.n + 8.0 * c->g.nc));
+    cufftHandle h = ncomp == 3 ? c->c2r3 : c->c2r1;
+    cufftResult r = cufftExecC2R(h, reinterpret_cast<cufftComplex*>(in), out);
+    if (r != CUFFT_SUCCESS) return fail_fft(c, r, "cufftExecC2R");
+    return REG_OK;
+}
+
+int op_spectral(reg_ctx* c, SpecOp op, const SpecArgs& a, int nfields) {
+    Phase p(c, REG_PH_SPECTRAL, 8.0 * nfields * c->g.nc);
+    REG_CK(c, launch_spectral(c->g, op, a, c->stream));
+    return REG_OK;
+}
+
+static SpecArgs spec_args(reg_ctx* c) {
+    SpecArgs a;
+    memset(&a, 0, sizeof a);
+    a.beta = c->beta;
+    a.kind = c->kind;
+    a.project = c->incompressible;
+    return a;
+}
+
+int op_grad(reg_ctx* c, const float* f, float* out3) {
+    REG_TRY(op_fft_r2c(c, f, c->spec[0], 1));
+    SpecArgs a = spec_args(c);
+    a.in_a = c->spec[0];
+    a.out = c->spec[1];
+    REG_TRY(op_spectral(c, SPEC_GRAD, a, 4));
+    return op_fft_c2r(c, c->spec[1], out3, 3);
+}
+
+int op_div(reg_ctx* c, const float* v3, float* out) {
+    REG_TRY(op_fft_r2c(c, v3, c->spec[0], 3));
+    SpecArgs a = spec_args(c);
+    a.in_a = c->spec[0];
+    a.out = c->spec[1];
+    REG_TRY(op_spectral(c, SPEC_DIV, a, 4));
+    return op_fft_c2r(c, c->spec[1], out, 1);
+}
+
+int op_leray(reg_ctx* c, const float* v, float* out) {
+    REG_TRY(op_fft_r2c(c, v, c->spec[0], 3));
+    SpecArgs a = spec_args(c);
+    a.in_a = c->spec[0];
+    a.out = c->spec[0];
+    REG_TRY(op_spectral(c, SPEC_LERAY, a, 6));
+    return op_fft_c2r(c, c->spec[0], out, 3);
+}
+
+// dsc[slot] = (2 pi)^3 / n * <a, b>
+int op_inner(reg_ctx* c, const float* a, const float* b, long long count, int slot) {
+    const int nb = blas_blocks();
+    {
+        Phase p(c, REG_PH_BLAS, 8.0 * count);
+        REG_CK(c, launch_dot_partials(a, b, count, c->partials, nb, c->stream));
+    }
+    Phase p(c, REG_PH_BLAS, 0.0);
+    REG_CK(c, launch_finalize(c->partials, nb, kTwoPi * kTwoPi * kTwoPi / c->g.n,
+                              c->dsc + slot, c->stream));
+    return REG_OK;
+}
+
+int bind_stream(reg_ctx* c, cudaStream_t s) {
+    c->stream = s;
+    cufftHandle hs[4] = {c->r2c1, c->c2r1, c->r2c3, c->c2r3};
+    for (int i = 0; i < 4; ++i) {
+        cufftResult r = cufftSetStream(hs[i], s);
+        if (r != CUFFT_SUCCESS) return fail_fft(c, r, "cufftSetStream");
+    }
+    return REG_OK;
+}
+
+int read_scalars(reg_ctx* c, int first, int count) {
+    REG_CK(c, cudaMemcpyAsync(c->hsc + first, c->dsc + first, sizeof(double) * count,
+                              cudaMemcpyDeviceToHost, c->stream));
+    REG_CK(c, cudaStreamSynchronize(c->stream));
+    return REG_OK;
+}
+
+static const float* grad_level(reg_ctx* c, int j) {
+    return c->grad_hist ? c->grad_hist + (long long)j * 3 * c->g.n : nullptr;
+}
+static const __nv_bfloat16* grad_level_bf(reg_ctx* c, int j) {
+    return c->grad_hist_bf ? c->grad_hist_bf + (long long)j * 3 * c->g.n : nullptr;
+}
+
+static double trap_w(int j, int nt) {
+    return (j == 0 || j == nt) ? 0.5 / nt : 1.0 / nt;
+}
+
+// Forward state solve into rho_hist (or into two ping-pong buffers when
+// hist == false); the last step forms lam(1) in buf[out_buf] and the mismatch.
+static int state_solve(reg_ctx* c, const float* d_fwd, float* hist, bool keep_hist,
+                       void* lam_out, const float* divv) {
+    const Dims& g = c->g;
+    const long long n = g.n;
+    const int nt = c->nt;
+    // rho(t_0) = rho_T
+    if (c->precision == REG_MIXED_BF16 && c->img_bf) {
+        Phase p(c, REG_PH_OTHER, 6.0 * n);
+        REG_CK(c, launch_from_bf16(c->img_bf, hist, n, c->stream));
+    } else {
+        REG_CK(c, cudaMemcpyAsync(hist, c->rho_T, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    }
+    const int nb = (g.n + 255) / 256;
+    for (int j = 0; j < nt; ++j) {
+        const float* in = keep_hist ? hist + j * n : hist + (j & 1) * n;
+        float* out = keep_hist ? hist + (j + 1) * n : hist + ((j + 1) & 1) * n;
+        const bool fin = (j == nt - 1);
+        double bytes = 20.0 * n;
+        if (fin) bytes += (4.0 + (lam_out ? (divv ? 12.0 : 4.0) : 0.0)) * n;
+        Phase p(c, REG_PH_STATE, bytes);
+        REG_CK(c, launch_state_step(g, in, d_fwd, out, fin ? c->rho_R : nullptr,
+                                    fin ? divv : nullptr, fin ? lam_out : nullptr,
+                                    c->partials, c->npartials, c->stream));
+    }
+    {
+        Phase p(c, REG_PH_BLAS, 0.0);
+        REG_CK(c, launch_finalize(c->partials, nb, 0.5 * kTwoPi * kTwoPi * kTwoPi / n,
+                                  c->dsc + SC_JMIS, c->stream));
+    }
+    return REG_OK;
+}
+
+// dsc[SC_JREG] = beta/2 <v, A v>_h from the spectrum of v in spec (3 fields).
+static int reg_energy(reg_ctx* c, const float2* vhat) {
+    const int nb = blas_blocks();
+    {
+        Phase p(c, REG_PH_SPECTRAL, 24.0 * c->g.nc);
+        REG_CK(c, launch_spec_energy(c->g, vhat, c->kind, c->partials, nb, c->stream));
+    }
+    const double n = c->g.n;
+    Phase p(c, REG_PH_BLAS, 0.0);
+    REG_CK(c, launch_finalize(c->partials, nb, 0.5 * c->beta * kTwoPi * kTwoPi * kTwoPi / (n * n),
+                              c->dsc + SC_JREG, c->stream));
+    return REG_OK;
+}
+
+int op_objective(reg_ctx* c, const float* v, int slot_J) {
+    (void)slot_J;
+    // scratch only: the linearisation point stays intact
+    REG_TRY(op_departure(c, v, c->tmp3, nullptr));
+    float* ping = reinterpret_cast<float*>(c->buf[0]);   // 2n floats: two levels
+    REG_TRY(state_solve(c, c->tmp3, ping, false, nullptr, nullptr));
+    REG_TRY(op_fft_r2c(c, v, c->spec[0], 3));
+    return reg_energy(c, c->spec[0]);
+}
+
+int op_gradient(reg_ctx* c, const float* v, float* gout, int slot_J) {
+    (void)slot_J;
+    const Dims& g = c->g;
+    const long long n = g.n;
+    const int nt = c->nt;
+    const bool comp = !c->incompressible;
+    c->have_lin = false;
+    REG_TRY(op_departure(c, v, c->d_fwd, c->d_adj));
+    if (comp) REG_TRY(op_div(c, v, c->divv));
+    // state history and lam(1) = rho_R - rho(1) in buf[0]
+    REG_TRY(state_solve(c, c->d_fwd, c->rho_hist, true, c->buf[0], comp ? c->divv : nullptr));
+    // spectral gradients of every level (cached for the matvecs)
+    for (int j = 0; j <= nt; ++j) {
+        if (c->grad_hist_bf) {
+            REG_TRY(op_grad(c, c->rho_hist + j * n, c->tmp3));
+            Phase p(c, REG_PH_OTHER, 18.0 * n);
+            REG_CK(c, launch_to_bf16(c->tmp3, c->grad_hist_bf + (long long)j * 3 * n, 3 * n,
+                                     c->stream));
+        } else {
+            REG_TRY(op_grad(c, c->rho_hist + j * n, c->grad_hist + (long long)j * 3 * n));
+        }
+    }
+    // adjoint backward in time with b accumulation
+    for (int j = nt - 1; j >= 0; --j) {
+        const int k = nt - 1 - j;
+        AdjointStepArgs a;
+        memset(&a, 0, sizeof a);
+        a.lam_in = c->buf[k & 1];
+        a.lam_out = c->buf[(k + 1) & 1];
+        a.d = c->d_adj;
+        a.grad_j = grad_level(c, j);
+        a.grad_j1 = grad_level(c, j + 1);
+        a.grad_j_bf = grad_level_bf(c, j);
+        a.grad_j1_bf = grad_level_bf(c, j + 1);
+        a.b = c->bacc;
+        a.w_j = (float)trap_w(j, nt);
+        a.w_j1 = (float)trap_w(j + 1, nt);
+        a.dt = (float)(1.0 / nt);
+        a.compressible = comp;
+        a.first = (j == nt - 1);
+        const double gb = c->grad_hist_bf ? 6.0 : 12.0;
+        double bytes = (12.0 + (comp ? 16.0 : 8.0) + gb + 24.0) * n;
+        if (a.first) bytes += gb * n - 12.0 * n;
+        Phase p(c, REG_PH_ADJOINT, bytes);
+        REG_CK(c, launch_adjoint_step(g, a, c->stream));
+    }
+    // g = beta A v + P b
+    REG_TRY(op_fft_r2c(c, v, c->spec[0], 3));
+    REG_TRY(reg_energy(c, c->spec[0]));
+    REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
+    SpecArgs a = spec_args(c);
+    a.in_a = c->spec[0];
+    a.in_b = c->spec[1];
+    a.out = c->spec[1];
+    REG_TRY(op_spectral(c, SPEC_ASSEMBLE, a, 9));
+    REG_TRY(op_fft_c2r(c, c->spec[1], gout, 3));
+    c->have_lin = true;
+    return REG_OK;
+}
+
+int op_matvec(reg_ctx* c, const float* vt, float* out) {
+    const Dims& g = c->g;
+    const long long n = g.n;
+    const int nt = c->nt;
+    const bool comp = !c->incompressible;
+    const double gb = c->grad_hist_bf ? 6.0 : 12.0;
+    {
+        Phase p(c, REG_PH_INCSTATE, (12.0 + gb + 8.0) * n);
+        REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), grad_level_bf(c, 0), c->buf[0],
+                                       c->stream));
+    }
+    for (int j = 0; j < nt; ++j) {
+        IncStateStepArgs a;
+        memset(&a, 0, sizeof a);
+        a.in = c->buf[j & 1];
+        a.out = c->buf[(j + 1) & 1];
+        a.d = c->d_fwd;
+        a.vt = vt;
+        a.grad_j1 = grad_level(c, j + 1);
+        a.grad_j1_bf = grad_level_bf(c, j + 1);
+        a.divv = c->divv;
+        a.dt = (float)(1.0 / nt);
+        a.final_step = (j == nt - 1);
+        a.compressible = comp;
+        double bytes = (12.0 + 8.0 + 12.0 + gb + 8.0) * n;
+        if (a.final_step) bytes += (comp ? 4.0 : -4.0) * n;
+        Phase p(c, REG_PH_INCSTATE, bytes);
+        REG_CK(c, launch_incstate_step(g, a, c->stream));
+    }
+    for (int j = nt - 1; j >= 0; --j) {
+        const int k = nt - 1 - j;
+        AdjointStepArgs a;
+        memset(&a, 0, sizeof a);
+        a.lam_in = c->buf[(nt + k) & 1];
+        a.lam_out = c->buf[(nt + k + 1) & 1];
+        a.d = c->d_adj;
+        a.grad_j = grad_level(c, j);
+        a.grad_j1 = grad_level(c, j + 1);
+        a.grad_j_bf = grad_level_bf(c, j);
+        a.grad_j1_bf = grad_level_bf(c, j + 1);
+        a.b = c->bacc;
+        a.w_j = (float)trap_w(j, nt);
+        a.w_j1 = (float)trap_w(j + 1, nt);
+        a.dt = (float)(1.0 / nt);
+        a.compressible = comp;
+        a.first = (j == nt - 1);
+        double bytes = (12.0 + (comp ? 16.0 : 8.0) + gb + 24.0) * n;
+        if (a.first) bytes += gb * n - 12.0 * n;
+        Phase p(c, REG_PH_INCADJ, bytes);
+        REG_CK(c, launch_adjoint_step(g, a, c->stream));
+    }
+    REG_TRY(op_fft_r2c(c, vt, c->spec[0], 3));
+    REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
+    SpecArgs a = spec_args(c);
+    a.in_a = c->spec[0];
+    a.in_b = c->spec[1];
+    a.out = c->spec[1];
+    REG_TRY(op_spectral(c, SPEC_ASSEMBLE, a, 9));
+    return op_fft_c2r(c, c->spec[1], out, 3);
+}
+
+int op_precond(reg_ctx* c, const float* r, float* z) {
+    REG_TRY(op_fft_r2c(c, r, c->spec[0], 3));
+    SpecArgs a = spec_args(c);
+    a.in_a = c->spec[0];
+    a.out = c->spec[0];
+    REG_TRY(op_spectral(c, SPEC_PRECOND, a, 6));
+    return op_fft_c2r(c, c->spec[0], z, 3);
+}
+
+int ensure_solver(reg_ctx* c) {
+    if (c->have_solver) return REG_OK;
+    const size_t bytes = sizeof(float) * 3 * (size_t)c->g.n;
+    for (int i = 0; i < 8; ++i) {
+        cudaError_t e = cudaMalloc(&c->sv[i], bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            for (int k = 0; k < i; ++k) { cudaFree(c->sv[k]); c->sv[k] = nullptr; }
+            return fail(c, REG_ENOMEM, "cannot allocate solver vectors");
+        }
+    }
+    c->have_solver = true;
+    return REG_OK;
+}
+
+}  // namespace reg
+
+// ====================================================================== C-ABI
+
+using namespace reg;
+
+#define CHECK_CTX(c)                                                         \
+    do {                                                                     \
+        if (!(c)) return REG_EINVAL;                                         \
+        if ((c)->dead) return fail(c, REG_ECUDA, "context unusable after a CUDA error"); \
+    } while (0)
+
+#define CHECK_PTR(c, p)                                                      \
+    do {                                                                     \
+        if (!(p)) return fail(c, REG_EINVAL, "null pointer: " #p);           \
+        if (((uintptr_t)(p)) & 15u) return fail(c, REG_EINVAL, "pointer not 16-byte aligned: " #p); \
+    } while (0)
+
+static void free_ctx(reg_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int i = 0; i < 4; ++i)
+        if (c->plans[i]) cufftDestroy(i == 0 ? c->r2c1 : i == 1 ? c->c2r1 : i == 2 ? c->r2c3 : c->c2r3);
+    void* ptrs[] = {c->rho_T, c->rho_R, c->img_bf, c->d_fwd, c->d_adj, c->divv, c->rho_hist,
+                    c->grad_hist, c->grad_hist_bf, c->buf[0], c->buf[1], c->bacc, c->tmp3,
+                    c->spec[0], c->spec[1], c->partials, c->dsc};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (int i = 0; i < 8; ++i)
+        if (c->sv[i]) cudaFree(c->sv[i]);
+    if (c->hsc) cudaFreeHost(c->hsc);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
+    for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto e : c->free_events) cudaEventDestroy(e);
+    delete c;
+}
+
+static int alloc_grad_hist(reg_ctx* c) {
+    const size_t cnt = (size_t)(c->nt + 1) * 3 * c->g.n;
+    if (c->grad_hist) { cudaFree(c->grad_hist); c->grad_hist = nullptr; }
+    if (c->grad_hist_bf) { cudaFree(c->grad_hist_bf); c->grad_hist_bf = nullptr; }
+    cudaError_t e;
+    if (c->precision == REG_MIXED_BF16)
+        e = cudaMalloc(&c->grad_hist_bf, cnt * sizeof(__nv_bfloat16));
+    else
+        e = cudaMalloc(&c->grad_hist, cnt * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, REG_ENOMEM, "cannot allocate the grad rho cache");
+    }
+    return REG_OK;
+}
+
+extern "C" {
+
+int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int incompressible,
+               reg_ctx** out) {
+    if (!out) return fail(nullptr, REG_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n1 < 4 || n2 < 4 || n3 < 4)
+        return fail(nullptr, REG_EINVAL, "grid sizes must be >= 4");
+    if ((long long)n1 * n2 * n3 > (1LL << 30))
+        return fail(nullptr, REG_EINVAL, "grid larger than 2^30 points");
+    if (nt < 1 || nt > 64) return fail(nullptr, REG_EINVAL, "nt must be in [1, 64]");
+    if (!(beta > 0.0) || !std::isfinite(beta)) return fail(nullptr, REG_EINVAL, "beta must be > 0");
+    if (reg_kind != REG_H1 && reg_kind != REG_H2 && reg_kind != REG_H1DIV)
+        return fail(nullptr, REG_EINVAL, "unknown reg_kind");
+    reg_ctx* c = new (std::nothrow) reg_ctx();
+    if (!c) return fail(nullptr, REG_ENOMEM, "host allocation failed");
+    c->g = make_dims(n1, n2, n3);
+    c->nt = nt;
+    c->beta = beta;
+    c->kind = reg_kind;
+    c->incompressible = incompressible ? 1 : 0;
+    c->precision = REG_FP32;
+    c->stream = nullptr;
+    const long long n = c->g.n;
+    const long long nc = c->g.nc;
+    c->npartials = (int)((n + 255) / 256);
+    if (c->npartials < blas_blocks()) c->npartials = blas_blocks();
+    struct A { void** p; size_t bytes; } allocs[] = {
+        {(void**)&c->rho_T, sizeof(float) * n},
+        {(void**)&c->rho_R, sizeof(float) * n},
+        {(void**)&c->d_fwd, sizeof(float) * 3 * n},
+        {(void**)&c->d_adj, sizeof(float) * 3 * n},
+        {(void**)&c->divv, sizeof(float) * n},
+        {(void**)&c->rho_hist, sizeof(float) * (nt + 1) * n},
+        {(void**)&c->buf[0], sizeof(float2) * n},
+        {(void**)&c->buf[1], sizeof(float2) * n},
+        {(void**)&c->bacc, sizeof(float) * 3 * n},
+        {(void**)&c->tmp3, sizeof(float) * 3 * n},
+        {(void**)&c->spec[0], sizeof(float2) * 3 * nc},
+        {(void**)&c->spec[1], sizeof(float2) * 3 * nc},
+        {(void**)&c->partials, sizeof(double) * c->npartials},
+        {(void**)&c->dsc, sizeof(double) * 32},
+    };
+    for (auto& a : allocs) {
+        if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+            cudaGetLastError();
+            free_ctx(c);
+            return fail(nullptr, REG_ENOMEM, "device allocation failed in reg_create");
+        }
+    }
+    if (cudaMallocHost(&c->hsc, sizeof(double) * 32) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return fail(nullptr, REG_ENOMEM, "pinned host allocation failed");
+    }
+    if (alloc_grad_hist(c) != REG_OK) {
+        free_ctx(c);
+        return fail(nullptr, REG_ENOMEM, "cannot allocate the grad rho cache");
+    }
+    cudaMemset(c->dsc, 0, sizeof(double) * 32);
+    int dims[3] = {n1, n2, n3};
+    cufftResult r;
+    r = cufftPlanMany(&c->r2c1, 3, dims, nullptr, 1, (int)n, nullptr, 1, (int)nc, CUFFT_R2C, 1);
+    c->plans[0] = (r == CUFFT_SUCCESS);
+    if (r == CUFFT_SUCCESS) {
+        r = cufftPlanMany(&c->c2r1, 3, dims, nullptr, 1, (int)nc, nullptr, 1, (int)n, CUFFT_C2R, 1);
+        c->plans[1] = (r == CUFFT_SUCCESS);
+    }
+    if (r == CUFFT_SUCCESS) {
+        r = cufftPlanMany(&c->r2c3, 3, dims, nullptr, 1, (int)n, nullptr, 1, (int)nc, CUFFT_R2C, 3);
+        c->plans[2] = (r == CUFFT_SUCCESS);
+    }
+    if (r == CUFFT_SUCCESS) {
+        r = cufftPlanMany(&c->c2r3, 3, dims, nullptr, 1, (int)nc, nullptr, 1, (int)n, CUFFT_C2R, 3);
+        c->plans[3] = (r == CUFFT_SUCCESS);
+    }
+    if (r != CUFFT_SUCCESS) {
+        free_ctx(c);
+        char buf[128];
+        snprintf(buf, sizeof buf, "cufftPlanMany failed (%d)", (int)r);
+        return fail(nullptr, REG_ECUFFT, buf);
+    }
+    if (cudaStreamCreate(&c->capture_stream) != cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return fail(nullptr, REG_ECUDA, "CUDA error during reg_create");
+    }
+    *out = c;
+    return REG_OK;
+}
+
+int reg_destroy(reg_ctx* c) {
+    free_ctx(c);
+    return REG_OK;
+}
+
+const char* reg_last_error(const reg_ctx* c) {
+    return c ? c->err.c_str() : g_create_error.c_str();
+}
+
+const char* reg_status_string(int s) {
+    switch (s) {
+    case REG_OK: return "REG_OK";
+    case REG_EINVAL: return "REG_EINVAL";
+    case REG_ENOMEM: return "REG_ENOMEM";
+    case REG_ECUDA: return "REG_ECUDA";
+    case REG_ECUFFT: return "REG_ECUFFT";
+    case REG_ENOTREADY: return "REG_ENOTREADY";
+    case REG_ENONFINITE: return "REG_ENONFINITE";
+    case REG_EMAXITER: return "REG_EMAXITER";
+    case REG_ENOTIMPL: return "REG_ENOTIMPL";
+    default: return "unknown status";
+    }
+}
+
+int reg_set_stream(reg_ctx* c, void* stream) {
+    CHECK_CTX(c);
+    return bind_stream(c, (cudaStream_t)stream);
+}
+
+int reg_set_precision(reg_ctx* c, int precision) {
+    CHECK_CTX(c);
+    if (precision != REG_FP32 && precision != REG_MIXED_BF16)
+        return fail(c, REG_EINVAL, "unknown precision");
+    if (precision == c->precision) return REG_OK;
+    REG_CK(c, cudaStreamSynchronize(c->stream));
+    c->precision = precision;
+    c->have_lin = false;
+    c->have_images = false;
+    REG_TRY(alloc_grad_hist(c));
+    if (precision == REG_MIXED_BF16 && !c->img_bf) {
+        if (cudaMalloc(&c->img_bf, sizeof(__nv_bfloat16) * 2 * c->g.n) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, REG_ENOMEM, "cannot allocate bf16 images");
+        }
+    }
+    return REG_OK;
+}
+
+int reg_set_images(reg_ctx* c, const float* rho_T, const float* rho_R, int presmooth) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, rho_T);
+    CHECK_PTR(c, rho_R);
+    const long long n = c->g.n;
+    c->have_lin = false;
+    if (rho_T != c->rho_T)
+        REG_CK(c, cudaMemcpyAsync(c->rho_T, rho_T, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    if (rho_R != c->rho_R)
+        REG_CK(c, cudaMemcpyAsync(c->rho_R, rho_R, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    if (presmooth) {
+        const double h1 = kTwoPi / c->g.n1, h2 = kTwoPi / c->g.n2, h3 = kTwoPi / c->g.n3;
+        for (int k = 0; k < 2; ++k) {
+            float* f = k == 0 ? c->rho_T : c->rho_R;
+            REG_TRY(op_fft_r2c(c, f, c->spec[0], 1));
+            SpecArgs a = spec_args(c);
+            a.in_a = c->spec[0];
+            a.out = c->spec[0];
+            a.s1 = (float)h1; a.s2 = (float)h2; a.s3 = (float)h3;
+            REG_TRY(op_spectral(c, SPEC_GAUSS, a, 2));
+            REG_TRY(op_fft_c2r(c, c->spec[0], f, 1));
+        }
+    }
+    if (c->precision == REG_MIXED_BF16) {
+        // images are kept in bfloat16: round both, and use the rounded values
+        REG_CK(c, launch_to_bf16(c->rho_T, c->img_bf, n, c->stream));
+        REG_CK(c, launch_to_bf16(c->rho_R, c->img_bf + n, n, c->stream));
+        REG_CK(c, launch_from_bf16(c->img_bf + n, c->rho_R, n, c->stream));
+    }
+    c->have_images = true;
+    return REG_OK;
+}
+
+int reg_objective(reg_ctx* c, const float* v, double* J) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, v);
+    if (!J) return fail(c, REG_EINVAL, "J is NULL");
+    if (!c->have_images) return fail(c, REG_ENOTREADY, "reg_set_images first");
+    REG_TRY(op_objective(c, v, SC_J));
+    REG_TRY(read_scalars(c, SC_JMIS, 2));
+    *J = c->hsc[SC_JMIS] + c->hsc[SC_JREG];
+    if (!std::isfinite(*J)) return fail(c, REG_ENONFINITE, "objective is not finite");
+    return REG_OK;
+}
+
+int reg_gradient(reg_ctx* c, const float* v, float* g, double* J) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, v);
+    CHECK_PTR(c, g);
+    if (v == g) return fail(c, REG_EINVAL, "v and g overlap");
+    if (!c->have_images) return fail(c, REG_ENOTREADY, "reg_set_images first");
+    REG_TRY(op_gradient(c, v, g, SC_J));
+    if (J) {
+        REG_TRY(read_scalars(c, SC_JMIS, 2));
+        *J = c->hsc[SC_JMIS] + c->hsc[SC_JREG];
+        if (!std::isfinite(*J)) return fail(c, REG_ENONFINITE, "objective is not finite");
+    }
+    return REG_OK;
+}
+
+int reg_hessian_matvec(reg_ctx* c, const float* vt, float* Hvt) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, vt);
+    CHECK_PTR(c, Hvt);
+    if (vt == Hvt) return fail(c, REG_EINVAL, "vt and Hvt overlap");
+    if (!c->have_lin) return fail(c, REG_ENOTREADY, "reg_gradient must come first");
+    return op_matvec(c, vt, Hvt);
+}
+
+int reg_precond_apply(reg_ctx* c, const float* r, float* z) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, r);
+    CHECK_PTR(c, z);
+    return op_precond(c, r, z);
+}
+
+int reg_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, v);
+    CHECK_PTR(c, d_fwd);
+    CHECK_PTR(c, d_adj);
+    return op_departure(c, v, d_fwd, d_adj);
+}
+
+int reg_interp(reg_ctx* c, const float* field, int nfields, const float* disp, float* out) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, field);
+    CHECK_PTR(c, disp);
+    CHECK_PTR(c, out);
+    if (nfields < 1 || nfields > 3) return fail(c, REG_EINVAL, "nfields must be 1..3");
+    Phase p(c, REG_PH_INTERP, (double)c->g.n * (12.0 + 8.0 * nfields));
+    REG_CK(c, launch_interp(c->g, field, nfields, disp, out, c->stream));
+    return REG_OK;
+}
+
+int reg_state_transport(reg_ctx* c, const float* rho0, const float* d_fwd, float* rho_hist) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, rho0);
+    CHECK_PTR(c, d_fwd);
+    CHECK_PTR(c, rho_hist);
+    const long long n = c->g.n;
+    REG_CK(c, cudaMemcpyAsync(rho_hist, rho0, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                              c->stream));
+    for (int j = 0; j < c->nt; ++j) {
+        Phase p(c, REG_PH_STATE, 20.0 * n);
+        REG_CK(c, launch_state_step(c->g, rho_hist + j * n, d_fwd, rho_hist + (j + 1) * n,
+                                    nullptr, nullptr, nullptr, nullptr, 0, c->stream));
+    }
+    return REG_OK;
+}
+
+int reg_spectral_grad(reg_ctx* c, const float* f, float* grad) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, f);
+    CHECK_PTR(c, grad);
+    return op_grad(c, f, grad);
+}
+
+int reg_spectral_div(reg_ctx* c, const float* v, float* div) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, v);
+    CHECK_PTR(c, div);
+    return op_div(c, v, div);
+}
+
+int reg_leray(reg_ctx* c, const float* v, float* pv) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, v);
+    CHECK_PTR(c, pv);
+    return op_leray(c, v, pv);
+}
+
+int reg_apply_regularisation(reg_ctx* c, const float* v, float* av) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, v);
+    CHECK_PTR(c, av);
+    REG_TRY(op_fft_r2c(c, v, c->spec[0], 3));
+    SpecArgs a = spec_args(c);
+    a.in_a = c->spec[0];
+    a.out = c->spec[0];
+    REG_TRY(op_spectral(c, SPEC_REG, a, 6));
+    return op_fft_c2r(c, c->spec[0], av, 3);
+}
+
+int reg_gaussian_smooth(reg_ctx* c, const float* f, float* out, double s1, double s2, double s3) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, f);
+    CHECK_PTR(c, out);
+    REG_TRY(op_fft_r2c(c, f, c->spec[0], 1));
+    SpecArgs a = spec_args(c);
+    a.in_a = c->spec[0];
+    a.out = c->spec[0];
+    a.s1 = (float)s1; a.s2 = (float)s2; a.s3 = (float)s3;
+    REG_TRY(op_spectral(c, SPEC_GAUSS, a, 2));
+    return op_fft_c2r(c, c->spec[0], out, 1);
+}
+
+int reg_inner(reg_ctx* c, const float* a, const float* b, size_t count, double* out) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, a);
+    CHECK_PTR(c, b);
+    if (!out) return fail(c, REG_EINVAL, "out is NULL");
+    if (count == 0 || count % (size_t)c->g.n)
+        return fail(c, REG_EINVAL, "count must be a positive multiple of n");
+    REG_TRY(op_inner(c, a, b, (long long)count, SC_INNER));
+    REG_TRY(read_scalars(c, SC_INNER, 1));
+    *out = c->hsc[SC_INNER];
+    if (!std::isfinite(*out)) return fail(c, REG_ENONFINITE, "inner product is not finite");
+    return REG_OK;
+}
+
+int reg_set_timing(reg_ctx* c, int on) {
+    CHECK_CTX(c);
+    REG_CK(c, cudaStreamSynchronize(c->stream));
+    for (auto& p : c->pending) {
+        c->free_events.push_back(p.a);
+        c->free_events.push_back(p.b);
+    }
+    c->pending.clear();
+    memset(&c->acc, 0, sizeof c->acc);
+    c->timing = on != 0;
+    return REG_OK;
+}
+
+int reg_get_timing(reg_ctx* c, reg_timing* out) {
+    CHECK_CTX(c);
+    if (!out) return fail(c, REG_EINVAL, "out is NULL");
+    REG_CK(c, cudaStreamSynchronize(c->stream));
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        REG_CK(c, cudaEventElapsedTime(&ms, p.a, p.b));
+        c->acc.ms[p.phase] += ms;
+        c->acc.launches[p.phase] += 1;
+        c->acc.bytes[p.phase] += p.bytes;
+        c->free_events.push_back(p.a);
+        c->free_events.push_back(p.b);
+    }
+    c->pending.clear();
+    *out = c->acc;
+    return REG_OK;
+}
+
+}  // extern "C"

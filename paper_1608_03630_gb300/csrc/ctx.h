@@ -1,0 +1,109 @@
+// The registration context behind the opaque reg_ctx handle, and the
+// internal operations shared by the C-ABI entry points and the solver.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "reg.h"
+
+struct reg_ctx {
+    reg::Dims g;
+    int nt;
+    double beta;
+    int kind;
+    int incompressible;
+    int precision;
+    cudaStream_t stream;
+    cudaStream_t capture_stream;  // owned; used to capture CUDA graphs
+    std::string err;
+    bool dead;            // a CUDA error happened: refuse further work
+
+    // cuFFT plans: one field and three fields (batched)
+    cufftHandle r2c1, c2r1, r2c3, c2r3;
+    bool plans[4];
+
+    // images (FP32 copies; bf16 copies in mixed precision)
+    float* rho_T;
+    float* rho_R;
+    __nv_bfloat16* img_bf;        // [2n] rho_T, rho_R in bf16 (mixed precision)
+    bool have_images;
+
+    // linearisation point
+    bool have_lin;
+    float* d_fwd;        // [3n]
+    float* d_adj;        // [3n]
+    float* divv;         // [n] (compressible)
+    float* rho_hist;     // [(nt+1) n]
+    float* grad_hist;    // [(nt+1) 3n] (FP32 mode)
+    __nv_bfloat16* grad_hist_bf;  // [(nt+1) 3n] (mixed precision)
+
+    // scratch
+    float2* buf[2];      // [n] float2 each: transport ping-pong
+    float* bacc;         // [3n] b / b~ accumulator
+    float* tmp3;         // [3n] real scratch
+    float2* spec[2];     // [3 nc] complex scratch each
+    double* partials;    // FP64 partial sums
+    int npartials;
+    double* dsc;         // device scalars [32]
+    double* hsc;         // pinned host mirror [32]
+
+    // solver vectors [3n] each
+    float* sv[8];
+    bool have_solver;
+
+    // timing
+    bool timing;
+    struct Pending { int phase; cudaEvent_t a, b; double bytes; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> free_events;
+    reg_timing acc;
+};
+
+namespace reg {
+
+int fail(reg_ctx* c, int status, const std::string& msg);
+int fail_cuda(reg_ctx* c, cudaError_t e, const char* what, int line);
+
+#define REG_CK(ctx, call)                                                     \
+    do {                                                                      \
+        cudaError_t e_ = (call);                                              \
+        if (e_ != cudaSuccess) return ::reg::fail_cuda(ctx, e_, #call, __LINE__); \
+    } while (0)
+
+#define REG_TRY(call)                     \
+    do {                                  \
+        int s_ = (call);                  \
+        if (s_ != REG_OK) return s_;      \
+    } while (0)
+
+// Phase timing: begin() before a launch, end() after it (no-ops when off).
+void phase_begin(reg_ctx* c, cudaEvent_t* ev);
+void phase_end(reg_ctx* c, int phase, cudaEvent_t ev, double bytes);
+
+// Internal operations (device pointers; all on c->stream).
+int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj);
+int op_fft_r2c(reg_ctx* c, const float* in, float2* out, int ncomp);
+int op_fft_c2r(reg_ctx* c, float2* in, float* out, int ncomp);
+int op_spectral(reg_ctx* c, SpecOp op, const SpecArgs& a, int ncomp_bytes_fields);
+int op_grad(reg_ctx* c, const float* f, float* out3);
+int op_div(reg_ctx* c, const float* v3, float* out);
+int op_inner(reg_ctx* c, const float* a, const float* b, long long count, int slot);
+int op_gradient(reg_ctx* c, const float* v, float* g, int slot_J);
+int op_objective(reg_ctx* c, const float* v, int slot_J);
+int op_matvec(reg_ctx* c, const float* vt, float* out);
+int op_precond(reg_ctx* c, const float* r, float* z);
+int op_leray(reg_ctx* c, const float* v, float* out);
+int read_scalars(reg_ctx* c, int first, int count);   // dsc -> hsc, synchronises
+int bind_stream(reg_ctx* c, cudaStream_t s);         // launch stream + cuFFT plans
+int ensure_solver(reg_ctx* c);
+
+// Device scalar slots.
+enum {
+    SC_JMIS = 0, SC_JREG = 1, SC_J = 2, SC_TMP = 3,
+    SC_RZ = 4, SC_PQ = 5, SC_RR = 6, SC_RZNEW = 7, SC_GG = 8, SC_GS = 9,
+    SC_INNER = 10
+};
+
+}  // namespace reg

@@ -1,0 +1,308 @@
+"""Thin Python binding of libreg.so (the C-ABI in include/reg.h).
+
+Argument marshalling only: every step of the registration path runs in the
+library's CUDA kernels and cuFFT.  Fields are torch CUDA float32 tensors,
+contiguous, scalar fields shaped (n1, n2, n3) and vector fields (3, n1, n2, n3);
+the binding passes their device pointers and the current torch stream.  If
+the library is not built, loading raises -- there is no other code path.
+"""
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, 'libreg.so')
+
+H1, H2, H1DIV = 1, 2, 3
+KINDS = {'H1': H1, 'H2': H2, 'H1DIV': H1DIV}
+FP32, MIXED_BF16 = 0, 1
+PHASES = ('departure', 'state', 'adjoint', 'incstate', 'incadj', 'interp', 'fft',
+          'spectral', 'blas', 'other')
+
+
+class RegError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__('%s: %s' % (status_name(status), message))
+        self.status = status
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [('gtol', ctypes.c_double), ('max_gn', ctypes.c_int),
+                ('max_pcg', ctypes.c_int), ('forcing', ctypes.c_int),
+                ('armijo_c', ctypes.c_double), ('armijo_shrink', ctypes.c_double),
+                ('armijo_max', ctypes.c_int), ('use_graph', ctypes.c_int),
+                ('verbose', ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [('gn_iters', ctypes.c_int), ('pcg_iters', ctypes.c_int),
+                ('matvecs', ctypes.c_int), ('objective_evals', ctypes.c_int),
+                ('gradient_evals', ctypes.c_int), ('line_search_failed', ctypes.c_int),
+                ('negative_curvature', ctypes.c_int),
+                ('J0', ctypes.c_double), ('J', ctypes.c_double),
+                ('gnorm0', ctypes.c_double), ('gnorm', ctypes.c_double),
+                ('gnorm_rel', ctypes.c_double), ('mismatch_rel', ctypes.c_double),
+                ('ms_total', ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+NPHASES = 10
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [('ms', ctypes.c_double * NPHASES), ('launches', ctypes.c_longlong * NPHASES),
+                ('bytes', ctypes.c_double * NPHASES)]
+
+    def as_dict(self):
+        return {p: dict(ms=self.ms[i], launches=self.launches[i], bytes=self.bytes[i])
+                for i, p in enumerate(PHASES)}
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_D = ctypes.c_double
+
+_SIGS = {
+    'reg_create': [_I, _I, _I, _I, _D, _I, _I, ctypes.POINTER(_P)],
+    'reg_destroy': [_P],
+    'reg_set_stream': [_P, _P],
+    'reg_set_precision': [_P, _I],
+    'reg_set_images': [_P, _P, _P, _I],
+    'reg_objective': [_P, _P, ctypes.POINTER(_D)],
+    'reg_gradient': [_P, _P, _P, ctypes.POINTER(_D)],
+    'reg_hessian_matvec': [_P, _P, _P],
+    'reg_precond_apply': [_P, _P, _P],
+    'reg_solve_opts_default': [ctypes.POINTER(SolveOpts)],
+    'reg_solve': [_P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)],
+    'reg_solve_host': [_P, _P, _P, _I, _P, ctypes.POINTER(SolveOpts),
+                       ctypes.POINTER(SolveStats)],
+    'reg_departure': [_P, _P, _P, _P],
+    'reg_interp': [_P, _P, _I, _P, _P],
+    'reg_state_transport': [_P, _P, _P, _P],
+    'reg_spectral_grad': [_P, _P, _P],
+    'reg_spectral_div': [_P, _P, _P],
+    'reg_leray': [_P, _P, _P],
+    'reg_apply_regularisation': [_P, _P, _P],
+    'reg_gaussian_smooth': [_P, _P, _P, _D, _D, _D],
+    'reg_inner': [_P, _P, _P, ctypes.c_size_t, ctypes.POINTER(_D)],
+    'reg_set_timing': [_P, _I],
+    'reg_get_timing': [_P, ctypes.POINTER(Timing)],
+}
+
+
+def lib():
+    """Load libreg.so once (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError('libreg.so is not built (%s); run '
+                              '`python -c "import __graft_entry__ as g; g.build()"`' % LIB_PATH)
+        l = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(l, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        l.reg_last_error.argtypes = [_P]
+        l.reg_last_error.restype = ctypes.c_char_p
+        l.reg_status_string.argtypes = [_I]
+        l.reg_status_string.restype = ctypes.c_char_p
+        _lib = l
+    return _lib
+
+
+def status_name(s):
+    try:
+        return lib().reg_status_string(s).decode()
+    except Exception:
+        return 'status %d' % s
+
+
+def _ptr(t, shape=None, what='tensor'):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError('%s must be a torch tensor' % what)
+    if t.device.type != 'cuda' or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError('%s must be a contiguous CUDA float32 tensor' % what)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError('%s has shape %s, expected %s' % (what, tuple(t.shape), tuple(shape)))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Registration:
+    """One registration context (reg_create ... reg_destroy)."""
+
+    def __init__(self, shape, nt, beta, kind='H2', incompressible=False, precision='fp32',
+                 stream=None):
+        self.shape = tuple(int(s) for s in shape)
+        self.nt = int(nt)
+        self.n = self.shape[0] * self.shape[1] * self.shape[2]
+        self._ctx = ctypes.c_void_p()
+        L = lib()
+        s = L.reg_create(self.shape[0], self.shape[1], self.shape[2], self.nt, float(beta),
+                         KINDS[kind] if isinstance(kind, str) else int(kind),
+                         1 if incompressible else 0, ctypes.byref(self._ctx))
+        if s != 0:
+            raise RegError(s, L.reg_last_error(None).decode())
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        self._call('reg_set_stream', ctypes.c_void_p(stream.cuda_stream))
+        if precision not in ('fp32', 'mixed_bf16'):
+            raise ValueError(precision)
+        if precision == 'mixed_bf16':
+            self._call('reg_set_precision', MIXED_BF16)
+
+    # -- plumbing ---------------------------------------------------------
+    def _call(self, name, *args):
+        s = getattr(lib(), name)(self._ctx, *args)
+        if s != 0:
+            raise RegError(s, lib().reg_last_error(self._ctx).decode())
+        return s
+
+    def close(self):
+        if self._ctx and self._ctx.value:
+            lib().reg_destroy(self._ctx)
+            self._ctx = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def vshape(self):
+        return (3,) + self.shape
+
+    def _new(self, shape):
+        return torch.empty(shape, device='cuda', dtype=torch.float32)
+
+    # -- API --------------------------------------------------------------
+    def set_images(self, rho_T, rho_R, presmooth=False):
+        self._call('reg_set_images', _ptr(rho_T, self.shape, 'rho_T'),
+                   _ptr(rho_R, self.shape, 'rho_R'), 1 if presmooth else 0)
+
+    def objective(self, v):
+        J = ctypes.c_double()
+        self._call('reg_objective', _ptr(v, self.vshape, 'v'), ctypes.byref(J))
+        return J.value
+
+    def gradient(self, v, out=None):
+        g = self._new(self.vshape) if out is None else out
+        J = ctypes.c_double()
+        self._call('reg_gradient', _ptr(v, self.vshape, 'v'), _ptr(g, self.vshape, 'g'),
+                   ctypes.byref(J))
+        return g, J.value
+
+    def hessian_matvec(self, vt, out=None):
+        o = self._new(self.vshape) if out is None else out
+        self._call('reg_hessian_matvec', _ptr(vt, self.vshape, 'vt'), _ptr(o, self.vshape, 'Hvt'))
+        return o
+
+    def precond(self, r, out=None):
+        o = self._new(self.vshape) if out is None else out
+        self._call('reg_precond_apply', _ptr(r, self.vshape, 'r'), _ptr(o, self.vshape, 'z'))
+        return o
+
+    @staticmethod
+    def default_opts():
+        o = SolveOpts()
+        lib().reg_solve_opts_default(ctypes.byref(o))
+        return o
+
+    def _opts(self, kw):
+        o = self.default_opts()
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def solve(self, v, **opts):
+        """Solve in place from the initial guess v; returns (status, stats)."""
+        st = SolveStats()
+        s = lib().reg_solve(self._ctx, _ptr(v, self.vshape, 'v'), ctypes.byref(self._opts(opts)),
+                            ctypes.byref(st))
+        if s not in (0, 7):
+            raise RegError(s, lib().reg_last_error(self._ctx).decode())
+        return s, st.as_dict()
+
+    def solve_host(self, rho_T_host, rho_R_host, v_host, presmooth=False, **opts):
+        """Same solve through host (CPU) float32 tensors; v_host is updated."""
+        for t, nm in ((rho_T_host, 'rho_T'), (rho_R_host, 'rho_R'), (v_host, 'v')):
+            if t.device.type != 'cpu' or t.dtype != torch.float32 or not t.is_contiguous():
+                raise ValueError('%s must be a contiguous CPU float32 tensor' % nm)
+        st = SolveStats()
+        s = lib().reg_solve_host(self._ctx, ctypes.c_void_p(rho_T_host.data_ptr()),
+                                 ctypes.c_void_p(rho_R_host.data_ptr()), 1 if presmooth else 0,
+                                 ctypes.c_void_p(v_host.data_ptr()),
+                                 ctypes.byref(self._opts(opts)), ctypes.byref(st))
+        if s not in (0, 7):
+            raise RegError(s, lib().reg_last_error(self._ctx).decode())
+        return s, st.as_dict()
+
+    def departure(self, v):
+        df, da = self._new(self.vshape), self._new(self.vshape)
+        self._call('reg_departure', _ptr(v, self.vshape, 'v'), _ptr(df), _ptr(da))
+        return df, da
+
+    def interp(self, field, disp, out=None):
+        nf = 1 if field.dim() == 3 else field.shape[0]
+        o = torch.empty_like(field) if out is None else out
+        self._call('reg_interp', _ptr(field, None, 'field'), nf, _ptr(disp, self.vshape, 'disp'),
+                   _ptr(o, tuple(field.shape), 'out'))
+        return o
+
+    def state_transport(self, rho0, d_fwd):
+        hist = self._new((self.nt + 1,) + self.shape)
+        self._call('reg_state_transport', _ptr(rho0, self.shape, 'rho0'),
+                   _ptr(d_fwd, self.vshape, 'd_fwd'), _ptr(hist))
+        return hist
+
+    def spectral_grad(self, f):
+        o = self._new(self.vshape)
+        self._call('reg_spectral_grad', _ptr(f, self.shape, 'f'), _ptr(o))
+        return o
+
+    def spectral_div(self, v):
+        o = self._new(self.shape)
+        self._call('reg_spectral_div', _ptr(v, self.vshape, 'v'), _ptr(o))
+        return o
+
+    def leray(self, v, out=None):
+        o = self._new(self.vshape) if out is None else out
+        self._call('reg_leray', _ptr(v, self.vshape, 'v'), _ptr(o, self.vshape, 'out'))
+        return o
+
+    def apply_regularisation(self, v):
+        o = self._new(self.vshape)
+        self._call('reg_apply_regularisation', _ptr(v, self.vshape, 'v'), _ptr(o))
+        return o
+
+    def gaussian_smooth(self, f, sigma):
+        o = self._new(self.shape)
+        self._call('reg_gaussian_smooth', _ptr(f, self.shape, 'f'), _ptr(o), float(sigma[0]),
+                   float(sigma[1]), float(sigma[2]))
+        return o
+
+    def inner(self, a, b):
+        out = ctypes.c_double()
+        self._call('reg_inner', _ptr(a), _ptr(b), ctypes.c_size_t(a.numel()), ctypes.byref(out))
+        return out.value
+
+    def set_timing(self, on):
+        self._call('reg_set_timing', 1 if on else 0)
+
+    def get_timing(self):
+        t = Timing()
+        self._call('reg_get_timing', ctypes.byref(t))
+        return t.as_dict()

@@ -1,0 +1,76 @@
+"""Host-side checks of the C-ABI library (no GPU needed).
+
+The library must build, load and export every function include/reg.h
+declares; argument validation that happens before any CUDA call is checked
+here on the CPU.
+"""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in os.listdir(os.path.join(ROOT, 'include')):
+        if fn.endswith('.h'):
+            text = open(os.path.join(ROOT, 'include', fn)).read()
+            text = re.sub(r'/\*.*?\*/', '', text, flags=re.S)
+            names += re.findall(r'^\s*(?:const\s+)?\w+\s*\*?\s*(reg_\w+)\s*\(', text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope='module')
+def lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1608_03630_gb300 import reg
+    return reg.lib()
+
+
+def test_header_declares_the_north_star_calls():
+    names = declared_functions()
+    for n in ('reg_create', 'reg_set_images', 'reg_gradient', 'reg_hessian_matvec',
+              'reg_precond_apply', 'reg_solve', 'reg_destroy'):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib):
+    out = ctypes.c_void_p()
+    cases = [(2, 8, 8, 4, 1e-2, 2, 0),        # grid too small
+             (8, 8, 8, 0, 1e-2, 2, 0),        # nt < 1
+             (8, 8, 8, 65, 1e-2, 2, 0),       # nt > 64
+             (8, 8, 8, 4, 0.0, 2, 0),         # beta <= 0
+             (8, 8, 8, 4, -1.0, 2, 0),
+             (8, 8, 8, 4, 1e-2, 7, 0),        # unknown operator
+             (2048, 1024, 1024, 4, 1e-2, 2, 0)]   # more than 2^30 points
+    for args in cases:
+        s = lib.reg_create(*args, ctypes.byref(out))
+        assert s == 1, (args, s)                 # REG_EINVAL
+        assert out.value is None
+        assert lib.reg_last_error(None)
+
+
+def test_status_strings_and_default_options(lib):
+    from paper_1608_03630_gb300 import reg
+    assert lib.reg_status_string(0) == b'REG_OK'
+    assert lib.reg_status_string(7) == b'REG_EMAXITER'
+    o = reg.Registration.default_opts()
+    assert o.gtol == 1e-2 and o.max_gn == 50 and o.max_pcg == 500
+    assert o.armijo_c == 1e-4 and o.armijo_shrink == 0.5
+
+
+def test_null_context_is_rejected(lib):
+    assert lib.reg_destroy(None) == 0
+    assert lib.reg_set_stream(None, None) == 1
+    assert lib.reg_hessian_matvec(None, None, None) == 1
+    assert lib.reg_solve(None, None, None, None) == 1

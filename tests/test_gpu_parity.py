@@ -1,0 +1,239 @@
+"""GPU parity: every step of the path through the C-ABI against the FP64 oracle.
+
+Sizes span several thread blocks and ragged tails (no dimension a multiple of
+the 256-thread block or of 32).  Tolerances: the FP32 kernels against the
+FP64 oracle at 1e-5 relative (single steps) and the gradient and Hessian
+matvec at 1e-4 relative L2 (the stated target for the FP32 path).
+"""
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip('torch')
+
+from oracle import interp as oip
+from oracle import problem as opr
+from oracle import solver as oso
+from oracle import spectral as osp
+from oracle import transport as otr
+from paper_1608_03630_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(32, 32, 32), (20, 28, 44), (17, 23, 30)]
+
+
+@pytest.fixture(scope='module')
+def reg():
+    if not torch.cuda.is_available():
+        pytest.skip('no CUDA device')
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1608_03630_gb300 import reg as _reg
+    return _reg
+
+
+def dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device='cuda')
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().double().numpy()
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize('shape', SHAPES)
+def test_departure_points(reg, shape):
+    nt = 4
+    v = 2.5 * synth.bandlimited(shape, 3, 7)      # several cells per step
+    R = reg.Registration(shape, nt, 1e-2)
+    df, da = R.departure(dev(v))
+    ef = otr.departure(v, 1.0 / nt)
+    ea = otr.departure(-v, 1.0 / nt)
+    assert np.abs(host(df) - ef).max() < 2e-5 * max(1.0, np.abs(ef).max())
+    assert np.abs(host(da) - ea).max() < 2e-5 * max(1.0, np.abs(ea).max())
+    R.close()
+
+
+@pytest.mark.parametrize('shape', SHAPES)
+@pytest.mark.parametrize('nf', [1, 2, 3])
+def test_interpolation_with_large_displacements(reg, shape, nf):
+    rng = np.random.default_rng(11)
+    f = synth.bandlimited(shape, 5, 13, ncomp=nf)
+    # displacements up to +-1.5 N: exercises the periodic wrap, CFL >> 1
+    d = np.stack([rng.uniform(-1.5 * n, 1.5 * n, shape) for n in shape])
+    R = reg.Registration(shape, 4, 1e-2)
+    out = host(R.interp(dev(f), dev(d)))
+    for c in range(nf):
+        exp = oip.interp_at_displacement(f[c], d)
+        assert np.abs(out[c] - exp).max() < 1e-5 * np.abs(f[c]).max() * 8
+    R.close()
+
+
+def test_interpolation_exact_at_integer_displacements(reg):
+    shape = (24, 20, 36)
+    rng = np.random.default_rng(3)
+    f = rng.standard_normal(shape)
+    d = np.stack([rng.integers(-50, 50, shape) for _ in range(3)]).astype(float)
+    R = reg.Registration(shape, 4, 1e-2)
+    out = host(R.interp(dev(f[None]), dev(d)))[0]
+    assert np.abs(out - oip.interp_at_displacement(f, d)).max() < 1e-6
+    R.close()
+
+
+@pytest.mark.parametrize('shape', SHAPES[:2])
+def test_state_transport(reg, shape):
+    nt = 4
+    v = 1.5 * synth.bandlimited(shape, 2, 21)
+    rho0 = synth.bandlimited(shape, 4, 22, ncomp=None)
+    d = otr.departure(v, 1.0 / nt)
+    R = reg.Registration(shape, nt, 1e-2)
+    hist = host(R.state_transport(dev(rho0), dev(d)))
+    exp = otr.state_solve(rho0, d, nt)
+    for j in range(nt + 1):
+        assert rel(hist[j], exp[j]) < 1e-5
+    R.close()
+
+
+@pytest.mark.parametrize('shape', [(32, 32, 32), (20, 28, 44)])
+def test_spectral_operators(reg, shape):
+    f = synth.bandlimited(shape, 6, 31, ncomp=None)
+    v = synth.bandlimited(shape, 6, 32)
+    beta = 3e-3
+    for kind in ('H2', 'H1'):
+        for incompressible in (False, True):
+            R = reg.Registration(shape, 4, beta, kind, incompressible)
+            assert rel(host(R.spectral_grad(dev(f))), osp.gradient(f)) < 1e-5
+            assert rel(host(R.spectral_div(dev(v))), osp.divergence(v)) < 1e-5
+            assert rel(host(R.leray(dev(v))), osp.leray(v)) < 1e-5
+            assert rel(host(R.apply_regularisation(dev(v))),
+                       beta * osp.apply_regularisation(v, kind)) < 1e-5
+            assert rel(host(R.precond(dev(v))),
+                       osp.preconditioner(v, beta, kind, incompressible)) < 1e-5
+            s = (0.2, 0.3, 0.1)
+            assert rel(host(R.gaussian_smooth(dev(f), s)), osp.gaussian_smooth(f, s)) < 1e-5
+            R.close()
+
+
+def test_inner_product(reg):
+    shape = (20, 28, 44)
+    a = synth.bandlimited(shape, 4, 41)
+    b = synth.bandlimited(shape, 4, 42)
+    R = reg.Registration(shape, 4, 1e-2)
+    got = R.inner(dev(a), dev(b))
+    exp = opr.inner(a.astype(np.float32).astype(float), b.astype(np.float32).astype(float))
+    assert abs(got - exp) < 1e-12 * np.sqrt(opr.inner(a, a) * opr.inner(b, b))
+    R.close()
+
+
+def _problem_case(shape, kind, incompressible, beta, nt, at_vstar):
+    rho_T, rho_R, vs = synth.sinusoid_problem(shape, 0.5)
+    v = vs if at_vstar else 0.3 * synth.bandlimited(shape, 2, 51)
+    if incompressible:
+        v = osp.leray(v)
+    return rho_T, rho_R, v
+
+
+CASES = [
+    ((32, 32, 32), 'H2', False, 1e-2, 4, True),
+    ((32, 32, 32), 'H2', False, 1e-2, 4, False),
+    ((20, 28, 44), 'H2', False, 1e-2, 4, True),
+    ((32, 32, 32), 'H1DIV', True, 1e-3, 4, True),
+    ((20, 28, 44), 'H1', False, 1e-3, 3, False),
+    ((24, 24, 24), 'H2', True, 1e-2, 1, True),      # nt = 1: a single step
+]
+
+
+@pytest.mark.parametrize('shape,kind,incompressible,beta,nt,at_vstar', CASES)
+def test_gradient_and_matvec(reg, shape, kind, incompressible, beta, nt, at_vstar):
+    rho_T, rho_R, v = _problem_case(shape, kind, incompressible, beta, nt, at_vstar)
+    P = opr.Problem(rho_T, rho_R, nt, beta, kind, incompressible)
+    g_ref, J_ref = P.gradient(v)
+    R = reg.Registration(shape, nt, beta, kind, incompressible)
+    R.set_images(dev(rho_T), dev(rho_R))
+    g, J = R.gradient(dev(v))
+    assert rel(host(g), g_ref) < 1e-4
+    assert abs(J - J_ref) < 1e-5 * abs(J_ref)
+    assert abs(R.objective(dev(v)) - J_ref) < 1e-5 * abs(J_ref)
+    for s in range(5):
+        w = synth.bandlimited(shape, 8, 1001 + s)
+        if incompressible:
+            w = osp.leray(w)
+        h = R.hessian_matvec(dev(w))
+        assert rel(host(h), P.hessian_matvec(w)) < 1e-4, s
+    R.close()
+
+
+def test_matvec_before_gradient_is_refused(reg):
+    shape = (16, 16, 16)
+    R = reg.Registration(shape, 4, 1e-2)
+    z = torch.zeros((3,) + shape, device='cuda')
+    with pytest.raises(reg.RegError) as e:
+        R.hessian_matvec(z)
+    assert e.value.status == 5
+    R.close()
+
+
+def test_zero_velocity_closed_form(reg):
+    # H(0) w = beta A w + (w . grad rho_T) grad rho_T; g(0) = (rho_R - rho_T) grad rho_T
+    shape = (20, 28, 44)
+    rho_T = synth.bandlimited(shape, 3, 61, ncomp=None)
+    rho_R = synth.bandlimited(shape, 3, 62, ncomp=None)
+    w = synth.bandlimited(shape, 6, 63)
+    R = reg.Registration(shape, 4, 1e-2)
+    R.set_images(dev(rho_T), dev(rho_R))
+    g, _ = R.gradient(torch.zeros((3,) + shape, device='cuda'))
+    gr = osp.gradient(rho_T)
+    assert rel(host(g), (rho_R - rho_T) * gr) < 1e-5
+    h = host(R.hessian_matvec(dev(w)))
+    exp = 1e-2 * osp.apply_regularisation(w, 'H2') + np.sum(w * gr, 0) * gr
+    assert rel(h, exp) < 1e-5
+    R.close()
+
+
+def test_presmoothing(reg):
+    shape = (32, 32, 32)
+    rho_T, rho_R, vs = synth.sinusoid_problem(shape, 0.5)
+    P = opr.Problem(rho_T, rho_R, 4, 1e-2, 'H2', False, presmooth=True)
+    g_ref, J_ref = P.gradient(vs)
+    R = reg.Registration(shape, 4, 1e-2)
+    R.set_images(dev(rho_T), dev(rho_R), presmooth=True)
+    g, J = R.gradient(dev(vs))
+    assert rel(host(g), g_ref) < 1e-4 and abs(J - J_ref) < 1e-5 * J_ref
+    R.close()
+
+
+def test_three_gauss_newton_steps_match_the_oracle(reg):
+    shape = (32, 32, 32)
+    rho_T, rho_R, _ = synth.sinusoid_problem(shape, 0.5)
+    P = opr.Problem(rho_T, rho_R, 4, 1e-2, 'H2', False)
+    v_ref, st_ref = oso.gauss_newton(P, np.zeros((3,) + shape), gtol=1e-2, max_gn=3)
+    R = reg.Registration(shape, 4, 1e-2)
+    R.set_images(dev(rho_T), dev(rho_R))
+    v = torch.zeros((3,) + shape, device='cuda')
+    status, st = R.solve(v, gtol=1e-2, max_gn=3)
+    assert st['gn_iters'] == st_ref['gn_iters']
+    assert abs(st['J'] - st_ref['J']) < 1e-4 * st_ref['J']
+    assert abs(st['mismatch_rel'] - st_ref['mismatch_rel']) < 1e-3
+    assert rel(host(v), v_ref) < 1e-3
+    assert abs(st['pcg_iters'] - st_ref['pcg_iters']) <= max(1, 0.1 * st_ref['pcg_iters'])
+    R.close()
+
+
+def test_graph_and_eager_pcg_agree(reg):
+    shape = (24, 24, 24)
+    rho_T, rho_R, _ = synth.sinusoid_problem(shape, 0.5)
+    out = []
+    for use_graph in (0, 1):
+        R = reg.Registration(shape, 4, 1e-3)
+        R.set_images(dev(rho_T), dev(rho_R))
+        v = torch.zeros((3,) + shape, device='cuda')
+        _, st = R.solve(v, gtol=1e-2, max_gn=4, use_graph=use_graph)
+        out.append((host(v), st))
+        R.close()
+    assert out[0][1]['pcg_iters'] == out[1][1]['pcg_iters']
+    assert rel(out[1][0], out[0][0]) < 1e-6
