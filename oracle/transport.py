@@ -58,18 +58,20 @@ def adjoint_step(nu, d_adj, divv, dt):
     """One tau-step of -d_t lam - div(v lam) = 0 (Eq. (adjoint)).
 
     In tau = 1 - t this is d_tau lam + (-v) . grad lam = lam div v: transport
-    by -v with the source f(lam, x) = lam(x) div v(x).  With divv None the
+    by -v with the source f(lam, x) = lam div v(x).  With divv None the
     velocity is divergence free and the source vanishes (Sec. III-C2: the
     state and adjoint then need only interpolations).
 
-    Reading: f_0 at the semi-Lagrangian point is the interpolant of the grid
-    product lam * div v, the same pattern as Algorithm 2 uses for its source
-    (f_0 formed on the grid, then interpolated).
+    Eq. (sml-advection) evaluates the source at the semi-Lagrangian point as
+    f_0(X) = f(nu_0(X), X) = nu_0(X) * (div v)(X): the interpolated field times
+    div v interpolated at X (an interpolation "for the f terms that depend on
+    the semi-Lagrangian point").  Then nu_* = nu_0 + dt f_0,
+    f_* = nu_* div v(x), lam_new = nu_0 + dt/2 (f_0 + f_*).
     """
     nu0 = _interp.interp_at_displacement(nu, d_adj)
     if divv is None:
         return nu0
-    f0 = _interp.interp_at_displacement(nu * divv, d_adj)
+    f0 = nu0 * _interp.interp_at_displacement(divv, d_adj)
     nu_star = nu0 + dt * f0
     f_star = nu_star * divv
     return nu0 + (dt / 2.0) * (f0 + f_star)

@@ -110,8 +110,11 @@ def test_spectral_operators(reg, shape):
             assert rel(host(R.spectral_grad(dev(f))), osp.gradient(f)) < 1e-5
             assert rel(host(R.spectral_div(dev(v))), osp.divergence(v)) < 1e-5
             assert rel(host(R.leray(dev(v))), osp.leray(v)) < 1e-5
+            # A amplifies FP32 FFT roundoff that lands in modes outside the
+            # band of v by up to |k|max^4 / |k|band^4 (about 450 for H2 here):
+            # the bound is 1e-7 * 450 ~ 5e-5 relative
             assert rel(host(R.apply_regularisation(dev(v))),
-                       beta * osp.apply_regularisation(v, kind)) < 1e-5
+                       beta * osp.apply_regularisation(v, kind)) < 1e-4
             assert rel(host(R.precond(dev(v))),
                        osp.preconditioner(v, beta, kind, incompressible)) < 1e-5
             s = (0.2, 0.3, 0.1)
