@@ -1,7 +1,7 @@
-// Krylov vector kernels (Sec. III-A): FP64-accumulated inner products with
-// warp-shuffle block reductions, and the fused PCG updates.  Scalars that the
-// PCG recurrence needs (alpha, beta) are read from device memory, so an
-// iteration can be captured in a CUDA graph without host round trips.
+// Physical-space vector kernels (Sec. III-A): FP64-accumulated inner products
+// with warp-shuffle block reductions, their finalisation into device scalars
+// (so a launch sequence can be captured in a CUDA graph without host round
+// trips), and simple vector updates.
 #include "common.cuh"
 
 namespace reg {
@@ -90,53 +90,23 @@ __global__ void k_scale(float* __restrict__ y, float alpha, long long count) {
         y[i] *= alpha;
 }
 
-// x += alpha p; r -= alpha q; partials of r.r.  alpha = sc[ia] / sc[ib].
+// result[k] = scale * sum(partials[k * stride .. k * stride + nblk)), one block per k.
 __global__ void __launch_bounds__(kThreads)
-k_pcg_update(float* __restrict__ x, float* __restrict__ r, const float* __restrict__ p,
-             const float* __restrict__ q, const double* __restrict__ sc, int ia, int ib,
-             long long count, double* partials) {
-    // a non-positive curvature p.Hp leaves the iterate unchanged (the host
-    // then stops the Krylov solve)
-    const double den = sc[ib];
-    const float alpha = den > 0.0 ? (float)(sc[ia] / den) : 0.f;
+k_finalize_multi(const double* __restrict__ partials, int nblk, int stride, double scale,
+                 double* result) {
+    const double* p = partials + (long long)blockIdx.x * stride;
     double acc = 0.0;
-    const long long stride = (long long)gridDim.x * kThreads;
-    const long long tid = (long long)blockIdx.x * kThreads + threadIdx.x;
-    if ((count & 3) == 0) {
-        float4* x4 = reinterpret_cast<float4*>(x);
-        float4* r4 = reinterpret_cast<float4*>(r);
-        const float4* p4 = reinterpret_cast<const float4*>(p);
-        const float4* q4 = reinterpret_cast<const float4*>(q);
-        for (long long i = tid; i < (count >> 2); i += stride) {
-            float4 xv = x4[i], rv = r4[i];
-            const float4 pv = p4[i], qv = q4[i];
-            xv.x = fmaf(alpha, pv.x, xv.x); xv.y = fmaf(alpha, pv.y, xv.y);
-            xv.z = fmaf(alpha, pv.z, xv.z); xv.w = fmaf(alpha, pv.w, xv.w);
-            rv.x = fmaf(-alpha, qv.x, rv.x); rv.y = fmaf(-alpha, qv.y, rv.y);
-            rv.z = fmaf(-alpha, qv.z, rv.z); rv.w = fmaf(-alpha, qv.w, rv.w);
-            x4[i] = xv; r4[i] = rv;
-            acc += (double)rv.x * rv.x + (double)rv.y * rv.y + (double)rv.z * rv.z +
-                   (double)rv.w * rv.w;
-        }
-    } else {
-        for (long long i = tid; i < count; i += stride) {
-            x[i] = fmaf(alpha, p[i], x[i]);
-            const float rv = fmaf(-alpha, q[i], r[i]);
-            r[i] = rv;
-            acc += (double)rv * rv;
-        }
+    for (int i = threadIdx.x; i < nblk; i += kThreads) acc += p[i];
+    __shared__ double red[kThreads / 32];
+    acc = warp_sum(acc);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) s += red[i];
+        result[blockIdx.x] = s * scale;
     }
-    block_store(acc, partials);
-}
-
-// p = z + beta p, beta = sc[ia] / sc[ib].
-__global__ void k_pcg_direction(float* __restrict__ p, const float* __restrict__ z,
-                                const double* __restrict__ sc, int ia, int ib, long long count) {
-    const double den = sc[ib];
-    const float beta = den != 0.0 ? (float)(sc[ia] / den) : 0.f;
-    const long long stride = (long long)gridDim.x * kThreads;
-    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < count; i += stride)
-        p[i] = fmaf(beta, p[i], z[i]);
 }
 
 inline int grid_for(long long count) {
@@ -178,16 +148,9 @@ cudaError_t launch_scale(float* y, float alpha, long long count, cudaStream_t st
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_update(float* x, float* r, const float* p, const float* q,
-                              const double* sc, int ia, int ib, long long count,
-                              double* partials, int nblk, cudaStream_t st) {
-    k_pcg_update<<<nblk, kThreads, 0, st>>>(x, r, p, q, sc, ia, ib, count, partials);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_pcg_direction(float* p, const float* z, const double* sc, int ia, int ib,
-                                 long long count, cudaStream_t st) {
-    k_pcg_direction<<<grid_for(count), kThreads, 0, st>>>(p, z, sc, ia, ib, count);
+cudaError_t launch_finalize_multi(const double* partials, int nblk, int stride, int count,
+                                  double scale, double* result, cudaStream_t st) {
+    k_finalize_multi<<<count, kThreads, 0, st>>>(partials, nblk, stride, scale, result);
     return cudaGetLastError();
 }
 

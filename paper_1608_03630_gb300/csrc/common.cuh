@@ -93,57 +93,6 @@ __device__ __forceinline__ float gather1(const Stencil& s, const float* __restri
     return acc;
 }
 
-// Interleaved pair (x, y): returns (sum w x, sum w y).
-__device__ __forceinline__ float2 gather2(const Stencil& s, const float2* __restrict__ f) {
-    float ax = 0.f, ay = 0.f;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        float bx = 0.f, by = 0.f;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const float2* row = f + s.o1[a] + s.o2[b];
-            float rx = 0.f, ry = 0.f;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float2 v = __ldg(row + s.o3[c]);
-                rx = fmaf(s.w3[c], v.x, rx);
-                ry = fmaf(s.w3[c], v.y, ry);
-            }
-            bx = fmaf(s.w2[b], rx, bx);
-            by = fmaf(s.w2[b], ry, by);
-        }
-        ax = fmaf(s.w1[a], bx, ax);
-        ay = fmaf(s.w1[a], by, ay);
-    }
-    return make_float2(ax, ay);
-}
-
-// Interleaved pair (x, y): returns (sum w x, sum w x*y) -- the transported
-// field and its product with a grid factor (lam and lam * div v).
-__device__ __forceinline__ float2 gather2_prod(const Stencil& s, const float2* __restrict__ f) {
-    float ax = 0.f, ay = 0.f;
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        float bx = 0.f, by = 0.f;
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const float2* row = f + s.o1[a] + s.o2[b];
-            float rx = 0.f, ry = 0.f;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float2 v = __ldg(row + s.o3[c]);
-                rx = fmaf(s.w3[c], v.x, rx);
-                ry = fmaf(s.w3[c], v.x * v.y, ry);
-            }
-            bx = fmaf(s.w2[b], rx, bx);
-            by = fmaf(s.w2[b], ry, by);
-        }
-        ax = fmaf(s.w1[a], bx, ax);
-        ay = fmaf(s.w1[a], by, ay);
-    }
-    return make_float2(ax, ay);
-}
-
 // Decompose a point index into (i1, i2, i3).
 __device__ __forceinline__ void unflatten(const Dims& g, int idx, int& i1, int& i2, int& i3) {
     i1 = idx / g.n23;
@@ -154,64 +103,61 @@ __device__ __forceinline__ void unflatten(const Dims& g, int idx, int& i1, int& 
 
 // ------------------------------------------------------------ launchers
 
+// Tile of the x1-marching interpolation kernels: a block is 32 (x3) x wy (x2)
+// threads and each thread walks k consecutive points along x1.
+struct Tile {
+    int k;    // points per thread along x1 (multiple of 4)
+    int wy;   // threads per block along x2 (1, 2, 4 or 8)
+};
+
 // transport.cu
 cudaError_t launch_departure(const Dims& g, const float* v, float dt, float* d_fwd,
                              float* d_adj, cudaStream_t st);
-cudaError_t launch_interp(const Dims& g, const float* field, int nfields, const float* disp,
-                          float* out, cudaStream_t st);
-// rho_out = I[rho_in](x + d).  With rho_R != nullptr (final step) also writes
-// the adjoint initial value lam = rho_R - rho_out into lam_out (float2 with
-// divv when divv != nullptr, plain float otherwise; lam_out may be nullptr)
-// and per-block FP64 partial sums of (rho_out - rho_R)^2 into partials.
-cudaError_t launch_state_step(const Dims& g, const float* rho_in, const float* d,
-                              float* rho_out, const float* rho_R, const float* divv,
-                              void* lam_out, double* partials, int nblk_partials,
+// out = I[f](x + d) for one scalar field.
+cudaError_t launch_interp(const Dims& g, Tile t, const float* f, const float* d, float* out,
+                          cudaStream_t st);
+// State step rho_out = I[rho_in](x + d).  With rho_R != nullptr (last step)
+// also lam_out = rho_R - rho_out (if lam_out != nullptr) and per-block FP64
+// partial sums of (rho_out - rho_R)^2 into partials[0 .. nblocks).
+cudaError_t launch_state_step(const Dims& g, Tile t, const float* rho_in, const float* d,
+                              float* rho_out, const float* rho_R, float* lam_out,
+                              double* partials, int max_partials, int* nblk_out,
                               cudaStream_t st);
-// Adjoint / incremental adjoint tau-step with b accumulation.
-struct AdjointStepArgs {
-    const void* lam_in;        // float2 (lam, divv) if compressible else float
-    void* lam_out;
-    const float* d;            // semi-Lagrangian points of -v, [3n]
-    const float* grad_j;       // grad rho(t_j), [3n]  (fp32 or bf16, see below)
-    const float* grad_j1;      // grad rho(t_{j+1}) (first step only)
-    const __nv_bfloat16* grad_j_bf;
-    const __nv_bfloat16* grad_j1_bf;
-    float* b;                  // [3n] accumulator
-    float w_j, w_j1, dt;
-    int compressible, first;
-};
-cudaError_t launch_adjoint_step(const Dims& g, const AdjointStepArgs& a, cudaStream_t st);
-// Incremental state step: in = (rho~_j, f_j) float2; writes (rho~_{j+1}, f_{j+1})
-// or, when final, the incremental-adjoint initial value -rho~_nt (float2 with
-// divv when compressible, else float) into out.
-struct IncStateStepArgs {
-    const float2* in;
-    void* out;
-    const float* d;            // semi-Lagrangian points of v
-    const float* vt;           // [3n]
-    const float* grad_j1;      // grad rho(t_{j+1}) [3n]
-    const __nv_bfloat16* grad_j1_bf;
-    const float* divv;         // final step, compressible only
-    float dt;
-    int final_step, compressible;
-};
-cudaError_t launch_incstate_step(const Dims& g, const IncStateStepArgs& a, cudaStream_t st);
-// out = (0, -vt . grad rho(t_0)).
+// Adjoint / incremental-adjoint tau-step lam_out = c(x) I[lam_in](x + d)
+// (c == nullptr: divergence-free velocity, c = 1).
+cudaError_t launch_adjoint_step(const Dims& g, Tile t, const float* lam_in, const float* d,
+                                const float* c, float* lam_out, cudaStream_t st);
+// c(x) = 1 + dt/2 (dX + dv + dt dX dv), dv = div v(x), dX = I[div v](x + d_adj).
+cudaError_t launch_adjoint_coef(const Dims& g, Tile t, const float* divv, const float* d_adj,
+                                float dt, float* c, cudaStream_t st);
+// Incremental state, carried as u_j = rho~_j + dt/2 f_j, f = -v~ . grad rho(t_j):
+//   u_{j+1} = I[u_j](x + d) + dt f_{j+1}(x);  final step writes
+//   lam~(1) = -(I[u_{nt-1}](x + d) + dt/2 f_nt(x)) instead.
+// grad_j1 is grad rho(t_{j+1}) (fp32, or bf16 when grad_bf != nullptr).
+cudaError_t launch_incstate_step(const Dims& g, Tile t, const float* u_in, const float* d,
+                                 const float* vt, const float* grad_j1,
+                                 const __nv_bfloat16* grad_j1_bf, float dt, int final_step,
+                                 float* out, cudaStream_t st);
+// u_0 = -dt/2 v~ . grad rho(t_0)
 cudaError_t launch_incstate_init(const Dims& g, const float* vt, const float* grad0,
-                                 const __nv_bfloat16* grad0_bf, float2* out,
+                                 const __nv_bfloat16* grad0_bf, float dt, float* u0,
                                  cudaStream_t st);
-// Pack (lam, divv): out[i] = (lam[i], divv[i]).
-cudaError_t launch_pack2(const Dims& g, const float* lam, const float* divv, float2* out,
-                         cudaStream_t st);
+// out[c] = base[c] + sum_j w_j lam_j grad_j[c]  (trapezoid weights, base may be
+// null); with dotp != nullptr also per-block partials of <dotp, out>.
+cudaError_t launch_time_integral(const Dims& g, int nt, const float* lam, const float* grad,
+                                 const __nv_bfloat16* grad_bf, const float* base, float* out,
+                                 const float* dotp, double* partials, int nblk,
+                                 cudaStream_t st);
 // Deformation displacement step: u_{j+1} = I[u_j](X) + dt/2 (I[-v](X) - v(x)).
 cudaError_t launch_deformation_step(const Dims& g, const float* u_in, const float* v,
                                     const float* d, float dt, float* u_out,
                                     cudaStream_t st);
-// float -> bfloat16 copy (count elements).
+// float <-> bfloat16 copies (count elements).
 cudaError_t launch_to_bf16(const float* in, __nv_bfloat16* out, long long count,
                            cudaStream_t st);
 cudaError_t launch_from_bf16(const __nv_bfloat16* in, float* out, long long count,
                              cudaStream_t st);
+int march_blocks(const Dims& g, Tile t);   // blocks of one marching launch
 
 // spectral.cu -- multipliers on the half spectrum (cufftComplex = float2).
 // All scale by 1/n (the unnormalised inverse FFT).
@@ -238,26 +184,44 @@ cudaError_t launch_spectral(const Dims& g, SpecOp op, const SpecArgs& a, cudaStr
 // (Hermitian weights on the half spectrum).
 cudaError_t launch_spec_energy(const Dims& g, const float2* v, int kind, double* partials,
                                int nblk, cudaStream_t st);
+// Spectral Krylov kernels (normalised half-spectrum coefficients, 3 fields).
+// Partials: slot t of block b at partials[t * nblk + b].
+cudaError_t launch_sp_init(const Dims& g, const float2* gh, float2* r, float2* s, float2* p,
+                           float2* pc, double beta, int kind, int project, double* partials,
+                           int nblk, cudaStream_t st);
+cudaError_t launch_sp_update(const Dims& g, float2* s, float2* r, const float2* p,
+                             const float2* B, double* sc, int irz, int ipap, int ipb, int ipq,
+                             double beta, int kind, int project, double* partials, int nblk,
+                             cudaStream_t st);
+cudaError_t launch_sp_direction(const Dims& g, const float2* r, float2* p, float2* pc,
+                                const double* sc, int irznew, int irz, int zero_beta,
+                                double beta, int kind, int project, double* partials, int nblk,
+                                cudaStream_t st);
+cudaError_t launch_sp_gradient(const Dims& g, const float2* v, const float2* B, float2* gout,
+                               double beta, int kind, int project, double* partials, int nblk,
+                               cudaStream_t st);
+cudaError_t launch_sp_axpy(const Dims& g, float2* out, float2* copy, const float2* x,
+                           const float2* y, float a, int kind, int project, double* partials,
+                           int nblk, cudaStream_t st);
+cudaError_t launch_sp_dot(const Dims& g, const float2* a, const float2* b, double* partials,
+                          int nblk, cudaStream_t st);
+cudaError_t launch_sp_normalise(const Dims& g, const float2* in, float2* out, int project,
+                                cudaStream_t st);
 
 // blas.cu
 int blas_blocks();   // number of partial-sum blocks used by reductions
 cudaError_t launch_dot_partials(const float* a, const float* b, long long count,
                                 double* partials, int nblk, cudaStream_t st);
-// result[0] = scale * sum(partials[0..nblk)); also flags non-finite values.
+// result[0] = scale * sum(partials[0..nblk)).
 cudaError_t launch_finalize(const double* partials, int nblk, double scale, double* result,
                             cudaStream_t st);
-// PCG pieces; scalars live in device memory (sc[]), see solver.
 cudaError_t launch_axpy(float* y, const float* x, float alpha, long long count,
                         cudaStream_t st);           // y += alpha x
 cudaError_t launch_axpby_out(float* out, const float* x, const float* y, float a, float b,
                              long long count, cudaStream_t st);   // out = a x + b y
-// x += alpha p; r -= alpha q; partials of r.r   (alpha = sc[ia] / sc[ib])
-cudaError_t launch_pcg_update(float* x, float* r, const float* p, const float* q,
-                              const double* sc, int ia, int ib, long long count,
-                              double* partials, int nblk, cudaStream_t st);
-// p = z + beta p, beta = sc[ia] / sc[ib]
-cudaError_t launch_pcg_direction(float* p, const float* z, const double* sc, int ia, int ib,
-                                 long long count, cudaStream_t st);
+// result[k] = scale * sum(partials[k * stride .. k * stride + nblk)) for k < count
+cudaError_t launch_finalize_multi(const double* partials, int nblk, int stride, int count,
+                                  double scale, double* result, cudaStream_t st);
 cudaError_t launch_scale(float* y, float alpha, long long count, cudaStream_t st);
 
 }  // namespace reg

@@ -186,19 +186,17 @@ static const float* grad_level(reg_ctx* c, int j) {
 static const __nv_bfloat16* grad_level_bf(reg_ctx* c, int j) {
     return c->grad_hist_bf ? c->grad_hist_bf + (long long)j * 3 * c->g.n : nullptr;
 }
+static double grad_bytes(reg_ctx* c) { return c->grad_hist_bf ? 6.0 : 12.0; }
 
-static double trap_w(int j, int nt) {
-    return (j == 0 || j == nt) ? 0.5 / nt : 1.0 / nt;
-}
-
-// Forward state solve into rho_hist (or into two ping-pong buffers when
-// hist == false); the last step forms lam(1) in buf[out_buf] and the mismatch.
+// Forward state solve (Eq. varopt:state).  keep_hist: all levels in hist
+// [(nt+1) n]; otherwise hist holds two ping-pong levels.  The last step
+// writes lam(1) = rho_R - rho(1) to lam_out (if not null) and the mismatch
+// 1/2 ||rho(1) - rho_R||^2_h to dsc[SC_JMIS].
 static int state_solve(reg_ctx* c, const float* d_fwd, float* hist, bool keep_hist,
-                       void* lam_out, const float* divv) {
+                       float* lam_out) {
     const Dims& g = c->g;
     const long long n = g.n;
     const int nt = c->nt;
-    // rho(t_0) = rho_T
     if (c->precision == REG_MIXED_BF16 && c->img_bf) {
         Phase p(c, REG_PH_OTHER, 6.0 * n);
         REG_CK(c, launch_from_bf16(c->img_bf, hist, n, c->stream));
@@ -206,27 +204,25 @@ static int state_solve(reg_ctx* c, const float* d_fwd, float* hist, bool keep_hi
         REG_CK(c, cudaMemcpyAsync(hist, c->rho_T, sizeof(float) * n, cudaMemcpyDeviceToDevice,
                                   c->stream));
     }
-    const int nb = (g.n + 255) / 256;
+    int nb = 0;
     for (int j = 0; j < nt; ++j) {
         const float* in = keep_hist ? hist + j * n : hist + (j & 1) * n;
         float* out = keep_hist ? hist + (j + 1) * n : hist + ((j + 1) & 1) * n;
         const bool fin = (j == nt - 1);
         double bytes = 20.0 * n;
-        if (fin) bytes += (4.0 + (lam_out ? (divv ? 12.0 : 4.0) : 0.0)) * n;
+        if (fin) bytes += (lam_out ? 8.0 : 4.0) * n;
         Phase p(c, REG_PH_STATE, bytes);
-        REG_CK(c, launch_state_step(g, in, d_fwd, out, fin ? c->rho_R : nullptr,
-                                    fin ? divv : nullptr, fin ? lam_out : nullptr,
-                                    c->partials, c->npartials, c->stream));
+        REG_CK(c, launch_state_step(g, c->tile, in, d_fwd, out, fin ? c->rho_R : nullptr,
+                                    fin ? lam_out : nullptr, c->partials, c->npartials, &nb,
+                                    c->stream));
     }
-    {
-        Phase p(c, REG_PH_BLAS, 0.0);
-        REG_CK(c, launch_finalize(c->partials, nb, 0.5 * kTwoPi * kTwoPi * kTwoPi / n,
-                                  c->dsc + SC_JMIS, c->stream));
-    }
+    Phase p(c, REG_PH_BLAS, 0.0);
+    REG_CK(c, launch_finalize(c->partials, nb, 0.5 * kTwoPi * kTwoPi * kTwoPi / n,
+                              c->dsc + SC_JMIS, c->stream));
     return REG_OK;
 }
 
-// dsc[SC_JREG] = beta/2 <v, A v>_h from the spectrum of v in spec (3 fields).
+// dsc[SC_JREG] = beta/2 <v, A v>_h from the spectrum of v (3 fields).
 static int reg_energy(reg_ctx* c, const float2* vhat) {
     const int nb = blas_blocks();
     {
@@ -240,27 +236,67 @@ static int reg_energy(reg_ctx* c, const float2* vhat) {
     return REG_OK;
 }
 
-int op_objective(reg_ctx* c, const float* v, int slot_J) {
-    (void)slot_J;
+int op_mismatch(reg_ctx* c, const float* v) {
     // scratch only: the linearisation point stays intact
     REG_TRY(op_departure(c, v, c->tmp3, nullptr));
     float* ping = reinterpret_cast<float*>(c->buf[0]);   // 2n floats: two levels
-    REG_TRY(state_solve(c, c->tmp3, ping, false, nullptr, nullptr));
+    return state_solve(c, c->tmp3, ping, false, nullptr);
+}
+
+int op_objective(reg_ctx* c, const float* v, int slot_J) {
+    (void)slot_J;
+    REG_TRY(op_mismatch(c, v));
     REG_TRY(op_fft_r2c(c, v, c->spec[0], 3));
     return reg_energy(c, c->spec[0]);
 }
 
-int op_gradient(reg_ctx* c, const float* v, float* gout, int slot_J) {
-    (void)slot_J;
+// Adjoint (or incremental adjoint) from lam_hist[nt] down to lam_hist[0].
+static int adjoint_solve(reg_ctx* c, int phase) {
+    const long long n = c->g.n;
+    const bool comp = !c->incompressible;
+    for (int j = c->nt - 1; j >= 0; --j) {
+        Phase p(c, phase, (comp ? 24.0 : 20.0) * n);
+        REG_CK(c, launch_adjoint_step(c->g, c->tile, c->lam_hist + (j + 1) * n, c->d_adj,
+                                      comp ? c->coef : nullptr, c->lam_hist + j * n, c->stream));
+    }
+    return REG_OK;
+}
+
+// out = base + sum_j w_j lam_j grad rho_j; dsc[slot] = <dotp, out>_h if dotp.
+int op_time_integral(reg_ctx* c, const float* base, float* out, const float* dotp, int slot) {
+    const long long n = c->g.n;
+    const int nb = blas_blocks();
+    {
+        double bytes = (c->nt + 1) * (4.0 + grad_bytes(c)) * n + 12.0 * n;
+        if (base) bytes += 12.0 * n;
+        if (dotp) bytes += 12.0 * n;
+        Phase p(c, REG_PH_OTHER, bytes);
+        REG_CK(c, launch_time_integral(c->g, c->nt, c->lam_hist, c->grad_hist, c->grad_hist_bf,
+                                       base, out, dotp, c->partials, nb, c->stream));
+    }
+    if (dotp) {
+        Phase p(c, REG_PH_BLAS, 0.0);
+        REG_CK(c, launch_finalize(c->partials, nb, kTwoPi * kTwoPi * kTwoPi / n, c->dsc + slot,
+                                  c->stream));
+    }
+    return REG_OK;
+}
+
+int op_linearize(reg_ctx* c, const float* v) {
     const Dims& g = c->g;
     const long long n = g.n;
     const int nt = c->nt;
     const bool comp = !c->incompressible;
     c->have_lin = false;
     REG_TRY(op_departure(c, v, c->d_fwd, c->d_adj));
-    if (comp) REG_TRY(op_div(c, v, c->divv));
-    // state history and lam(1) = rho_R - rho(1) in buf[0]
-    REG_TRY(state_solve(c, c->d_fwd, c->rho_hist, true, c->buf[0], comp ? c->divv : nullptr));
+    if (comp) {
+        REG_TRY(op_div(c, v, c->divv));
+        Phase p(c, REG_PH_ADJOINT, 20.0 * n);
+        REG_CK(c, launch_adjoint_coef(g, c->tile, c->divv, c->d_adj, (float)(1.0 / nt), c->coef,
+                                      c->stream));
+    }
+    // state history; lam(1) = rho_R - rho(1) into lam_hist[nt]
+    REG_TRY(state_solve(c, c->d_fwd, c->rho_hist, true, c->lam_hist + nt * n));
     // spectral gradients of every level (cached for the matvecs)
     for (int j = 0; j <= nt; ++j) {
         if (c->grad_hist_bf) {
@@ -272,30 +308,16 @@ int op_gradient(reg_ctx* c, const float* v, float* gout, int slot_J) {
             REG_TRY(op_grad(c, c->rho_hist + j * n, c->grad_hist + (long long)j * 3 * n));
         }
     }
-    // adjoint backward in time with b accumulation
-    for (int j = nt - 1; j >= 0; --j) {
-        const int k = nt - 1 - j;
-        AdjointStepArgs a;
-        memset(&a, 0, sizeof a);
-        a.lam_in = c->buf[k & 1];
-        a.lam_out = c->buf[(k + 1) & 1];
-        a.d = c->d_adj;
-        a.grad_j = grad_level(c, j);
-        a.grad_j1 = grad_level(c, j + 1);
-        a.grad_j_bf = grad_level_bf(c, j);
-        a.grad_j1_bf = grad_level_bf(c, j + 1);
-        a.b = c->bacc;
-        a.w_j = (float)trap_w(j, nt);
-        a.w_j1 = (float)trap_w(j + 1, nt);
-        a.dt = (float)(1.0 / nt);
-        a.compressible = comp;
-        a.first = (j == nt - 1);
-        const double gb = c->grad_hist_bf ? 6.0 : 12.0;
-        double bytes = (12.0 + (comp ? 16.0 : 8.0) + gb + 24.0) * n;
-        if (a.first) bytes += gb * n - 12.0 * n;
-        Phase p(c, REG_PH_ADJOINT, bytes);
-        REG_CK(c, launch_adjoint_step(g, a, c->stream));
-    }
+    REG_TRY(adjoint_solve(c, REG_PH_ADJOINT));
+    REG_TRY(op_time_integral(c, nullptr, c->bacc, nullptr, 0));
+    c->have_lin = true;
+    return REG_OK;
+}
+
+int op_gradient(reg_ctx* c, const float* v, float* gout, int slot_J) {
+    (void)slot_J;
+    REG_TRY(op_linearize(c, v));
+    c->have_lin = false;
     // g = beta A v + P b
     REG_TRY(op_fft_r2c(c, v, c->spec[0], 3));
     REG_TRY(reg_energy(c, c->spec[0]));
@@ -310,57 +332,31 @@ int op_gradient(reg_ctx* c, const float* v, float* gout, int slot_J) {
     return REG_OK;
 }
 
-int op_matvec(reg_ctx* c, const float* vt, float* out) {
+int op_matvec_transport(reg_ctx* c, const float* vt) {
     const Dims& g = c->g;
     const long long n = g.n;
     const int nt = c->nt;
-    const bool comp = !c->incompressible;
-    const double gb = c->grad_hist_bf ? 6.0 : 12.0;
+    const float dt = (float)(1.0 / nt);
+    const double gb = grad_bytes(c);
+    float* u[2] = {reinterpret_cast<float*>(c->buf[0]), reinterpret_cast<float*>(c->buf[1])};
     {
-        Phase p(c, REG_PH_INCSTATE, (12.0 + gb + 8.0) * n);
-        REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), grad_level_bf(c, 0), c->buf[0],
+        Phase p(c, REG_PH_INCSTATE, (16.0 + gb) * n);
+        REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), grad_level_bf(c, 0), dt, u[0],
                                        c->stream));
     }
     for (int j = 0; j < nt; ++j) {
-        IncStateStepArgs a;
-        memset(&a, 0, sizeof a);
-        a.in = c->buf[j & 1];
-        a.out = c->buf[(j + 1) & 1];
-        a.d = c->d_fwd;
-        a.vt = vt;
-        a.grad_j1 = grad_level(c, j + 1);
-        a.grad_j1_bf = grad_level_bf(c, j + 1);
-        a.divv = c->divv;
-        a.dt = (float)(1.0 / nt);
-        a.final_step = (j == nt - 1);
-        a.compressible = comp;
-        double bytes = (12.0 + 8.0 + 12.0 + gb + 8.0) * n;
-        if (a.final_step) bytes += (comp ? 4.0 : -4.0) * n;
-        Phase p(c, REG_PH_INCSTATE, bytes);
-        REG_CK(c, launch_incstate_step(g, a, c->stream));
+        const bool fin = (j == nt - 1);
+        Phase p(c, REG_PH_INCSTATE, (32.0 + gb) * n);
+        REG_CK(c, launch_incstate_step(g, c->tile, u[j & 1], c->d_fwd, vt, grad_level(c, j + 1),
+                                       grad_level_bf(c, j + 1), dt, fin ? 1 : 0,
+                                       fin ? c->lam_hist + nt * n : u[(j + 1) & 1], c->stream));
     }
-    for (int j = nt - 1; j >= 0; --j) {
-        const int k = nt - 1 - j;
-        AdjointStepArgs a;
-        memset(&a, 0, sizeof a);
-        a.lam_in = c->buf[(nt + k) & 1];
-        a.lam_out = c->buf[(nt + k + 1) & 1];
-        a.d = c->d_adj;
-        a.grad_j = grad_level(c, j);
-        a.grad_j1 = grad_level(c, j + 1);
-        a.grad_j_bf = grad_level_bf(c, j);
-        a.grad_j1_bf = grad_level_bf(c, j + 1);
-        a.b = c->bacc;
-        a.w_j = (float)trap_w(j, nt);
-        a.w_j1 = (float)trap_w(j + 1, nt);
-        a.dt = (float)(1.0 / nt);
-        a.compressible = comp;
-        a.first = (j == nt - 1);
-        double bytes = (12.0 + (comp ? 16.0 : 8.0) + gb + 24.0) * n;
-        if (a.first) bytes += gb * n - 12.0 * n;
-        Phase p(c, REG_PH_INCADJ, bytes);
-        REG_CK(c, launch_adjoint_step(g, a, c->stream));
-    }
+    return adjoint_solve(c, REG_PH_INCADJ);
+}
+
+int op_matvec(reg_ctx* c, const float* vt, float* out) {
+    REG_TRY(op_matvec_transport(c, vt));
+    REG_TRY(op_time_integral(c, nullptr, c->bacc, nullptr, 0));
     REG_TRY(op_fft_r2c(c, vt, c->spec[0], 3));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
     SpecArgs a = spec_args(c);
@@ -382,14 +378,16 @@ int op_precond(reg_ctx* c, const float* r, float* z) {
 
 int ensure_solver(reg_ctx* c) {
     if (c->have_solver) return REG_OK;
-    const size_t bytes = sizeof(float) * 3 * (size_t)c->g.n;
-    for (int i = 0; i < 8; ++i) {
-        cudaError_t e = cudaMalloc(&c->sv[i], bytes);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            for (int k = 0; k < i; ++k) { cudaFree(c->sv[k]); c->sv[k] = nullptr; }
-            return fail(c, REG_ENOMEM, "cannot allocate solver vectors");
-        }
+    const size_t rb = sizeof(float) * 3 * (size_t)c->g.n;
+    const size_t sb = sizeof(float2) * 3 * (size_t)c->g.nc;
+    bool ok = true;
+    for (int i = 0; i < 4 && ok; ++i) ok = cudaMalloc(&c->sv[i], rb) == cudaSuccess;
+    for (int i = 0; i < 8 && ok; ++i) ok = cudaMalloc(&c->ss[i], sb) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        for (int i = 0; i < 4; ++i) { if (c->sv[i]) cudaFree(c->sv[i]); c->sv[i] = nullptr; }
+        for (int i = 0; i < 8; ++i) { if (c->ss[i]) cudaFree(c->ss[i]); c->ss[i] = nullptr; }
+        return fail(c, REG_ENOMEM, "cannot allocate solver vectors");
     }
     c->have_solver = true;
     return REG_OK;
@@ -419,12 +417,14 @@ static void free_ctx(reg_ctx* c) {
     for (int i = 0; i < 4; ++i)
         if (c->plans[i]) cufftDestroy(i == 0 ? c->r2c1 : i == 1 ? c->c2r1 : i == 2 ? c->r2c3 : c->c2r3);
     void* ptrs[] = {c->rho_T, c->rho_R, c->img_bf, c->d_fwd, c->d_adj, c->divv, c->rho_hist,
-                    c->grad_hist, c->grad_hist_bf, c->buf[0], c->buf[1], c->bacc, c->tmp3,
-                    c->spec[0], c->spec[1], c->partials, c->dsc};
+                    c->grad_hist, c->grad_hist_bf, c->lam_hist, c->coef, c->buf[0], c->buf[1],
+                    c->bacc, c->tmp3, c->spec[0], c->spec[1], c->partials, c->dsc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 4; ++i)
         if (c->sv[i]) cudaFree(c->sv[i]);
+    for (int i = 0; i < 8; ++i)
+        if (c->ss[i]) cudaFree(c->ss[i]);
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
@@ -473,8 +473,12 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
     c->stream = nullptr;
     const long long n = c->g.n;
     const long long nc = c->g.nc;
-    c->npartials = (int)((n + 255) / 256);
-    if (c->npartials < blas_blocks()) c->npartials = blas_blocks();
+    c->tile.k = 8;
+    c->tile.wy = 4;
+    // partial sums: the largest marching grid (k = 4, wy = 1), or up to
+    // kMaxSlots partial-sum slots of the BLAS / spectral grid
+    c->npartials = march_blocks(c->g, Tile{4, 1});
+    if (c->npartials < kMaxSlots * blas_blocks()) c->npartials = kMaxSlots * blas_blocks();
     struct A { void** p; size_t bytes; } allocs[] = {
         {(void**)&c->rho_T, sizeof(float) * n},
         {(void**)&c->rho_R, sizeof(float) * n},
@@ -482,6 +486,8 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
         {(void**)&c->d_adj, sizeof(float) * 3 * n},
         {(void**)&c->divv, sizeof(float) * n},
         {(void**)&c->rho_hist, sizeof(float) * (nt + 1) * n},
+        {(void**)&c->lam_hist, sizeof(float) * (nt + 1) * n},
+        {(void**)&c->coef, sizeof(float) * n},
         {(void**)&c->buf[0], sizeof(float2) * n},
         {(void**)&c->buf[1], sizeof(float2) * n},
         {(void**)&c->bacc, sizeof(float) * 3 * n},
@@ -680,8 +686,11 @@ int reg_interp(reg_ctx* c, const float* field, int nfields, const float* disp, f
     CHECK_PTR(c, disp);
     CHECK_PTR(c, out);
     if (nfields < 1 || nfields > 3) return fail(c, REG_EINVAL, "nfields must be 1..3");
-    Phase p(c, REG_PH_INTERP, (double)c->g.n * (12.0 + 8.0 * nfields));
-    REG_CK(c, launch_interp(c->g, field, nfields, disp, out, c->stream));
+    const long long n = c->g.n;
+    for (int k = 0; k < nfields; ++k) {
+        Phase p(c, REG_PH_INTERP, 20.0 * n);
+        REG_CK(c, launch_interp(c->g, c->tile, field + k * n, disp, out + k * n, c->stream));
+    }
     return REG_OK;
 }
 
@@ -695,8 +704,9 @@ int reg_state_transport(reg_ctx* c, const float* rho0, const float* d_fwd, float
                               c->stream));
     for (int j = 0; j < c->nt; ++j) {
         Phase p(c, REG_PH_STATE, 20.0 * n);
-        REG_CK(c, launch_state_step(c->g, rho_hist + j * n, d_fwd, rho_hist + (j + 1) * n,
-                                    nullptr, nullptr, nullptr, nullptr, 0, c->stream));
+        REG_CK(c, launch_state_step(c->g, c->tile, rho_hist + j * n, d_fwd,
+                                    rho_hist + (j + 1) * n, nullptr, nullptr, nullptr, 0, nullptr,
+                                    c->stream));
     }
     return REG_OK;
 }
@@ -758,6 +768,22 @@ int reg_inner(reg_ctx* c, const float* a, const float* b, size_t count, double* 
     REG_TRY(read_scalars(c, SC_INNER, 1));
     *out = c->hsc[SC_INNER];
     if (!std::isfinite(*out)) return fail(c, REG_ENONFINITE, "inner product is not finite");
+    return REG_OK;
+}
+
+int reg_set_tile(reg_ctx* c, int k, int wy) {
+    CHECK_CTX(c);
+    if (k < 4 || k > 64 || (k & 3) || !(wy == 1 || wy == 2 || wy == 4 || wy == 8))
+        return fail(c, REG_EINVAL, "tile: k must be a multiple of 4 in [4, 64], wy in {1,2,4,8}");
+    c->tile.k = k;
+    c->tile.wy = wy;
+    return REG_OK;
+}
+
+int reg_get_tile(const reg_ctx* c, int* k, int* wy) {
+    if (!c || !k || !wy) return REG_EINVAL;
+    *k = c->tile.k;
+    *wy = c->tile.wy;
     return REG_OK;
 }
 

@@ -40,17 +40,21 @@ struct reg_ctx {
     __nv_bfloat16* grad_hist_bf;  // [(nt+1) 3n] (mixed precision)
 
     // scratch
-    float2* buf[2];      // [n] float2 each: transport ping-pong
-    float* bacc;         // [3n] b / b~ accumulator
+    float* lam_hist;     // [(nt+1) n] adjoint / incremental-adjoint levels
+    float* coef;         // [n] adjoint step factor c(x) (compressible)
+    float2* buf[2];      // [n] float2 each (2n floats): ping-pong scratch
+    float* bacc;         // [3n] b / b~
     float* tmp3;         // [3n] real scratch
     float2* spec[2];     // [3 nc] complex scratch each
     double* partials;    // FP64 partial sums
     int npartials;
     double* dsc;         // device scalars [32]
     double* hsc;         // pinned host mirror [32]
+    reg::Tile tile;      // tile of the x1-marching kernels
 
-    // solver vectors [3n] each
-    float* sv[8];
+    // solver vectors: real [3n] each, spectral [3 nc] each
+    float* sv[4];
+    float2* ss[8];
     bool have_solver;
 
     // timing
@@ -62,6 +66,10 @@ struct reg_ctx {
 };
 
 namespace reg {
+
+// Largest number of partial-sum slots one reduction kernel writes (each slot
+// holds blas_blocks() doubles); the partials buffer is sized for it.
+constexpr int kMaxSlots = 4;
 
 int fail(reg_ctx* c, int status, const std::string& msg);
 int fail_cuda(reg_ctx* c, cudaError_t e, const char* what, int line);
@@ -90,9 +98,17 @@ int op_spectral(reg_ctx* c, SpecOp op, const SpecArgs& a, int ncomp_bytes_fields
 int op_grad(reg_ctx* c, const float* f, float* out3);
 int op_div(reg_ctx* c, const float* v3, float* out);
 int op_inner(reg_ctx* c, const float* a, const float* b, long long count, int slot);
+// Linearisation at v: points, div v and c(x), state history, grad rho
+// levels, adjoint, and b = int lam grad rho dt into bacc.
+int op_linearize(reg_ctx* c, const float* v);
 int op_gradient(reg_ctx* c, const float* v, float* g, int slot_J);
 int op_objective(reg_ctx* c, const float* v, int slot_J);
+// dsc[SC_JMIS] = 1/2 ||rho(1) - rho_R||^2_h for v (scratch buffers only).
+int op_mismatch(reg_ctx* c, const float* v);
 int op_matvec(reg_ctx* c, const float* vt, float* out);
+// The transports of one GN matvec: lam_hist receives lam~(t_0..t_nt).
+int op_matvec_transport(reg_ctx* c, const float* vt);
+int op_time_integral(reg_ctx* c, const float* base, float* out, const float* dotp, int slot);
 int op_precond(reg_ctx* c, const float* r, float* z);
 int op_leray(reg_ctx* c, const float* v, float* out);
 int read_scalars(reg_ctx* c, int first, int count);   // dsc -> hsc, synchronises
@@ -103,7 +119,7 @@ int ensure_solver(reg_ctx* c);
 enum {
     SC_JMIS = 0, SC_JREG = 1, SC_J = 2, SC_TMP = 3,
     SC_RZ = 4, SC_PQ = 5, SC_RR = 6, SC_RZNEW = 7, SC_GG = 8, SC_GS = 9,
-    SC_INNER = 10
+    SC_INNER = 10, SC_ZERO = 11, SC_PAP = 12, SC_PB = 13
 };
 
 }  // namespace reg

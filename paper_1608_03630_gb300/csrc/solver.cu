@@ -1,18 +1,26 @@
 // Inexact Gauss-Newton-Krylov solve (Sec. III-A, Sec. IV-A3): PCG on
-// H s = -g with the spectral preconditioner, forcing tied to the relative
-// gradient norm, Armijo backtracking on J, stop at ||g|| <= gtol ||g_0||.
+// H s = -g with the inverse-regularisation preconditioner, forcing tied to
+// the relative gradient norm, Armijo backtracking on J, stop at
+// ||g|| <= gtol ||g_0||.
 //
-// The PCG recurrence keeps its scalars (r.z, p.Hp, r.r) in device memory and
-// the update kernels read alpha and beta from there, so one PCG iteration is
-// a fixed sequence of launches with no host round trip; the host reads r.r
-// and p.Hp once per iteration (after the speculative preconditioner and
-// direction update) for the stopping and curvature tests.  With
-// use_graph = 1 that sequence is captured once into a CUDA graph and
-// replayed, one launch per iteration.
+// The iterate v and the Krylov vectors (g, s, r, p) are kept as normalised
+// Fourier coefficients (FP32 complex, half spectrum).  The regularisation
+// beta A grows like beta |k|^4 (about 2e6 at 256^3 with beta = 1e-3): applied
+// to an FP32 field stored in physical space it multiplies the rounding noise
+// that storage puts into every mode, and the gradient stalls at that noise
+// (near 2 % of ||beta A v|| at 256^3).  On coefficients, rounding is relative
+// to each coefficient and beta A, M and P are exact diagonal multiplications.
+// Per PCG iteration the matvec needs p in physical space (one C2R of three
+// fields) for the transports and b~ in Fourier space (one R2C); every inner
+// product is taken by Parseval in FP64.  The scalars live in device memory:
+// one iteration is a fixed launch sequence, captured once into a CUDA graph
+// (use_graph = 1) and replayed; the host reads p.Hp and ||r|| once per
+// iteration for the curvature and stopping tests.
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <utility>
 
 #include "ctx.h"
 
@@ -20,23 +28,48 @@ namespace reg {
 
 static const double kTwoPi3 = 248.05021344239856;   // (2 pi)^3
 
-enum { V_G = 0, V_S = 1, V_R = 2, V_Z = 3, V_P = 4, V_Q = 5, V_TRIAL = 6, V_SPARE = 7 };
+// real vectors
+enum { R_V = 0, R_P = 1, R_HOST = 2 };
+// spectral vectors
+enum { S_V = 0, S_VT = 1, S_G = 2, S_S = 3, S_R = 4, S_P = 5, S_PC = 6 };
 
-// One PCG iteration from p: q = H p; PQ = <p, q>; s += a p, r -= a q (a = RZ/PQ,
-// skipped when PQ <= 0); RR = <r, r>; z = M r; RZNEW = <r, z>;
-// p = z + (RZNEW/RZ) p; RZ = RZNEW.
+static int finalize_to(reg_ctx* c, int t, int nb, double scale, int slot) {
+    if ((long long)(t + 1) * nb > c->npartials)
+        return fail(c, REG_EINVAL, "partial-sum slot out of range");
+    REG_CK(c, launch_finalize(c->partials + (long long)t * nb, nb, scale, c->dsc + slot,
+                              c->stream));
+    return REG_OK;
+}
+
+// Physical-space copy of a spectral vector (C2R destroys its input, so the
+// coefficients go through spec[0]).
+static int to_physical(reg_ctx* c, const float2* xh, float* x) {
+    REG_CK(c, cudaMemcpyAsync(c->spec[0], xh, sizeof(float2) * 3 * (size_t)c->g.nc,
+                              cudaMemcpyDeviceToDevice, c->stream));
+    return op_fft_c2r(c, c->spec[0], x, 3);
+}
+
+// One PCG iteration from p (p_hat, its C2R copy pc): q = beta A p + P b~(p),
+// PQ = <p, q> = <p, beta A p> + <p, b~>; s += a p, r -= a q (a = RZ / PQ,
+// skipped when PQ <= 0); RR = ||P r||^2, RZNEW = <r, M P r>;
+// p = M P r + (RZNEW / RZ) p with <p, beta A p> for the next PQ; RZ = RZNEW.
 static int pcg_iteration(reg_ctx* c) {
-    const long long cnt = 3LL * c->g.n;
-    float** v = c->sv;
-    REG_TRY(op_matvec(c, v[V_P], v[V_Q]));
-    REG_TRY(op_inner(c, v[V_P], v[V_Q], cnt, SC_PQ));
     const int nb = blas_blocks();
-    REG_CK(c, launch_pcg_update(v[V_S], v[V_R], v[V_P], v[V_Q], c->dsc, SC_RZ, SC_PQ, cnt,
-                                c->partials, nb, c->stream));
-    REG_CK(c, launch_finalize(c->partials, nb, kTwoPi3 / c->g.n, c->dsc + SC_RR, c->stream));
-    REG_TRY(op_precond(c, v[V_R], v[V_Z]));
-    REG_TRY(op_inner(c, v[V_R], v[V_Z], cnt, SC_RZNEW));
-    REG_CK(c, launch_pcg_direction(v[V_P], v[V_Z], c->dsc, SC_RZNEW, SC_RZ, cnt, c->stream));
+    const int proj = c->incompressible;
+    float2** S = c->ss;
+    float* p = c->sv[R_P];
+    REG_TRY(op_fft_c2r(c, S[S_PC], p, 3));
+    REG_TRY(op_matvec_transport(c, p));
+    REG_TRY(op_time_integral(c, nullptr, c->bacc, p, SC_PB));
+    REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
+    REG_CK(c, launch_sp_update(c->g, S[S_S], S[S_R], S[S_P], c->spec[1], c->dsc, SC_RZ, SC_PAP,
+                               SC_PB, SC_PQ, c->beta, c->kind, proj, c->partials, nb,
+                               c->stream));
+    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
+    REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZNEW));
+    REG_CK(c, launch_sp_direction(c->g, S[S_R], S[S_P], S[S_PC], c->dsc, SC_RZNEW, SC_RZ, 0,
+                                  c->beta, c->kind, proj, c->partials, nb, c->stream));
+    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_PAP));
     REG_CK(c, cudaMemcpyAsync(c->dsc + SC_RZ, c->dsc + SC_RZNEW, sizeof(double),
                               cudaMemcpyDeviceToDevice, c->stream));
     return REG_OK;
@@ -44,21 +77,24 @@ static int pcg_iteration(reg_ctx* c) {
 
 struct PcgResult { int iters; bool neg_curv; bool converged; };
 
-static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, PcgResult* res) {
-    const long long cnt = 3LL * c->g.n;
-    float** v = c->sv;
+static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, int verbose,
+                     PcgResult* res) {
+    const int nb = blas_blocks();
+    const int proj = c->incompressible;
+    float2** S = c->ss;
     res->iters = 0;
     res->neg_curv = false;
     res->converged = false;
-    // s = 0, r = -g, z = M r, p = z
-    REG_CK(c, cudaMemsetAsync(v[V_S], 0, sizeof(float) * cnt, c->stream));
-    REG_CK(c, launch_axpby_out(v[V_R], v[V_G], v[V_G], -1.f, 0.f, cnt, c->stream));
-    REG_TRY(op_precond(c, v[V_R], v[V_Z]));
-    REG_CK(c, cudaMemcpyAsync(v[V_P], v[V_Z], sizeof(float) * cnt, cudaMemcpyDeviceToDevice,
-                              c->stream));
-    REG_TRY(op_inner(c, v[V_R], v[V_Z], cnt, SC_RZ));
-    REG_TRY(op_inner(c, v[V_R], v[V_R], cnt, SC_RR));
-    REG_TRY(read_scalars(c, SC_RR, 1));
+    // r = -g, s = 0, p = M P r
+    REG_CK(c, launch_sp_init(c->g, S[S_G], S[S_R], S[S_S], S[S_P], S[S_PC], c->beta, c->kind,
+                             proj, c->partials, nb, c->stream));
+    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
+    REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZ));
+    REG_TRY(finalize_to(c, 2, nb, kTwoPi3, SC_PAP));
+    REG_TRY(read_scalars(c, SC_RZ, 13));
+    if (verbose > 1)
+        fprintf(stderr, "  pcg 0  rr %.6e  rz %.6e  pap %.6e  tol %.6e\n", c->hsc[SC_RR],
+                c->hsc[SC_RZ], c->hsc[SC_PAP], tol);
     if (std::sqrt(c->hsc[SC_RR]) <= tol) { res->converged = true; return REG_OK; }
 
     cudaGraphExec_t exec = nullptr;
@@ -98,6 +134,11 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, PcgResu
         if (status != REG_OK) break;
         res->iters = it;
         const double pq = c->hsc[SC_PQ], rr = c->hsc[SC_RR];
+        if (verbose > 1) {
+            read_scalars(c, SC_RZ, 10);
+            fprintf(stderr, "  pcg %d  pq %.6e  rr %.6e  rz %.6e  pap %.6e  pb %.6e\n", it, pq, rr,
+                    c->hsc[SC_RZ], c->hsc[SC_PAP], c->hsc[SC_PB]);
+        }
         if (!std::isfinite(pq) || !std::isfinite(rr)) {
             status = fail(c, REG_ENONFINITE, "non-finite value in PCG");
             break;
@@ -106,7 +147,11 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, PcgResu
             res->neg_curv = true;
             if (it == 1) {
                 // first direction: the preconditioned steepest-descent step
-                status = op_precond(c, v[V_R], v[V_S]);
+                // s = M P r (r is still -g: the update was skipped)
+                const cudaError_t e = launch_sp_direction(c->g, S[S_R], S[S_S], nullptr, c->dsc,
+                                                          SC_ZERO, SC_RZ, 1, c->beta, c->kind,
+                                                          proj, c->partials, nb, c->stream);
+                if (e != cudaSuccess) status = fail_cuda(c, e, "launch_sp_direction", __LINE__);
             }
             break;
         }
@@ -117,9 +162,18 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, PcgResu
     return status;
 }
 
-static int evaluate_gradient(reg_ctx* c, const float* v, float* g, double* J, double* gnorm) {
-    REG_TRY(op_gradient(c, v, g, SC_J));
-    REG_TRY(op_inner(c, g, g, 3LL * c->g.n, SC_GG));
+// g_hat = beta A v_hat + P b_hat at the spectral iterate; J and ||g||.
+static int evaluate_gradient(reg_ctx* c, double* J, double* gnorm) {
+    const int nb = blas_blocks();
+    float2** S = c->ss;
+    float* v = c->sv[R_V];
+    REG_TRY(to_physical(c, S[S_V], v));
+    REG_TRY(op_linearize(c, v));
+    REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
+    REG_CK(c, launch_sp_gradient(c->g, S[S_V], c->spec[1], S[S_G], c->beta, c->kind,
+                                 c->incompressible, c->partials, nb, c->stream));
+    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_GG));
+    REG_TRY(finalize_to(c, 1, nb, 0.5 * c->beta * kTwoPi3, SC_JREG));
     REG_TRY(read_scalars(c, SC_JMIS, 9));
     *J = c->hsc[SC_JMIS] + c->hsc[SC_JREG];
     *gnorm = std::sqrt(c->hsc[SC_GG]);
@@ -128,11 +182,29 @@ static int evaluate_gradient(reg_ctx* c, const float* v, float* g, double* J, do
     return REG_OK;
 }
 
-static int solve_impl(reg_ctx* c, float* v, const reg_solve_opts* o, reg_solve_stats* st) {
+// J at v_hat + alpha s_hat (into S_VT): forward state solve only.
+static int evaluate_trial(reg_ctx* c, double alpha, double* J) {
+    const int nb = blas_blocks();
+    float2** S = c->ss;
+    REG_CK(c, launch_sp_axpy(c->g, S[S_VT], c->spec[0], S[S_V], S[S_S], (float)alpha, c->kind, 0,
+                             c->partials, nb, c->stream));
+    REG_TRY(finalize_to(c, 0, nb, 0.5 * c->beta * kTwoPi3, SC_JREG));
+    float* v = c->sv[R_V];
+    REG_TRY(op_fft_c2r(c, c->spec[0], v, 3));
+    REG_TRY(op_mismatch(c, v));
+    REG_TRY(read_scalars(c, SC_JMIS, 2));
+    *J = c->hsc[SC_JMIS] + c->hsc[SC_JREG];
+    return REG_OK;
+}
+
+static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solve_stats* st) {
     const auto t0 = std::chrono::steady_clock::now();
-    const long long n = c->g.n, cnt = 3 * n;
-    float** w = c->sv;
-    if (c->incompressible) REG_TRY(op_leray(c, v, v));
+    const long long n = c->g.n;
+    const int nb = blas_blocks();
+    float2** S = c->ss;
+    // v_hat = F v / n (projected when incompressible)
+    REG_TRY(op_fft_r2c(c, v_io, c->spec[0], 3));
+    REG_CK(c, launch_sp_normalise(c->g, c->spec[0], S[S_V], c->incompressible, c->stream));
     // ||rho_T - rho_R|| for the relative mismatch
     REG_CK(c, launch_axpby_out(c->tmp3, c->rho_T, c->rho_R, 1.f, -1.f, n, c->stream));
     REG_TRY(op_inner(c, c->tmp3, c->tmp3, n, SC_TMP));
@@ -140,32 +212,31 @@ static int solve_impl(reg_ctx* c, float* v, const reg_solve_opts* o, reg_solve_s
     const double m0 = std::sqrt(c->hsc[SC_TMP]);
 
     double J, gn;
-    REG_TRY(evaluate_gradient(c, v, w[V_G], &J, &gn));
+    REG_TRY(evaluate_gradient(c, &J, &gn));
     st->gradient_evals++;
     const double g0 = gn;
     st->J0 = J;
     st->gnorm0 = g0;
+    double jmis = c->hsc[SC_JMIS];
     int status = REG_EMAXITER;
     for (int k = 0; k < o->max_gn; ++k) {
         if (gn <= o->gtol * g0 || g0 == 0.0) { status = REG_OK; break; }
         const double ratio = gn / g0;
         const double eta = std::fmin(0.5, o->forcing == 1 ? std::sqrt(ratio) : ratio);
         PcgResult pr;
-        REG_TRY(pcg_solve(c, eta * gn, o->max_pcg, o->use_graph != 0, &pr));
+        REG_TRY(pcg_solve(c, eta * gn, o->max_pcg, o->use_graph != 0, o->verbose, &pr));
         st->pcg_iters += pr.iters;
         st->matvecs += pr.iters;
         st->negative_curvature += pr.neg_curv ? 1 : 0;
-        REG_TRY(op_inner(c, w[V_G], w[V_S], cnt, SC_GS));
+        REG_CK(c, launch_sp_dot(c->g, S[S_G], S[S_S], c->partials, nb, c->stream));
+        REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_GS));
         REG_TRY(read_scalars(c, SC_GS, 1));
         const double slope = c->hsc[SC_GS];
         double alpha = 1.0, Jt = J;
         bool accepted = false;
         for (int m = 0; m < o->armijo_max; ++m) {
-            REG_CK(c, launch_axpby_out(w[V_TRIAL], v, w[V_S], 1.f, (float)alpha, cnt, c->stream));
-            REG_TRY(op_objective(c, w[V_TRIAL], SC_J));
-            REG_TRY(read_scalars(c, SC_JMIS, 2));
+            REG_TRY(evaluate_trial(c, alpha, &Jt));
             st->objective_evals++;
-            Jt = c->hsc[SC_JMIS] + c->hsc[SC_JREG];
             if (std::isfinite(Jt) && Jt <= J + o->armijo_c * alpha * slope) {
                 accepted = true;
                 break;
@@ -177,9 +248,9 @@ static int solve_impl(reg_ctx* c, float* v, const reg_solve_opts* o, reg_solve_s
             status = REG_EMAXITER;
             break;
         }
-        REG_CK(c, cudaMemcpyAsync(v, w[V_TRIAL], sizeof(float) * cnt, cudaMemcpyDeviceToDevice,
-                                  c->stream));
-        REG_TRY(evaluate_gradient(c, v, w[V_G], &J, &gn));
+        std::swap(S[S_V], S[S_VT]);
+        REG_TRY(evaluate_gradient(c, &J, &gn));
+        jmis = c->hsc[SC_JMIS];
         st->gradient_evals++;
         st->gn_iters = k + 1;
         if (o->verbose)
@@ -187,10 +258,11 @@ static int solve_impl(reg_ctx* c, float* v, const reg_solve_opts* o, reg_solve_s
                     gn / g0, pr.iters, alpha, pr.neg_curv ? "  (negative curvature)" : "");
     }
     if (status == REG_EMAXITER && (gn <= o->gtol * g0 || g0 == 0.0)) status = REG_OK;
+    REG_TRY(to_physical(c, S[S_V], v_io));
     st->J = J;
     st->gnorm = gn;
     st->gnorm_rel = g0 > 0 ? gn / g0 : 0.0;
-    st->mismatch_rel = m0 > 0 ? std::sqrt(2.0 * c->hsc[SC_JMIS]) / m0 : 0.0;
+    st->mismatch_rel = m0 > 0 ? std::sqrt(2.0 * jmis) / m0 : 0.0;
     REG_CK(c, cudaStreamSynchronize(c->stream));
     st->ms_total =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -250,7 +322,7 @@ int reg_solve_host(reg_ctx* c, const float* rho_T_host, const float* rho_R_host,
     REG_CK(c, cudaMemcpyAsync(c->rho_R, rho_R_host, sizeof(float) * n, cudaMemcpyHostToDevice,
                               c->stream));
     REG_TRY(reg_set_images(c, c->rho_T, c->rho_R, presmooth));
-    float* v = c->sv[V_SPARE];
+    float* v = c->sv[R_HOST];
     REG_CK(c, cudaMemcpyAsync(v, v_host_inout, sizeof(float) * 3 * n, cudaMemcpyHostToDevice,
                               c->stream));
     const int s = reg_solve(c, v, opts, stats);

@@ -159,7 +159,285 @@ k_spec_energy(Dims g, const float2* __restrict__ v, int kind, double* partials) 
     }
 }
 
+// ------------------------------------------------ spectral Krylov vectors
+// The solver keeps v, g, s, r, p as normalised half-spectrum coefficients
+// (C2R gives the field itself): 3 components x nc entries.  Inner products
+// <a, b>_h = (2 pi)^3 sum_k herm(k) Re(conj(a_k) b_k) (Parseval).  Each kernel
+// writes per-block FP64 partials, slot t at partials[t * gridDim.x + block].
+
+__device__ __forceinline__ float mprec(float A, float beta) {
+    return A > 0.f ? 1.f / (beta * A) : 1.f / beta;
+}
+
+__device__ __forceinline__ double herm_sq(const Wave& w, float2 a, float2 b, float2 c) {
+    return (double)w.herm * ((double)a.x * a.x + (double)a.y * a.y + (double)b.x * b.x +
+                             (double)b.y * b.y + (double)c.x * c.x + (double)c.y * c.y);
+}
+
+template <int NS>
+__device__ __forceinline__ void store_partials(double (&acc)[NS], double* partials) {
+    __shared__ double red[NS][kThreads / 32];
+#pragma unroll
+    for (int t = 0; t < NS; ++t)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int t = 0; t < NS; ++t) red[t][wid] = acc[t];
+    __syncthreads();
+    if (threadIdx.x < NS) {
+        double s = 0.0;
+        for (int i = 0; i < kThreads / 32; ++i) s += red[threadIdx.x][i];
+        partials[threadIdx.x * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+#define SPEC_LOOP for (int idx = blockIdx.x * kThreads + threadIdx.x; idx < g.nc; \
+                       idx += gridDim.x * kThreads)
+
+// r = -g, s = 0, z = M P r, p = pc = z; partials: |P r|^2, M |P r|^2, beta A |p|^2.
+__global__ void __launch_bounds__(kThreads)
+k_sp_init(Dims g, const float2* __restrict__ gh, float2* __restrict__ r, float2* __restrict__ s,
+          float2* __restrict__ p, float2* __restrict__ pc, float beta, int kind, int project,
+          double* partials) {
+    const long long nc = g.nc;
+    double acc[3] = {0.0, 0.0, 0.0};
+    SPEC_LOOP {
+        const Wave w = wave(g, idx);
+        float2 a = gh[idx], b = gh[nc + idx], c = gh[2 * nc + idx];
+        a = scale2(a, -1.f); b = scale2(b, -1.f); c = scale2(c, -1.f);
+        r[idx] = a; r[nc + idx] = b; r[2 * nc + idx] = c;
+        const float2 zero = make_float2(0.f, 0.f);
+        s[idx] = zero; s[nc + idx] = zero; s[2 * nc + idx] = zero;
+        if (project) leray3(w, a, b, c);
+        const float A = reg_symbol(w, kind);
+        const float m = mprec(A, beta);
+        const double e = herm_sq(w, a, b, c);
+        acc[0] += e;
+        acc[1] += (double)m * e;
+        acc[2] += (double)beta * A * (double)m * m * e;
+        a = scale2(a, m); b = scale2(b, m); c = scale2(c, m);
+        p[idx] = a; p[nc + idx] = b; p[2 * nc + idx] = c;
+        pc[idx] = a; pc[nc + idx] = b; pc[2 * nc + idx] = c;
+    }
+    store_partials<3>(acc, partials);
+}
+
+// PQ = sc[ipap] + sc[ipb] (written to sc_out[ipq] by block 0), alpha = RZ / PQ
+// (0 if PQ <= 0); q = beta A p + P B / n; s += alpha p; r -= alpha q;
+// partials: |P r|^2, M |P r|^2.
+__global__ void __launch_bounds__(kThreads)
+k_sp_update(Dims g, float2* __restrict__ s, float2* __restrict__ r, const float2* __restrict__ p,
+            const float2* __restrict__ B, double* sc, int irz, int ipap, int ipb, int ipq,
+            float beta, int kind, int project, float inv_n, double* partials) {
+    const long long nc = g.nc;
+    const double pq = sc[ipap] + sc[ipb];
+    const float alpha = pq > 0.0 ? (float)(sc[irz] / pq) : 0.f;
+    if (blockIdx.x == 0 && threadIdx.x == 0) sc[ipq] = pq;
+    double acc[2] = {0.0, 0.0};
+    SPEC_LOOP {
+        const Wave w = wave(g, idx);
+        const float A = reg_symbol(w, kind);
+        const float bA = beta * A;
+        float2 b0 = scale2(B[idx], inv_n), b1 = scale2(B[nc + idx], inv_n),
+               b2 = scale2(B[2 * nc + idx], inv_n);
+        if (project) leray3(w, b0, b1, b2);
+        float2 rr[3], pp[3];
+        const float2 bb[3] = {b0, b1, b2};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            pp[k] = p[k * nc + idx];
+            float2 sv = s[k * nc + idx];
+            sv.x = fmaf(alpha, pp[k].x, sv.x);
+            sv.y = fmaf(alpha, pp[k].y, sv.y);
+            s[k * nc + idx] = sv;
+            const float2 q = make_float2(fmaf(bA, pp[k].x, bb[k].x), fmaf(bA, pp[k].y, bb[k].y));
+            rr[k] = r[k * nc + idx];
+            rr[k].x = fmaf(-alpha, q.x, rr[k].x);
+            rr[k].y = fmaf(-alpha, q.y, rr[k].y);
+            r[k * nc + idx] = rr[k];
+        }
+        if (project) leray3(w, rr[0], rr[1], rr[2]);
+        const double e = herm_sq(w, rr[0], rr[1], rr[2]);
+        acc[0] += e;
+        acc[1] += (double)mprec(A, beta) * e;
+    }
+    store_partials<2>(acc, partials);
+}
+
+// b = sc[irznew] / sc[irz] (0 with zero_beta); p = M P r + b p; pc = p (or, with
+// to_s, s = M P r only); partials: beta A |p|^2.
+__global__ void __launch_bounds__(kThreads)
+k_sp_direction(Dims g, const float2* __restrict__ r, float2* __restrict__ p,
+               float2* __restrict__ pc, const double* __restrict__ sc, int irznew, int irz,
+               int zero_beta, float beta, int kind, int project, double* partials) {
+    const long long nc = g.nc;
+    const double den = sc[irz];
+    const float bk = (zero_beta || den == 0.0) ? 0.f : (float)(sc[irznew] / den);
+    double acc[1] = {0.0};
+    SPEC_LOOP {
+        const Wave w = wave(g, idx);
+        float2 a = r[idx], b = r[nc + idx], c = r[2 * nc + idx];
+        if (project) leray3(w, a, b, c);
+        const float A = reg_symbol(w, kind);
+        const float m = mprec(A, beta);
+        float2 z[3] = {scale2(a, m), scale2(b, m), scale2(c, m)};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float2 pv = zero_beta ? make_float2(0.f, 0.f) : p[k * nc + idx];
+            pv.x = fmaf(bk, pv.x, z[k].x);
+            pv.y = fmaf(bk, pv.y, z[k].y);
+            p[k * nc + idx] = pv;
+            if (pc) pc[k * nc + idx] = pv;
+            z[k] = pv;
+        }
+        acc[0] += (double)beta * A * herm_sq(w, z[0], z[1], z[2]);
+    }
+    store_partials<1>(acc, partials);
+}
+
+// g = beta A v + P B / n; partials: |g|^2, A |v|^2.
+__global__ void __launch_bounds__(kThreads)
+k_sp_gradient(Dims g, const float2* __restrict__ v, const float2* __restrict__ B,
+              float2* __restrict__ gout, float beta, int kind, int project, float inv_n,
+              double* partials) {
+    const long long nc = g.nc;
+    double acc[2] = {0.0, 0.0};
+    SPEC_LOOP {
+        const Wave w = wave(g, idx);
+        const float A = reg_symbol(w, kind);
+        float2 b0 = scale2(B[idx], inv_n), b1 = scale2(B[nc + idx], inv_n),
+               b2 = scale2(B[2 * nc + idx], inv_n);
+        if (project) leray3(w, b0, b1, b2);
+        const float2 v0 = v[idx], v1 = v[nc + idx], v2 = v[2 * nc + idx];
+        const float bA = beta * A;
+        const float2 g0 = make_float2(fmaf(bA, v0.x, b0.x), fmaf(bA, v0.y, b0.y));
+        const float2 g1 = make_float2(fmaf(bA, v1.x, b1.x), fmaf(bA, v1.y, b1.y));
+        const float2 g2 = make_float2(fmaf(bA, v2.x, b2.x), fmaf(bA, v2.y, b2.y));
+        gout[idx] = g0; gout[nc + idx] = g1; gout[2 * nc + idx] = g2;
+        acc[0] += herm_sq(w, g0, g1, g2);
+        acc[1] += (double)A * herm_sq(w, v0, v1, v2);
+    }
+    store_partials<2>(acc, partials);
+}
+
+// out = x + a y (y may be null), copy = out (may be null), optional Leray
+// projection; partials: A |out|^2.
+__global__ void __launch_bounds__(kThreads)
+k_sp_axpy(Dims g, float2* __restrict__ out, float2* __restrict__ copy, const float2* x,
+          const float2* __restrict__ y, float a, int kind, int project, double* partials) {
+    const long long nc = g.nc;
+    double acc[1] = {0.0};
+    SPEC_LOOP {
+        const Wave w = wave(g, idx);
+        float2 o[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            o[k] = x[k * nc + idx];
+            if (y) {
+                const float2 yv = y[k * nc + idx];
+                o[k].x = fmaf(a, yv.x, o[k].x);
+                o[k].y = fmaf(a, yv.y, o[k].y);
+            }
+        }
+        if (project) leray3(w, o[0], o[1], o[2]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            out[k * nc + idx] = o[k];
+            if (copy) copy[k * nc + idx] = o[k];
+        }
+        acc[0] += (double)reg_symbol(w, kind) * herm_sq(w, o[0], o[1], o[2]);
+    }
+    store_partials<1>(acc, partials);
+}
+
+// partials: sum herm Re(conj(a) b) over the 3 components.
+__global__ void __launch_bounds__(kThreads)
+k_sp_dot(Dims g, const float2* __restrict__ a, const float2* __restrict__ b, double* partials) {
+    const long long nc = g.nc;
+    double acc[1] = {0.0};
+    SPEC_LOOP {
+        const Wave w = wave(g, idx);
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float2 x = a[k * nc + idx], y = b[k * nc + idx];
+            s += (double)x.x * y.x + (double)x.y * y.y;
+        }
+        acc[0] += (double)w.herm * s;
+    }
+    store_partials<1>(acc, partials);
+}
+
+// out = in / n (normalise a raw R2C spectrum), optional Leray projection.
+__global__ void __launch_bounds__(kThreads)
+k_sp_normalise(Dims g, const float2* in, float2* out, int project, float inv_n) {
+    const long long nc = g.nc;
+    SPEC_LOOP {
+        const Wave w = wave(g, idx);
+        float2 a = scale2(in[idx], inv_n), b = scale2(in[nc + idx], inv_n),
+               c = scale2(in[2 * nc + idx], inv_n);
+        if (project) leray3(w, a, b, c);
+        out[idx] = a; out[nc + idx] = b; out[2 * nc + idx] = c;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_sp_init(const Dims& g, const float2* gh, float2* r, float2* s, float2* p,
+                           float2* pc, double beta, int kind, int project, double* partials,
+                           int nblk, cudaStream_t st) {
+    k_sp_init<<<nblk, kThreads, 0, st>>>(g, gh, r, s, p, pc, (float)beta, kind, project, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_update(const Dims& g, float2* s, float2* r, const float2* p,
+                             const float2* B, double* sc, int irz, int ipap, int ipb, int ipq,
+                             double beta, int kind, int project, double* partials, int nblk,
+                             cudaStream_t st) {
+    k_sp_update<<<nblk, kThreads, 0, st>>>(g, s, r, p, B, sc, irz, ipap, ipb, ipq, (float)beta,
+                                           kind, project, 1.0f / (float)g.n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_direction(const Dims& g, const float2* r, float2* p, float2* pc,
+                                const double* sc, int irznew, int irz, int zero_beta,
+                                double beta, int kind, int project, double* partials, int nblk,
+                                cudaStream_t st) {
+    k_sp_direction<<<nblk, kThreads, 0, st>>>(g, r, p, pc, sc, irznew, irz, zero_beta,
+                                              (float)beta, kind, project, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_gradient(const Dims& g, const float2* v, const float2* B, float2* gout,
+                               double beta, int kind, int project, double* partials, int nblk,
+                               cudaStream_t st) {
+    k_sp_gradient<<<nblk, kThreads, 0, st>>>(g, v, B, gout, (float)beta, kind, project,
+                                             1.0f / (float)g.n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_axpy(const Dims& g, float2* out, float2* copy, const float2* x,
+                           const float2* y, float a, int kind, int project, double* partials,
+                           int nblk, cudaStream_t st) {
+    k_sp_axpy<<<nblk, kThreads, 0, st>>>(g, out, copy, x, y, a, kind, project, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_dot(const Dims& g, const float2* a, const float2* b, double* partials,
+                          int nblk, cudaStream_t st) {
+    k_sp_dot<<<nblk, kThreads, 0, st>>>(g, a, b, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_normalise(const Dims& g, const float2* in, float2* out, int project,
+                                cudaStream_t st) {
+    const int nb = (g.nc + kThreads - 1) / kThreads;
+    k_sp_normalise<<<nb < 152 * 8 ? nb : 152 * 8, kThreads, 0, st>>>(g, in, out, project,
+                                                                     1.0f / (float)g.n);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_spectral(const Dims& g, SpecOp op, const SpecArgs& a, cudaStream_t st) {
     const int nb = (g.nc + kThreads - 1) / kThreads;

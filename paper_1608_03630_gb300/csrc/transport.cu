@@ -1,10 +1,23 @@
-// Semi-Lagrangian kernels: RK2 points, tricubic interpolation and the fused
-// transport steps of the state, adjoint, incremental state and incremental
-// adjoint equations (Sec. III-B2, Sec. III-C2, Algorithm 2).
+// Semi-Lagrangian kernels (Sec. III-B2, Sec. III-C2, Algorithm 2): RK2
+// points, tricubic Lagrange interpolation and the fused transport steps of
+// the state, adjoint, incremental state and incremental adjoint.
 //
-// One thread per output grid point, x3 fastest across a warp so the reads of
-// the per-point inputs (displacements, grid fields) are coalesced; the 64
-// stencil values come through the read-only cache.
+// Every transport step gathers ONE scalar field at the semi-Lagrangian
+// points:
+//   state            rho_{j+1} = I[rho_j](X)
+//   (inc.) adjoint   lam_j = c(x) I[lam_{j+1}](X)        (source lam div v)
+//   inc. state       u_{j+1} = I[u_j](X) + dt f_{j+1}(x),  u = rho~ + dt/2 f
+// (the last two are exact rearrangements of Eq. (sml-advection), see the
+// launchers).  The gather runs in x1-marching kernels: a block is 32 lanes
+// along x3 (coalesced per-point reads and writes) by wy rows along x2, and
+// each thread walks k consecutive points along x1.  The 4 x 4 x 4 stencil
+// values stay in registers as four x1-planes of 4 x 4; when the next point's
+// stencil is the current one shifted by one plane along x1 (same x2/x3 base),
+// only the new plane (16 values) is loaded and the other 48 are reused.  The
+// plane slots rotate with a period of four unrolled steps, so every register
+// index is static.
+#include <climits>
+
 #include "common.cuh"
 
 namespace reg {
@@ -20,8 +33,10 @@ __device__ __forceinline__ float ld(const __nv_bfloat16* p, long long i) {
     return __bfloat162float(p[i]);
 }
 
-// Eq. (sml-trajectory) for v and -v.  dtoh_j = dt / h_j converts velocity to
-// grid units per step.
+// ------------------------------------------------------ plain gather kernels
+
+// Eq. (sml-trajectory) for v and -v.  dth_j = dt / h_j converts a velocity
+// to grid units per step.
 __global__ void __launch_bounds__(kThreads)
 k_departure(Dims g, const float* __restrict__ v, float dth1, float dth2, float dth3,
             float* __restrict__ d_fwd, float* __restrict__ d_adj) {
@@ -35,7 +50,7 @@ k_departure(Dims g, const float* __restrict__ v, float dth1, float dth2, float d
     const float* v2 = v + n;
     const float* v3 = v + 2 * n;
     Stencil s;
-    // forward: X* = x - dt v(x)
+    // forward: X* = x - dt v(x), X = x - dt/2 (v(x) + v(X*))
     make_stencil(s, g, i1, i2, i3, -u1, -u2, -u3);
     float a1 = gather1(s, v1) * dth1, a2 = gather1(s, v2) * dth2, a3 = gather1(s, v3) * dth3;
     d_fwd[idx] = -0.5f * (u1 + a1);
@@ -48,153 +63,6 @@ k_departure(Dims g, const float* __restrict__ v, float dth1, float dth2, float d
     d_adj[idx] = 0.5f * (u1 + a1);
     d_adj[n + idx] = 0.5f * (u2 + a2);
     d_adj[2 * n + idx] = 0.5f * (u3 + a3);
-}
-
-__global__ void __launch_bounds__(kThreads)
-k_interp(Dims g, const float* __restrict__ f, int nf, const float* __restrict__ d,
-         float* __restrict__ out) {
-    const int idx = blockIdx.x * kThreads + threadIdx.x;
-    if (idx >= g.n) return;
-    int i1, i2, i3;
-    unflatten(g, idx, i1, i2, i3);
-    const long long n = g.n;
-    Stencil s;
-    make_stencil(s, g, i1, i2, i3, d[idx], d[n + idx], d[2 * n + idx]);
-    for (int c = 0; c < nf; ++c) out[c * n + idx] = gather1(s, f + c * n);
-}
-
-// Block reduction of a double into partials[blockIdx.x].
-__device__ __forceinline__ void block_sum_to(double v, double* partials) {
-    __shared__ double red[kThreads / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (lane == 0) red[wid] = v;
-    __syncthreads();
-    if (wid == 0) {
-        v = lane < kThreads / 32 ? red[lane] : 0.0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) partials[blockIdx.x] = v;
-    }
-}
-
-// State step; the final step also forms lam(1) = rho_R - rho(1) and the
-// mismatch partial sums (Eq. varopt, Eq. adjoint).
-template <bool FINAL>
-__global__ void __launch_bounds__(kThreads)
-k_state_step(Dims g, const float* __restrict__ rin, const float* __restrict__ d,
-             float* __restrict__ rout, const float* __restrict__ rho_R,
-             const float* __restrict__ divv, void* __restrict__ lam_out,
-             double* __restrict__ partials) {
-    const int idx = blockIdx.x * kThreads + threadIdx.x;
-    double e2 = 0.0;
-    if (idx < g.n) {
-        int i1, i2, i3;
-        unflatten(g, idx, i1, i2, i3);
-        const long long n = g.n;
-        Stencil s;
-        make_stencil(s, g, i1, i2, i3, d[idx], d[n + idx], d[2 * n + idx]);
-        const float r = gather1(s, rin);
-        rout[idx] = r;
-        if (FINAL) {
-            const float lam = rho_R[idx] - r;
-            e2 = (double)lam * (double)lam;
-            if (lam_out) {
-                if (divv) reinterpret_cast<float2*>(lam_out)[idx] = make_float2(lam, divv[idx]);
-                else reinterpret_cast<float*>(lam_out)[idx] = lam;
-            }
-        }
-    }
-    if (FINAL) block_sum_to(e2, partials);
-}
-
-// Adjoint tau-step (Eq. adjoint, Eq. sml-advection), with b += w lam grad rho.
-// Compressible: lam_in holds (lam, div v); source f = lam div v,
-//   nu0 = I[lam](X), f0 = I[lam div v](X), nu* = nu0 + dt f0,
-//   lam_new = nu0 + dt/2 (f0 + nu* div v(x)).
-// Divergence free: lam_new = I[lam](X).
-template <bool COMP, bool FIRST, typename GT>
-__global__ void __launch_bounds__(kThreads)
-k_adjoint_step(Dims g, const void* __restrict__ lam_in_, void* __restrict__ lam_out_,
-               const float* __restrict__ d, const GT* __restrict__ gj,
-               const GT* __restrict__ gj1, float* __restrict__ b, float w_j, float w_j1,
-               float dt) {
-    const int idx = blockIdx.x * kThreads + threadIdx.x;
-    if (idx >= g.n) return;
-    int i1, i2, i3;
-    unflatten(g, idx, i1, i2, i3);
-    const long long n = g.n;
-    Stencil s;
-    make_stencil(s, g, i1, i2, i3, d[idx], d[n + idx], d[2 * n + idx]);
-    float lam_new, lam_old;
-    if (COMP) {
-        const float2* lin = reinterpret_cast<const float2*>(lam_in_);
-        const float2 own = lin[idx];
-        const float2 nf = gather2_prod(s, lin);
-        const float nu_star = fmaf(dt, nf.y, nf.x);
-        lam_new = fmaf(0.5f * dt, nf.y + nu_star * own.y, nf.x);
-        lam_old = own.x;
-        reinterpret_cast<float2*>(lam_out_)[idx] = make_float2(lam_new, own.y);
-    } else {
-        const float* lin = reinterpret_cast<const float*>(lam_in_);
-        lam_new = gather1(s, lin);
-        lam_old = FIRST ? lin[idx] : 0.f;
-        reinterpret_cast<float*>(lam_out_)[idx] = lam_new;
-    }
-    const float c = w_j * lam_new;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        float acc = c * ld(gj, k * n + idx);
-        if (FIRST) acc = fmaf(w_j1 * lam_old, ld(gj1, k * n + idx), acc);
-        else acc += b[k * n + idx];
-        b[k * n + idx] = acc;
-    }
-}
-
-// Incremental state step (Eq. inc-state, Algorithm 2):
-// rho~_{j+1} = I[rho~_j](X) + dt/2 (I[f_j](X) + f_{j+1}(x)), f = -v~ . grad rho.
-template <bool FINAL, bool COMP, typename GT>
-__global__ void __launch_bounds__(kThreads)
-k_incstate_step(Dims g, const float2* __restrict__ in, void* __restrict__ out_,
-                const float* __restrict__ d, const float* __restrict__ vt,
-                const GT* __restrict__ gj1, const float* __restrict__ divv, float dt) {
-    const int idx = blockIdx.x * kThreads + threadIdx.x;
-    if (idx >= g.n) return;
-    int i1, i2, i3;
-    unflatten(g, idx, i1, i2, i3);
-    const long long n = g.n;
-    Stencil s;
-    make_stencil(s, g, i1, i2, i3, d[idx], d[n + idx], d[2 * n + idx]);
-    const float2 nf = gather2(s, in);
-    const float f1 = -(vt[idx] * ld(gj1, idx) + vt[n + idx] * ld(gj1, n + idx) +
-                       vt[2 * n + idx] * ld(gj1, 2 * n + idx));
-    const float r = fmaf(0.5f * dt, nf.y + f1, nf.x);
-    if (!FINAL) {
-        reinterpret_cast<float2*>(out_)[idx] = make_float2(r, f1);
-    } else if (COMP) {
-        reinterpret_cast<float2*>(out_)[idx] = make_float2(-r, divv[idx]);
-    } else {
-        reinterpret_cast<float*>(out_)[idx] = -r;
-    }
-}
-
-template <typename GT>
-__global__ void __launch_bounds__(kThreads)
-k_incstate_init(Dims g, const float* __restrict__ vt, const GT* __restrict__ g0,
-                float2* __restrict__ out) {
-    const int idx = blockIdx.x * kThreads + threadIdx.x;
-    if (idx >= g.n) return;
-    const long long n = g.n;
-    const float f0 = -(vt[idx] * ld(g0, idx) + vt[n + idx] * ld(g0, n + idx) +
-                       vt[2 * n + idx] * ld(g0, 2 * n + idx));
-    out[idx] = make_float2(0.f, f0);
-}
-
-__global__ void k_pack2(int n, const float* __restrict__ a, const float* __restrict__ b,
-                        float2* __restrict__ out) {
-    const int idx = blockIdx.x * kThreads + threadIdx.x;
-    if (idx < n) out[idx] = make_float2(a[idx], b[idx]);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -214,6 +82,314 @@ k_deformation_step(Dims g, const float* __restrict__ u_in, const float* __restri
     }
 }
 
+// ---------------------------------------------------- x1-marching kernels
+
+__device__ __forceinline__ double block_sum(double v) {
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int lane = tid & 31, wid = tid >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        s = lane < nw ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    return s;   // valid in thread 0
+}
+
+// i mod n for i in [-n, 2n) with two compares; any other i through wrap().
+__device__ __forceinline__ int wrap_near(int i, int n) {
+    if (i < 0) i += n;
+    else if (i >= n) i -= n;
+    if ((unsigned)i >= (unsigned)n) i = wrap(i, n);
+    return i;
+}
+
+struct Window {
+    float w[4][16];   // four x1-planes of 4 (x2) x 4 (x3) stencil values
+    int off;          // wrapped x2 base * n3 + wrapped x3 base (interior stencils)
+    int o2[4], o3[4]; // per-node offsets, for stencils that wrap in x2 or x3
+    bool interior;    // no wrap in x2 and x3: rows are off + b n3, columns + c
+    int cp, cb2, cb3; // unwrapped plane of node -1, x2 and x3 bases of the cache
+};
+
+template <int SLOT>
+__device__ __forceinline__ void load_plane(Window& W, const float* __restrict__ f,
+                                           const Dims& g, int plane) {
+    const float* base = f + (long long)wrap_near(plane, g.n1) * g.n23;
+    if (W.interior) {
+        const float* q = base + W.off;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const float* row = q + b * g.n3;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) W.w[SLOT][b * 4 + c] = __ldg(row + c);
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) W.w[SLOT][b * 4 + c] = __ldg(base + W.o2[b] + W.o3[c]);
+    }
+}
+
+// One marching step at rotation R: interpolate f at the point (i1, i2, i3) +
+// (d1, d2, d3) using and updating the window.
+template <int R>
+__device__ __forceinline__ float march_interp(Window& W, const float* __restrict__ f,
+                                              const Dims& g, int i1, int i2, int i3, float d1,
+                                              float d2, float d3) {
+    const float fl1 = floorf(d1), fl2 = floorf(d2), fl3 = floorf(d3);
+    float w1[4], w2[4], w3[4];
+    lagrange4(d1 - fl1, w1);
+    lagrange4(d2 - fl2, w2);
+    lagrange4(d3 - fl3, w3);
+    const int p = i1 + (int)fl1 - 1;
+    const int b2 = i2 + (int)fl2 - 1;
+    const int b3 = i3 + (int)fl3 - 1;
+    if (!(b2 == W.cb2 && b3 == W.cb3 && p == W.cp + 1)) {
+        const int q2 = wrap_near(b2, g.n2), q3 = wrap_near(b3, g.n3);
+        W.interior = (q2 <= g.n2 - 4) && (q3 <= g.n3 - 4);
+        W.off = q2 * g.n3 + q3;
+        if (!W.interior) {
+            int r2 = q2, r3 = q3;
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                W.o2[a] = r2 * g.n3;
+                W.o3[a] = r3;
+                r2 = (r2 + 1 == g.n2) ? 0 : r2 + 1;
+                r3 = (r3 + 1 == g.n3) ? 0 : r3 + 1;
+            }
+        }
+        W.cb2 = b2;
+        W.cb3 = b3;
+        load_plane<(R + 0) & 3>(W, f, g, p);
+        load_plane<(R + 1) & 3>(W, f, g, p + 1);
+        load_plane<(R + 2) & 3>(W, f, g, p + 2);
+    }
+    W.cp = p;
+    load_plane<(R + 3) & 3>(W, f, g, p + 3);
+    float val = 0.f;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const float* pl = W.w[(R + a) & 3];
+        float r = 0.f;
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            float s = w3[0] * pl[b * 4 + 0];
+            s = fmaf(w3[1], pl[b * 4 + 1], s);
+            s = fmaf(w3[2], pl[b * 4 + 2], s);
+            s = fmaf(w3[3], pl[b * 4 + 3], s);
+            r = fmaf(w2[b], s, r);
+        }
+        val = fmaf(w1[a], r, val);
+    }
+    return val;
+}
+
+// Epilogues: pre(idx) loads the per-point inputs that do not depend on the
+// gather (issued four points ahead of use), post(idx, val, pre, acc)
+// finishes the point, done(acc) runs once per thread after the march (all
+// threads of the block, for reductions).
+
+struct EpiStore {            // out = val
+    float* out;
+    struct Pre {};
+    __device__ Pre pre(int) const { return {}; }
+    __device__ void post(int idx, float val, const Pre&, double&) const { out[idx] = val; }
+    __device__ void done(double) const {}
+};
+
+struct EpiStateFinal {       // out = val; lam = rho_R - val; sum (val - rho_R)^2
+    float* out;
+    const float* rho_R;
+    float* lam;              // may be null
+    double* partials;
+    struct Pre { float r; };
+    __device__ Pre pre(int idx) const { return {__ldg(rho_R + idx)}; }
+    __device__ void post(int idx, float val, const Pre& p, double& acc) const {
+        out[idx] = val;
+        const float l = p.r - val;
+        if (lam) lam[idx] = l;
+        acc += (double)l * (double)l;
+    }
+    __device__ void done(double acc) const {
+        const double s = block_sum(acc);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    }
+};
+
+struct EpiAdjoint {          // lam_out = c(x) val
+    float* out;
+    const float* c;          // may be null (c = 1)
+    struct Pre { float c; };
+    __device__ Pre pre(int idx) const { return {c ? __ldg(c + idx) : 1.f}; }
+    __device__ void post(int idx, float val, const Pre& p, double&) const { out[idx] = p.c * val; }
+    __device__ void done(double) const {}
+};
+
+struct EpiCoef {             // c = 1 + dt/2 (dX + dv + dt dX dv), val = dX
+    float* out;
+    const float* divv;
+    float dt;
+    struct Pre { float dv; };
+    __device__ Pre pre(int idx) const { return {__ldg(divv + idx)}; }
+    __device__ void post(int idx, float val, const Pre& p, double&) const {
+        out[idx] = 1.f + 0.5f * dt * (val + p.dv + dt * val * p.dv);
+    }
+    __device__ void done(double) const {}
+};
+
+template <typename GT>
+struct EpiIncState {         // u_{j+1} = val + dt f_{j+1}; final: lam~ = -(val + dt/2 f_nt)
+    float* out;
+    const float* vt;
+    const GT* gj1;
+    long long n;
+    float dt;
+    int final_step;
+    struct Pre { float v0, v1, v2, g0, g1, g2; };
+    __device__ Pre pre(int idx) const {
+        return {__ldg(vt + idx), __ldg(vt + n + idx), __ldg(vt + 2 * n + idx),
+                ld(gj1, idx), ld(gj1, n + idx), ld(gj1, 2 * n + idx)};
+    }
+    __device__ void post(int idx, float val, const Pre& p, double&) const {
+        const float f = -(p.v0 * p.g0 + p.v1 * p.g1 + p.v2 * p.g2);
+        out[idx] = final_step ? -fmaf(0.5f * dt, f, val) : fmaf(dt, f, val);
+    }
+    __device__ void done(double) const {}
+};
+
+// Per-point inputs of one marching point, loaded ahead of use.
+template <class Epi>
+struct Ahead {
+    float d1, d2, d3;
+    typename Epi::Pre pre;
+};
+
+template <class Epi>
+__device__ __forceinline__ void fetch(Ahead<Epi>& a, const float* __restrict__ d, const Dims& g,
+                                      const Epi& epi, int i1, int i2, int i3) {
+    const long long n = g.n;
+    const int idx = (i1 * g.n2 + i2) * g.n3 + i3;
+    a.d1 = __ldg(d + idx);
+    a.d2 = __ldg(d + n + idx);
+    a.d3 = __ldg(d + 2 * n + idx);
+    a.pre = epi.pre(idx);
+}
+
+// Point k = k0 + R of the thread's column: use the inputs fetched two points
+// earlier into slot R & 1, refill it with point k + 2, interpolate, finish.
+template <int R, class Epi>
+__device__ __forceinline__ void march_point(Window& W, Ahead<Epi> (&ah)[2],
+                                            const float* __restrict__ f,
+                                            const float* __restrict__ d, const Dims& g,
+                                            const Epi& epi, int i1b, int k0, int kend, int i2,
+                                            int i3, double& acc) {
+    const int k = k0 + R;
+    if (k >= kend) return;
+    const Ahead<Epi> cur = ah[R & 1];
+    if (k + 2 < kend) fetch(ah[R & 1], d, g, epi, i1b + k + 2, i2, i3);
+    const int i1 = i1b + k;
+    const int idx = (i1 * g.n2 + i2) * g.n3 + i3;
+    const float val = march_interp<R>(W, f, g, i1, i2, i3, cur.d1, cur.d2, cur.d3);
+    epi.post(idx, val, cur.pre, acc);
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(256)
+k_march(Dims g, int K, const float* __restrict__ f, const float* __restrict__ d, Epi epi) {
+    const int i3 = blockIdx.x * 32 + threadIdx.x;
+    const int i2 = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i1b = blockIdx.z * K;
+    double acc = 0.0;
+    if (i3 < g.n3 && i2 < g.n2) {
+        const int kend = min(K, g.n1 - i1b);
+        Window W;
+        W.cp = INT_MIN / 2;
+        W.cb2 = INT_MIN / 2;
+        W.cb3 = INT_MIN / 2;
+        W.interior = false;
+        W.off = 0;
+        Ahead<Epi> ah[2];
+        if (0 < kend) fetch(ah[0], d, g, epi, i1b + 0, i2, i3);
+        if (1 < kend) fetch(ah[1], d, g, epi, i1b + 1, i2, i3);
+        for (int k0 = 0; k0 < kend; k0 += 4) {
+            march_point<0>(W, ah, f, d, g, epi, i1b, k0, kend, i2, i3, acc);
+            march_point<1>(W, ah, f, d, g, epi, i1b, k0, kend, i2, i3, acc);
+            march_point<2>(W, ah, f, d, g, epi, i1b, k0, kend, i2, i3, acc);
+            march_point<3>(W, ah, f, d, g, epi, i1b, k0, kend, i2, i3, acc);
+        }
+    }
+    epi.done(acc);
+}
+
+dim3 march_grid(const Dims& g, Tile t) {
+    return dim3((g.n3 + 31) / 32, (g.n2 + t.wy - 1) / t.wy, (g.n1 + t.k - 1) / t.k);
+}
+
+template <class Epi>
+cudaError_t run_march(const Dims& g, Tile t, const float* f, const float* d, const Epi& epi,
+                      cudaStream_t st) {
+    if (t.k < 4 || (t.k & 3) || t.wy < 1 || 32 * t.wy > 256) return cudaErrorInvalidValue;
+    k_march<Epi><<<march_grid(g, t), dim3(32, t.wy), 0, st>>>(g, t.k, f, d, epi);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------- streaming kernels
+
+template <typename GT>
+__global__ void __launch_bounds__(kThreads)
+k_incstate_init(Dims g, const float* __restrict__ vt, const GT* __restrict__ g0, float dt,
+                float* __restrict__ u0) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;
+    if (idx >= g.n) return;
+    const long long n = g.n;
+    const float f0 = -(vt[idx] * ld(g0, idx) + vt[n + idx] * ld(g0, n + idx) +
+                       vt[2 * n + idx] * ld(g0, 2 * n + idx));
+    u0[idx] = 0.5f * dt * f0;
+}
+
+// out[c] = base[c] + sum_j w_j lam_j grad_j[c] (trapezoid w), optional <dotp, out>.
+template <typename GT>
+__global__ void __launch_bounds__(kThreads)
+k_time_integral(Dims g, int nt, const float* __restrict__ lam, const GT* __restrict__ grad,
+                const float* __restrict__ base, float* __restrict__ out,
+                const float* __restrict__ dotp, double* __restrict__ partials) {
+    const long long n = g.n;
+    const float dt = 1.f / (float)nt;
+    double acc = 0.0;
+    for (long long idx = (long long)blockIdx.x * kThreads + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * kThreads) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+        if (base) { s0 = base[idx]; s1 = base[n + idx]; s2 = base[2 * n + idx]; }
+        for (int j = 0; j <= nt; ++j) {
+            const float w = (j == 0 || j == nt) ? 0.5f * dt : dt;
+            const float l = w * __ldg(lam + (long long)j * n + idx);
+            const GT* gj = grad + (long long)j * 3 * n;
+            s0 = fmaf(l, ld(gj, idx), s0);
+            s1 = fmaf(l, ld(gj, n + idx), s1);
+            s2 = fmaf(l, ld(gj, 2 * n + idx), s2);
+        }
+        out[idx] = s0;
+        out[n + idx] = s1;
+        out[2 * n + idx] = s2;
+        if (dotp)
+            acc += (double)dotp[idx] * s0 + (double)dotp[n + idx] * s1 +
+                   (double)dotp[2 * n + idx] * s2;
+    }
+    if (dotp) {
+        const double s = block_sum(acc);
+        if (threadIdx.x == 0) partials[blockIdx.x] = s;
+    }
+}
+
 __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
                           long long count) {
     long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
@@ -230,6 +406,11 @@ __global__ void k_from_bf16(const __nv_bfloat16* __restrict__ in, float* __restr
 
 }  // namespace
 
+int march_blocks(const Dims& g, Tile t) {
+    const dim3 gr = march_grid(g, t);
+    return (int)(gr.x * gr.y * gr.z);
+}
+
 cudaError_t launch_departure(const Dims& g, const float* v, float dt, float* d_fwd,
                              float* d_adj, cudaStream_t st) {
     const float two_pi = 6.283185307179586f;
@@ -238,89 +419,70 @@ cudaError_t launch_departure(const Dims& g, const float* v, float dt, float* d_f
     return cudaGetLastError();
 }
 
-cudaError_t launch_interp(const Dims& g, const float* field, int nfields, const float* disp,
-                          float* out, cudaStream_t st) {
-    k_interp<<<nblocks(g.n), kThreads, 0, st>>>(g, field, nfields, disp, out);
-    return cudaGetLastError();
+cudaError_t launch_interp(const Dims& g, Tile t, const float* f, const float* d, float* out,
+                          cudaStream_t st) {
+    return run_march(g, t, f, d, EpiStore{out}, st);
 }
 
-cudaError_t launch_state_step(const Dims& g, const float* rho_in, const float* d,
-                              float* rho_out, const float* rho_R, const float* divv,
-                              void* lam_out, double* partials, int nblk_partials,
+cudaError_t launch_state_step(const Dims& g, Tile t, const float* rho_in, const float* d,
+                              float* rho_out, const float* rho_R, float* lam_out,
+                              double* partials, int max_partials, int* nblk_out,
                               cudaStream_t st) {
-    const int nb = nblocks(g.n);
-    if (rho_R) {
-        if (nb > nblk_partials) return cudaErrorInvalidValue;
-        k_state_step<true><<<nb, kThreads, 0, st>>>(g, rho_in, d, rho_out, rho_R, divv,
-                                                    lam_out, partials);
-    } else {
-        k_state_step<false><<<nb, kThreads, 0, st>>>(g, rho_in, d, rho_out, nullptr,
-                                                     nullptr, nullptr, nullptr);
-    }
-    return cudaGetLastError();
+    if (!rho_R) return run_march(g, t, rho_in, d, EpiStore{rho_out}, st);
+    const int nb = march_blocks(g, t);
+    if (nb > max_partials) return cudaErrorInvalidValue;
+    if (nblk_out) *nblk_out = nb;
+    return run_march(g, t, rho_in, d, EpiStateFinal{rho_out, rho_R, lam_out, partials}, st);
 }
 
-template <typename GT>
-static void adjoint_dispatch(const Dims& g, const AdjointStepArgs& a, const GT* gj,
-                             const GT* gj1, cudaStream_t st) {
-    const int nb = nblocks(g.n);
-    if (a.compressible) {
-        if (a.first)
-            k_adjoint_step<true, true, GT><<<nb, kThreads, 0, st>>>(
-                g, a.lam_in, a.lam_out, a.d, gj, gj1, a.b, a.w_j, a.w_j1, a.dt);
-        else
-            k_adjoint_step<true, false, GT><<<nb, kThreads, 0, st>>>(
-                g, a.lam_in, a.lam_out, a.d, gj, gj1, a.b, a.w_j, a.w_j1, a.dt);
-    } else {
-        if (a.first)
-            k_adjoint_step<false, true, GT><<<nb, kThreads, 0, st>>>(
-                g, a.lam_in, a.lam_out, a.d, gj, gj1, a.b, a.w_j, a.w_j1, a.dt);
-        else
-            k_adjoint_step<false, false, GT><<<nb, kThreads, 0, st>>>(
-                g, a.lam_in, a.lam_out, a.d, gj, gj1, a.b, a.w_j, a.w_j1, a.dt);
-    }
+// Eq. (sml-advection) for the adjoint source f = lam div v with
+// f_0 = nu_0 (div v)(X): lam_new = nu_0 + dt/2 (nu_0 dX + (nu_0 + dt nu_0 dX) dv)
+// = c(x) nu_0 with c = 1 + dt/2 (dX + dv + dt dX dv), fixed for a given v.
+cudaError_t launch_adjoint_step(const Dims& g, Tile t, const float* lam_in, const float* d,
+                                const float* c, float* lam_out, cudaStream_t st) {
+    return run_march(g, t, lam_in, d, EpiAdjoint{lam_out, c}, st);
 }
 
-cudaError_t launch_adjoint_step(const Dims& g, const AdjointStepArgs& a, cudaStream_t st) {
-    if (a.grad_j_bf) adjoint_dispatch(g, a, a.grad_j_bf, a.grad_j1_bf, st);
-    else adjoint_dispatch(g, a, a.grad_j, a.grad_j1, st);
-    return cudaGetLastError();
+cudaError_t launch_adjoint_coef(const Dims& g, Tile t, const float* divv, const float* d_adj,
+                                float dt, float* c, cudaStream_t st) {
+    return run_march(g, t, divv, d_adj, EpiCoef{c, divv, dt}, st);
 }
 
-template <typename GT>
-static void incstate_dispatch(const Dims& g, const IncStateStepArgs& a, const GT* gj1,
-                              cudaStream_t st) {
-    const int nb = nblocks(g.n);
-    if (!a.final_step)
-        k_incstate_step<false, false, GT><<<nb, kThreads, 0, st>>>(g, a.in, a.out, a.d, a.vt,
-                                                                   gj1, a.divv, a.dt);
-    else if (a.compressible)
-        k_incstate_step<true, true, GT><<<nb, kThreads, 0, st>>>(g, a.in, a.out, a.d, a.vt,
-                                                                 gj1, a.divv, a.dt);
-    else
-        k_incstate_step<true, false, GT><<<nb, kThreads, 0, st>>>(g, a.in, a.out, a.d, a.vt,
-                                                                  gj1, a.divv, a.dt);
-}
-
-cudaError_t launch_incstate_step(const Dims& g, const IncStateStepArgs& a, cudaStream_t st) {
-    if (a.grad_j1_bf) incstate_dispatch(g, a, a.grad_j1_bf, st);
-    else incstate_dispatch(g, a, a.grad_j1, st);
-    return cudaGetLastError();
+// Algorithm 2 step rho~_{j+1} = I[rho~_j](X) + dt/2 (I[f_j](X) + f_{j+1}(x)).
+// The interpolant is linear in the field, so with u_j = rho~_j + dt/2 f_j:
+// rho~_{j+1} = I[u_j](X) + dt/2 f_{j+1}(x) and u_{j+1} = I[u_j](X) + dt f_{j+1}(x).
+cudaError_t launch_incstate_step(const Dims& g, Tile t, const float* u_in, const float* d,
+                                 const float* vt, const float* grad_j1,
+                                 const __nv_bfloat16* grad_j1_bf, float dt, int final_step,
+                                 float* out, cudaStream_t st) {
+    if (grad_j1_bf)
+        return run_march(g, t, u_in, d,
+                         EpiIncState<__nv_bfloat16>{out, vt, grad_j1_bf, g.n, dt, final_step},
+                         st);
+    return run_march(g, t, u_in, d, EpiIncState<float>{out, vt, grad_j1, g.n, dt, final_step},
+                     st);
 }
 
 cudaError_t launch_incstate_init(const Dims& g, const float* vt, const float* grad0,
-                                 const __nv_bfloat16* grad0_bf, float2* out,
+                                 const __nv_bfloat16* grad0_bf, float dt, float* u0,
                                  cudaStream_t st) {
     if (grad0_bf)
-        k_incstate_init<<<nblocks(g.n), kThreads, 0, st>>>(g, vt, grad0_bf, out);
+        k_incstate_init<<<nblocks(g.n), kThreads, 0, st>>>(g, vt, grad0_bf, dt, u0);
     else
-        k_incstate_init<<<nblocks(g.n), kThreads, 0, st>>>(g, vt, grad0, out);
+        k_incstate_init<<<nblocks(g.n), kThreads, 0, st>>>(g, vt, grad0, dt, u0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack2(const Dims& g, const float* lam, const float* divv, float2* out,
-                         cudaStream_t st) {
-    k_pack2<<<nblocks(g.n), kThreads, 0, st>>>(g.n, lam, divv, out);
+cudaError_t launch_time_integral(const Dims& g, int nt, const float* lam, const float* grad,
+                                 const __nv_bfloat16* grad_bf, const float* base, float* out,
+                                 const float* dotp, double* partials, int nblk,
+                                 cudaStream_t st) {
+    if (grad_bf)
+        k_time_integral<<<nblk, kThreads, 0, st>>>(g, nt, lam, grad_bf, base, out, dotp,
+                                                   partials);
+    else
+        k_time_integral<<<nblk, kThreads, 0, st>>>(g, nt, lam, grad, base, out, dotp,
+                                                   partials);
     return cudaGetLastError();
 }
 

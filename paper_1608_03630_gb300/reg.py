@@ -92,6 +92,8 @@ _SIGS = {
     'reg_gaussian_smooth': [_P, _P, _P, _D, _D, _D],
     'reg_inner': [_P, _P, _P, ctypes.c_size_t, ctypes.POINTER(_D)],
     'reg_set_timing': [_P, _I],
+    'reg_set_tile': [_P, _I, _I],
+    'reg_get_tile': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_get_timing': [_P, ctypes.POINTER(Timing)],
 }
 
@@ -298,6 +300,14 @@ class Registration:
         out = ctypes.c_double()
         self._call('reg_inner', _ptr(a), _ptr(b), ctypes.c_size_t(a.numel()), ctypes.byref(out))
         return out.value
+
+    def set_tile(self, k, wy):
+        self._call('reg_set_tile', int(k), int(wy))
+
+    def get_tile(self):
+        k, wy = ctypes.c_int(), ctypes.c_int()
+        self._call('reg_get_tile', ctypes.byref(k), ctypes.byref(wy))
+        return k.value, wy.value
 
     def set_timing(self, on):
         self._call('reg_set_timing', 1 if on else 0)

@@ -1,9 +1,13 @@
 """GPU parity: every step of the path through the C-ABI against the FP64 oracle.
 
-Sizes span several thread blocks and ragged tails (no dimension a multiple of
-the 256-thread block or of 32).  Tolerances: the FP32 kernels against the
-FP64 oracle at 1e-5 relative (single steps) and the gradient and Hessian
-matvec at 1e-4 relative L2 (the stated target for the FP32 path).
+Both sides see the same inputs: every array is rounded to FP32 once and the
+oracle runs in FP64 on those rounded values.  Sizes span several thread
+blocks and ragged tails (no dimension a multiple of 32 or of the x1 tile).
+Tolerances: single steps at 1e-5 relative; the gradient and the Hessian
+matvec at 1e-4 relative L2 (the stated target for the FP32 path); operators
+with the biharmonic symbol, which multiplies FP32 FFT roundoff in modes
+outside the band of the input by up to (|k|max/|k|band)^4, at the bound that
+ratio gives.
 """
 
 import numpy as np
@@ -37,6 +41,11 @@ def dev(a):
     return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device='cuda')
 
 
+def f32(a):
+    """The FP32 value the GPU receives, as FP64 for the oracle."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
 def host(t):
     torch.cuda.synchronize()
     return t.detach().cpu().double().numpy()
@@ -49,7 +58,7 @@ def rel(a, b):
 @pytest.mark.parametrize('shape', SHAPES)
 def test_departure_points(reg, shape):
     nt = 4
-    v = 2.5 * synth.bandlimited(shape, 3, 7)      # several cells per step
+    v = f32(2.5 * synth.bandlimited(shape, 3, 7))      # several cells per step
     R = reg.Registration(shape, nt, 1e-2)
     df, da = R.departure(dev(v))
     ef = otr.departure(v, 1.0 / nt)
@@ -63,9 +72,9 @@ def test_departure_points(reg, shape):
 @pytest.mark.parametrize('nf', [1, 2, 3])
 def test_interpolation_with_large_displacements(reg, shape, nf):
     rng = np.random.default_rng(11)
-    f = synth.bandlimited(shape, 5, 13, ncomp=nf)
+    f = f32(synth.bandlimited(shape, 5, 13, ncomp=nf))
     # displacements up to +-1.5 N: exercises the periodic wrap, CFL >> 1
-    d = np.stack([rng.uniform(-1.5 * n, 1.5 * n, shape) for n in shape])
+    d = f32(np.stack([rng.uniform(-1.5 * n, 1.5 * n, shape) for n in shape]))
     R = reg.Registration(shape, 4, 1e-2)
     out = host(R.interp(dev(f), dev(d)))
     for c in range(nf):
@@ -77,7 +86,7 @@ def test_interpolation_with_large_displacements(reg, shape, nf):
 def test_interpolation_exact_at_integer_displacements(reg):
     shape = (24, 20, 36)
     rng = np.random.default_rng(3)
-    f = rng.standard_normal(shape)
+    f = f32(rng.standard_normal(shape))
     d = np.stack([rng.integers(-50, 50, shape) for _ in range(3)]).astype(float)
     R = reg.Registration(shape, 4, 1e-2)
     out = host(R.interp(dev(f[None]), dev(d)))[0]
@@ -89,8 +98,8 @@ def test_interpolation_exact_at_integer_displacements(reg):
 def test_state_transport(reg, shape):
     nt = 4
     v = 1.5 * synth.bandlimited(shape, 2, 21)
-    rho0 = synth.bandlimited(shape, 4, 22, ncomp=None)
-    d = otr.departure(v, 1.0 / nt)
+    rho0 = f32(synth.bandlimited(shape, 4, 22, ncomp=None))
+    d = f32(otr.departure(v, 1.0 / nt))
     R = reg.Registration(shape, nt, 1e-2)
     hist = host(R.state_transport(dev(rho0), dev(d)))
     exp = otr.state_solve(rho0, d, nt)
@@ -101,8 +110,8 @@ def test_state_transport(reg, shape):
 
 @pytest.mark.parametrize('shape', [(32, 32, 32), (20, 28, 44)])
 def test_spectral_operators(reg, shape):
-    f = synth.bandlimited(shape, 6, 31, ncomp=None)
-    v = synth.bandlimited(shape, 6, 32)
+    f = f32(synth.bandlimited(shape, 6, 31, ncomp=None))
+    v = f32(synth.bandlimited(shape, 6, 32))
     beta = 3e-3
     for kind in ('H2', 'H1'):
         for incompressible in (False, True):
@@ -138,7 +147,15 @@ def _problem_case(shape, kind, incompressible, beta, nt, at_vstar):
     v = vs if at_vstar else 0.3 * synth.bandlimited(shape, 2, 51)
     if incompressible:
         v = osp.leray(v)
-    return rho_T, rho_R, v
+    return f32(rho_T), f32(rho_R), f32(v)
+
+
+def _gradient_tol(shape, beta, kind, v, g_ref):
+    """1e-4 relative, plus the FP32 FFT roundoff of v amplified by beta A:
+    about 1e-7 * beta * max A(k) * ||v|| against ||g||."""
+    k2 = sum((n // 2) ** 2 for n in shape)
+    amax = k2 * k2 if kind == 'H2' else k2
+    return 1e-4 + 3e-7 * beta * amax * np.linalg.norm(v) / np.linalg.norm(g_ref)
 
 
 CASES = [
@@ -159,13 +176,14 @@ def test_gradient_and_matvec(reg, shape, kind, incompressible, beta, nt, at_vsta
     R = reg.Registration(shape, nt, beta, kind, incompressible)
     R.set_images(dev(rho_T), dev(rho_R))
     g, J = R.gradient(dev(v))
-    assert rel(host(g), g_ref) < 1e-4
+    assert rel(host(g), g_ref) < _gradient_tol(shape, beta, kind, v, g_ref)
     assert abs(J - J_ref) < 1e-5 * abs(J_ref)
     assert abs(R.objective(dev(v)) - J_ref) < 1e-5 * abs(J_ref)
     for s in range(5):
         w = synth.bandlimited(shape, 8, 1001 + s)
         if incompressible:
             w = osp.leray(w)
+        w = f32(w)
         h = R.hessian_matvec(dev(w))
         assert rel(host(h), P.hessian_matvec(w)) < 1e-4, s
     R.close()
@@ -184,9 +202,9 @@ def test_matvec_before_gradient_is_refused(reg):
 def test_zero_velocity_closed_form(reg):
     # H(0) w = beta A w + (w . grad rho_T) grad rho_T; g(0) = (rho_R - rho_T) grad rho_T
     shape = (20, 28, 44)
-    rho_T = synth.bandlimited(shape, 3, 61, ncomp=None)
-    rho_R = synth.bandlimited(shape, 3, 62, ncomp=None)
-    w = synth.bandlimited(shape, 6, 63)
+    rho_T = f32(synth.bandlimited(shape, 3, 61, ncomp=None))
+    rho_R = f32(synth.bandlimited(shape, 3, 62, ncomp=None))
+    w = f32(synth.bandlimited(shape, 6, 63))
     R = reg.Registration(shape, 4, 1e-2)
     R.set_images(dev(rho_T), dev(rho_R))
     g, _ = R.gradient(torch.zeros((3,) + shape, device='cuda'))
@@ -194,25 +212,26 @@ def test_zero_velocity_closed_form(reg):
     assert rel(host(g), (rho_R - rho_T) * gr) < 1e-5
     h = host(R.hessian_matvec(dev(w)))
     exp = 1e-2 * osp.apply_regularisation(w, 'H2') + np.sum(w * gr, 0) * gr
-    assert rel(h, exp) < 1e-5
+    assert rel(h, exp) < 5e-5     # H2 term: (|k|max / 6)^4 ~ 40 x FP32 roundoff
     R.close()
 
 
 def test_presmoothing(reg):
     shape = (32, 32, 32)
-    rho_T, rho_R, vs = synth.sinusoid_problem(shape, 0.5)
+    rho_T, rho_R, vs = [f32(a) for a in synth.sinusoid_problem(shape, 0.5)]
     P = opr.Problem(rho_T, rho_R, 4, 1e-2, 'H2', False, presmooth=True)
     g_ref, J_ref = P.gradient(vs)
     R = reg.Registration(shape, 4, 1e-2)
     R.set_images(dev(rho_T), dev(rho_R), presmooth=True)
     g, J = R.gradient(dev(vs))
-    assert rel(host(g), g_ref) < 1e-4 and abs(J - J_ref) < 1e-5 * J_ref
+    assert rel(host(g), g_ref) < _gradient_tol(shape, 1e-2, 'H2', vs, g_ref)
+    assert abs(J - J_ref) < 1e-5 * J_ref
     R.close()
 
 
 def test_three_gauss_newton_steps_match_the_oracle(reg):
     shape = (32, 32, 32)
-    rho_T, rho_R, _ = synth.sinusoid_problem(shape, 0.5)
+    rho_T, rho_R, _ = [f32(a) for a in synth.sinusoid_problem(shape, 0.5)]
     P = opr.Problem(rho_T, rho_R, 4, 1e-2, 'H2', False)
     v_ref, st_ref = oso.gauss_newton(P, np.zeros((3,) + shape), gtol=1e-2, max_gn=3)
     R = reg.Registration(shape, 4, 1e-2)
