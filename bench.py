@@ -10,8 +10,11 @@ is far larger than the 129 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
-Prints one JSON line.  With --impl reference the FP64 CPU oracle is timed
-instead (see cpu_reference()).
+Prints one JSON line.  The timed region runs with the library's per-launch
+CUDA events on (they are captured into the PCG graph and read after every
+replay), which give the per-phase device times and the roofline figures.
+With --impl reference the FP64 CPU oracle is timed instead (see
+cpu_reference()).
 """
 
 import argparse
@@ -91,6 +94,25 @@ class ClockSampler:
         return {'sm_mhz': statistics.median(sm) if sm else None,
                 'sm_max_mhz': max(smax) if smax else None, 'reasons': reasons,
                 'samples': len(sm)}
+
+
+def measured_traffic(phase, points):
+    """DRAM bytes per launch of an interpolation kernel, from the committed
+    ncu summary (bytes per point at 192^3, scaled to `points`), or None when
+    the kernel source has changed since the capture."""
+    import hashlib
+    import re
+    try:
+        with open(os.path.join(ROOT, 'profiles', 'traffic_march_phantom192.md')) as f:
+            text = f.read()
+        with open(os.path.join(ROOT, 'paper_1608_03630_gb300', 'csrc', 'transport.cu'), 'rb') as f:
+            sha = hashlib.sha1(f.read()).hexdigest()[:12]
+        if ('sha1 ' + sha) not in text:
+            return None
+        m = re.search(r'traffic_bytes_per_point %s: ([0-9.]+)' % phase, text)
+        return float(m.group(1)) * points if m else None
+    except OSError:
+        return None
 
 
 def make_inputs(shape=SHAPE, seed=SEED):
@@ -279,7 +301,8 @@ def gpu_bench(args):
         'phase_ms_per_step': {k: v['ms'] / args.steps for k, v in timing.items()},
         'roofline': {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': peak,
                      'unit': 'GB/s', 'frac': achieved / peak, 'peak_source': peak_kind,
-                     'traffic': None},
+                     'bytes_per_launch': d['bytes'] / max(1, d['launches']),
+                     'traffic': measured_traffic(dom, n)},
         'gpu_launches': launches,
         'clocks': clk,
         'e2e': {'value': e2e_s, 'unit': UNIT, 'h2d_bytes_per_step': 4 * n * 2 + 12 * n,
@@ -292,6 +315,28 @@ def gpu_bench(args):
         dist.destroy_process_group()
 
 
+def profile_matvec(n, nt, count):
+    """A short, fixed launch sequence for ncu captures: one gradient and
+    `count` Hessian matvecs of the phantom problem at n^3 (no timing)."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1608_03630_gb300 import reg, synth
+    shape = (n, n, n)
+    rho_T, rho_R, u = synth.phantom_problem(shape, SEED)
+    w = synth.bandlimited(shape, 6, 1001)
+    R = reg.Registration(shape, nt, BETA, KIND, False)
+    R.set_images(torch.from_numpy(rho_T.astype(np.float32)).cuda(),
+                 torch.from_numpy(rho_R.astype(np.float32)).cuda(), True)
+    R.gradient(torch.from_numpy((0.5 * u).astype(np.float32)).cuda())
+    wt = torch.from_numpy(w.astype(np.float32)).cuda()
+    for _ in range(count):
+        R.hessian_matvec(wt)
+    torch.cuda.synchronize()
+    R.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -300,8 +345,12 @@ def main():
     ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
     ap.add_argument('--precision', default='fp32', choices=['fp32', 'mixed_bf16'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
+    ap.add_argument('--profile-matvec', type=int, default=0, metavar='N',
+                    help='run one gradient and two matvecs at N^3 (nt = 4) for ncu, then exit')
     args = ap.parse_args()
-    if args.impl == 'reference':
+    if args.profile_matvec:
+        profile_matvec(args.profile_matvec, 4, 2)
+    elif args.impl == 'reference':
         cpu_reference(args)
     else:
         gpu_bench(args)

@@ -45,7 +45,10 @@ void phase_begin(reg_ctx* c, cudaEvent_t* ev) {
     }
     *ev = c->free_events.back();
     c->free_events.pop_back();
-    cudaEventRecord(*ev, c->stream);
+    // inside a stream capture an ordinary record only orders streams; an
+    // external record becomes an event node that fires on every replay
+    if (c->capturing) cudaEventRecordWithFlags(*ev, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(*ev, c->stream);
 }
 
 void phase_end(reg_ctx* c, int phase, cudaEvent_t ev, double bytes) {
@@ -57,7 +60,12 @@ void phase_end(reg_ctx* c, int phase, cudaEvent_t ev, double bytes) {
     }
     cudaEvent_t b = c->free_events.back();
     c->free_events.pop_back();
-    cudaEventRecord(b, c->stream);
+    if (c->capturing) cudaEventRecordWithFlags(b, c->stream, cudaEventRecordExternal);
+    else cudaEventRecord(b, c->stream);
+    if (c->capturing) {
+        c->graph_pairs.push_back({phase, ev, b, bytes});
+        return;
+    }
     c->pending.push_back({phase, ev, b, bytes});
     // keep the number of outstanding event pairs bounded
     if (c->pending.size() > 4096) {
@@ -73,6 +81,25 @@ void phase_end(reg_ctx* c, int phase, cudaEvent_t ev, double bytes) {
         }
         c->pending.clear();
     }
+}
+
+int harvest_graph_timing(reg_ctx* c) {
+    for (auto& p : c->graph_pairs) {
+        float ms = 0.f;
+        REG_CK(c, cudaEventElapsedTime(&ms, p.a, p.b));
+        c->acc.ms[p.phase] += ms;
+        c->acc.launches[p.phase] += 1;
+        c->acc.bytes[p.phase] += p.bytes;
+    }
+    return REG_OK;
+}
+
+void release_graph_timing(reg_ctx* c) {
+    for (auto& p : c->graph_pairs) {
+        c->free_events.push_back(p.a);
+        c->free_events.push_back(p.b);
+    }
+    c->graph_pairs.clear();
 }
 
 // RAII helper around one launch.
@@ -428,6 +455,7 @@ static void free_ctx(reg_ctx* c) {
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+    for (auto& p : c->graph_pairs) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto e : c->free_events) cudaEventDestroy(e);
     delete c;
 }

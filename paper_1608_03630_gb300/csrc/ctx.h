@@ -59,8 +59,10 @@ struct reg_ctx {
 
     // timing
     bool timing;
+    bool capturing;       // recording a CUDA graph: event pairs go to graph_pairs
     struct Pending { int phase; cudaEvent_t a, b; double bytes; };
     std::vector<Pending> pending;
+    std::vector<Pending> graph_pairs;   // re-recorded on every replay of the graph
     std::vector<cudaEvent_t> free_events;
     reg_timing acc;
 };
@@ -89,6 +91,10 @@ int fail_cuda(reg_ctx* c, cudaError_t e, const char* what, int line);
 // Phase timing: begin() before a launch, end() after it (no-ops when off).
 void phase_begin(reg_ctx* c, cudaEvent_t* ev);
 void phase_end(reg_ctx* c, int phase, cudaEvent_t ev, double bytes);
+// After a replay of a captured graph has completed: add its event pairs.
+int harvest_graph_timing(reg_ctx* c);
+// When the graph is destroyed: return its events to the pool.
+void release_graph_timing(reg_ctx* c);
 
 // Internal operations (device pointers; all on c->stream).
 int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj);

@@ -99,13 +99,17 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, int ver
 
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
-    if (use_graph && !c->timing) {
+    if (use_graph) {
         // The legacy default stream cannot be captured: capture on the
         // context's own capture stream and replay on the caller's stream.
+        // With timing on, the phase events are captured too and read back
+        // after every replay.
         cudaStream_t user = c->stream;
         REG_TRY(bind_stream(c, c->capture_stream));
         if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            c->capturing = true;
             const int s = pcg_iteration(c);
+            c->capturing = false;
             const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
             if (s != REG_OK || e != cudaSuccess ||
                 cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
@@ -113,6 +117,7 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, int ver
                 if (graph) cudaGraphDestroy(graph);
                 graph = nullptr;
                 exec = nullptr;
+                release_graph_timing(c);
                 c->dead = false;   // a failed capture is not a device fault
                 c->err.clear();
             }
@@ -130,8 +135,12 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, int ver
             status = pcg_iteration(c);
             if (status != REG_OK) break;
         }
-        status = read_scalars(c, SC_PQ, 2);    // PQ, RR
+        status = read_scalars(c, SC_PQ, 2);    // PQ, RR (synchronises the stream)
         if (status != REG_OK) break;
+        if (exec && c->timing) {
+            status = harvest_graph_timing(c);
+            if (status != REG_OK) break;
+        }
         res->iters = it;
         const double pq = c->hsc[SC_PQ], rr = c->hsc[SC_RR];
         if (verbose > 1) {
@@ -159,6 +168,7 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, int ver
     }
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    release_graph_timing(c);
     return status;
 }
 
