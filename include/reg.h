@@ -185,6 +185,27 @@ int reg_interp(reg_ctx* ctx, const float* field, int nfields, const float* disp,
 int reg_state_transport(reg_ctx* ctx, const float* rho0, const float* d_fwd,
                         float* rho_hist);
 
+/* The forward state transport of reg_state_transport, for callers that
+ * cannot allocate device memory (code running during CUDA graph capture,
+ * inside another library's callback, on a fixed memory pool, or in a loop
+ * where a possibly synchronising cudaMalloc is not acceptable).  The paper
+ * has no counterpart: it is a property of this library's interface only.
+ * No context: grid n1 x n2 x n3 (n <= 2^22 points, else REG_EINVAL), nt
+ * steps (1..64) with the points d_fwd [3n]; rho0 [n] -> rho1 [n] = rho(t_nt)
+ * (only the last level; rho0 == rho1 is refused; d_fwd must not overlap
+ * rho1).  Launched on `stream` (a cudaStream_t, NULL = legacy default);
+ * asynchronous.  No cudaMalloc/cudaFree or allocating library call: the one
+ * intermediate level lives in a fixed 16 MiB static device array that every
+ * GPU loading the library keeps until exit.  The first call on a device
+ * looks up that array's address (cudaGetSymbolAddress) with the device
+ * current, so make the first call on each device before any stream capture.
+ * All calls share the array: calls whose GPU work overlaps (other streams,
+ * other threads) race on it; serialise them.  Every element of the array is
+ * written before it is read within a call.  REG_ECUDA on a launch or
+ * set-up failure. */
+int reg_state_transport_noalloc(int n1, int n2, int n3, int nt, const float* rho0,
+                                const float* d_fwd, float* rho1, void* stream);
+
 /* Spectral first derivatives (Sec. III-B1): grad [3n] = grad f (f [n]);
  * div [n] = div v (v [3n]).  Odd derivatives zero the Nyquist mode. */
 int reg_spectral_grad(reg_ctx* ctx, const float* f, float* grad);

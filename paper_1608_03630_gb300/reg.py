@@ -112,6 +112,8 @@ def lib():
             f.restype = ctypes.c_int
         l.reg_last_error.argtypes = [_P]
         l.reg_last_error.restype = ctypes.c_char_p
+        l.reg_state_transport_noalloc.argtypes = [_I, _I, _I, _I, _P, _P, _P, _P]
+        l.reg_state_transport_noalloc.restype = ctypes.c_int
         l.reg_status_string.argtypes = [_I]
         l.reg_status_string.restype = ctypes.c_char_p
         _lib = l
@@ -133,6 +135,21 @@ def _ptr(t, shape=None, what='tensor'):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError('%s has shape %s, expected %s' % (what, tuple(t.shape), tuple(shape)))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def state_transport_noalloc(rho0, d_fwd, rho1, nt, stream=None):
+    """reg_state_transport_noalloc: rho1 = rho(t_nt) from rho0 with the
+    points d_fwd, with no allocation and no context (see include/reg.h)."""
+    shape = tuple(rho0.shape)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    s = lib().reg_state_transport_noalloc(shape[0], shape[1], shape[2], int(nt),
+                                          _ptr(rho0, shape, 'rho0'),
+                                          _ptr(d_fwd, (3,) + shape, 'd_fwd'),
+                                          _ptr(rho1, shape, 'rho1'),
+                                          ctypes.c_void_p(stream.cuda_stream))
+    if s != 0:
+        raise RegError(s, 'reg_state_transport_noalloc failed')
 
 
 class Registration:
