@@ -232,7 +232,7 @@ int reg_inner(reg_ctx* ctx, const float* a, const float* b, size_t count,
 
 /* Tile of the interpolation kernels: each thread walks k points (multiple of
  * 4, 4..64) along x1 and a block is 32 x wy threads (wy in 1, 2, 4, 8) over
- * (x3, x2).  The default is k = 8, wy = 4.  Results do not depend on the tile. */
+ * (x3, x2).  The default is k = 16, wy = 8.  Results do not depend on the tile. */
 int reg_set_tile(reg_ctx* ctx, int k, int wy);
 int reg_get_tile(const reg_ctx* ctx, int* k, int* wy);
 

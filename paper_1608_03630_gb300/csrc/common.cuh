@@ -106,9 +106,18 @@ __device__ __forceinline__ void unflatten(const Dims& g, int idx, int& i1, int& 
 // Tile of the x1-marching interpolation kernels: a block is 32 (x3) x wy (x2)
 // threads and each thread walks k consecutive points along x1.
 struct Tile {
-    int k;    // points per thread along x1 (multiple of 4)
-    int wy;   // threads per block along x2 (1, 2, 4 or 8)
+    int k;          // points per thread along x1 (multiple of 4)
+    int wy;         // threads per block along x2 (1, 2, 4 or 8)
+    int halo = -1;  // bound on |floor(displacement)| (cells) of the launch's
+                    // points; >= 0 selects the shared-memory staged kernel,
+                    // -1 (unknown) the register-window kernel
 };
+
+// Largest shared-memory box (floats) of the staged interpolation kernel.
+constexpr int kMaxBoxFloats = 18432;
+
+// out[0] = max over i < count of |d[i]| as float bits (d: 3 components).
+cudaError_t launch_absmax(const float* d, long long count, unsigned int* out, cudaStream_t st);
 
 // transport.cu
 cudaError_t launch_departure(const Dims& g, const float* v, float dt, float* d_fwd,
@@ -158,6 +167,7 @@ cudaError_t launch_to_bf16(const float* in, __nv_bfloat16* out, long long count,
 cudaError_t launch_from_bf16(const __nv_bfloat16* in, float* out, long long count,
                              cudaStream_t st);
 int march_blocks(const Dims& g, Tile t);   // blocks of one marching launch
+bool tile_staged(const Tile& t);           // t runs the shared-memory staged kernel
 
 // spectral.cu -- multipliers on the half spectrum (cufftComplex = float2).
 // All scale by 1/n (the unnormalised inverse FFT).

@@ -207,6 +207,28 @@ int read_scalars(reg_ctx* c, int first, int count) {
     return REG_OK;
 }
 
+int op_halo(reg_ctx* c, const float* d, int* halo) {
+    REG_CK(c, launch_absmax(d, 3LL * c->g.n, c->dabs, c->stream));
+    unsigned int bits = 0;
+    REG_CK(c, cudaMemcpyAsync(&bits, c->dabs, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+    REG_CK(c, cudaStreamSynchronize(c->stream));
+    float m;
+    memcpy(&m, &bits, sizeof m);
+    if (!std::isfinite(m)) return fail(c, REG_ENONFINITE, "non-finite displacement");
+    *halo = m < 1e6f ? (int)std::ceil(m) : 1000000;
+    return REG_OK;
+}
+
+// The configured tile with a halo; when its staged box does not fit in shared
+// memory, halve k (down to 4) before falling back to the register window.
+Tile tile_with(const reg_ctx* c, int halo) {
+    Tile t = c->tile;
+    t.halo = halo;
+    while (!tile_staged(t) && t.k > 4) t.k = ((t.k / 2) + 3) & ~3;
+    if (!tile_staged(t)) t = c->tile;   // register-window kernel, configured tile
+    return t;
+}
+
 static const float* grad_level(reg_ctx* c, int j) {
     return c->grad_hist ? c->grad_hist + (long long)j * 3 * c->g.n : nullptr;
 }
@@ -219,7 +241,7 @@ static double grad_bytes(reg_ctx* c) { return c->grad_hist_bf ? 6.0 : 12.0; }
 // [(nt+1) n]; otherwise hist holds two ping-pong levels.  The last step
 // writes lam(1) = rho_R - rho(1) to lam_out (if not null) and the mismatch
 // 1/2 ||rho(1) - rho_R||^2_h to dsc[SC_JMIS].
-static int state_solve(reg_ctx* c, const float* d_fwd, float* hist, bool keep_hist,
+static int state_solve(reg_ctx* c, const float* d_fwd, int halo, float* hist, bool keep_hist,
                        float* lam_out) {
     const Dims& g = c->g;
     const long long n = g.n;
@@ -239,7 +261,8 @@ static int state_solve(reg_ctx* c, const float* d_fwd, float* hist, bool keep_hi
         double bytes = 20.0 * n;
         if (fin) bytes += (lam_out ? 8.0 : 4.0) * n;
         Phase p(c, REG_PH_STATE, bytes);
-        REG_CK(c, launch_state_step(g, c->tile, in, d_fwd, out, fin ? c->rho_R : nullptr,
+        REG_CK(c, launch_state_step(g, tile_with(c, halo), in, d_fwd, out,
+                                    fin ? c->rho_R : nullptr,
                                     fin ? lam_out : nullptr, c->partials, c->npartials, &nb,
                                     c->stream));
     }
@@ -266,8 +289,10 @@ static int reg_energy(reg_ctx* c, const float2* vhat) {
 int op_mismatch(reg_ctx* c, const float* v) {
     // scratch only: the linearisation point stays intact
     REG_TRY(op_departure(c, v, c->tmp3, nullptr));
+    int halo;
+    REG_TRY(op_halo(c, c->tmp3, &halo));
     float* ping = reinterpret_cast<float*>(c->buf[0]);   // 2n floats: two levels
-    return state_solve(c, c->tmp3, ping, false, nullptr);
+    return state_solve(c, c->tmp3, halo, ping, false, nullptr);
 }
 
 int op_objective(reg_ctx* c, const float* v, int slot_J) {
@@ -283,7 +308,8 @@ static int adjoint_solve(reg_ctx* c, int phase) {
     const bool comp = !c->incompressible;
     for (int j = c->nt - 1; j >= 0; --j) {
         Phase p(c, phase, (comp ? 24.0 : 20.0) * n);
-        REG_CK(c, launch_adjoint_step(c->g, c->tile, c->lam_hist + (j + 1) * n, c->d_adj,
+        REG_CK(c, launch_adjoint_step(c->g, tile_with(c, c->halo_adj), c->lam_hist + (j + 1) * n,
+                                      c->d_adj,
                                       comp ? c->coef : nullptr, c->lam_hist + j * n, c->stream));
     }
     return REG_OK;
@@ -316,14 +342,16 @@ int op_linearize(reg_ctx* c, const float* v) {
     const bool comp = !c->incompressible;
     c->have_lin = false;
     REG_TRY(op_departure(c, v, c->d_fwd, c->d_adj));
+    REG_TRY(op_halo(c, c->d_fwd, &c->halo_fwd));
+    REG_TRY(op_halo(c, c->d_adj, &c->halo_adj));
     if (comp) {
         REG_TRY(op_div(c, v, c->divv));
         Phase p(c, REG_PH_ADJOINT, 20.0 * n);
-        REG_CK(c, launch_adjoint_coef(g, c->tile, c->divv, c->d_adj, (float)(1.0 / nt), c->coef,
-                                      c->stream));
+        REG_CK(c, launch_adjoint_coef(g, tile_with(c, c->halo_adj), c->divv, c->d_adj,
+                                      (float)(1.0 / nt), c->coef, c->stream));
     }
     // state history; lam(1) = rho_R - rho(1) into lam_hist[nt]
-    REG_TRY(state_solve(c, c->d_fwd, c->rho_hist, true, c->lam_hist + nt * n));
+    REG_TRY(state_solve(c, c->d_fwd, c->halo_fwd, c->rho_hist, true, c->lam_hist + nt * n));
     // spectral gradients of every level (cached for the matvecs)
     for (int j = 0; j <= nt; ++j) {
         if (c->grad_hist_bf) {
@@ -374,7 +402,8 @@ int op_matvec_transport(reg_ctx* c, const float* vt) {
     for (int j = 0; j < nt; ++j) {
         const bool fin = (j == nt - 1);
         Phase p(c, REG_PH_INCSTATE, (32.0 + gb) * n);
-        REG_CK(c, launch_incstate_step(g, c->tile, u[j & 1], c->d_fwd, vt, grad_level(c, j + 1),
+        REG_CK(c, launch_incstate_step(g, tile_with(c, c->halo_fwd), u[j & 1], c->d_fwd, vt,
+                                       grad_level(c, j + 1),
                                        grad_level_bf(c, j + 1), dt, fin ? 1 : 0,
                                        fin ? c->lam_hist + nt * n : u[(j + 1) & 1], c->stream));
     }
@@ -445,7 +474,7 @@ static void free_ctx(reg_ctx* c) {
         if (c->plans[i]) cufftDestroy(i == 0 ? c->r2c1 : i == 1 ? c->c2r1 : i == 2 ? c->r2c3 : c->c2r3);
     void* ptrs[] = {c->rho_T, c->rho_R, c->img_bf, c->d_fwd, c->d_adj, c->divv, c->rho_hist,
                     c->grad_hist, c->grad_hist_bf, c->lam_hist, c->coef, c->buf[0], c->buf[1],
-                    c->bacc, c->tmp3, c->spec[0], c->spec[1], c->partials, c->dsc};
+                    c->bacc, c->tmp3, c->spec[0], c->spec[1], c->partials, c->dsc, c->dabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i)
@@ -501,8 +530,9 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
     c->stream = nullptr;
     const long long n = c->g.n;
     const long long nc = c->g.nc;
-    c->tile.k = 8;
-    c->tile.wy = 4;
+    c->tile.k = 16;
+    c->tile.wy = 8;
+    c->halo_fwd = c->halo_adj = -1;
     // partial sums: the largest marching grid (k = 4, wy = 1), or up to
     // kMaxSlots partial-sum slots of the BLAS / spectral grid
     c->npartials = march_blocks(c->g, Tile{4, 1});
@@ -524,6 +554,7 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
         {(void**)&c->spec[1], sizeof(float2) * 3 * nc},
         {(void**)&c->partials, sizeof(double) * c->npartials},
         {(void**)&c->dsc, sizeof(double) * 32},
+        {(void**)&c->dabs, sizeof(unsigned int) * 4},
     };
     for (auto& a : allocs) {
         if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -715,9 +746,12 @@ int reg_interp(reg_ctx* c, const float* field, int nfields, const float* disp, f
     CHECK_PTR(c, out);
     if (nfields < 1 || nfields > 3) return fail(c, REG_EINVAL, "nfields must be 1..3");
     const long long n = c->g.n;
+    int halo;
+    REG_TRY(op_halo(c, disp, &halo));
     for (int k = 0; k < nfields; ++k) {
         Phase p(c, REG_PH_INTERP, 20.0 * n);
-        REG_CK(c, launch_interp(c->g, c->tile, field + k * n, disp, out + k * n, c->stream));
+        REG_CK(c, launch_interp(c->g, tile_with(c, halo), field + k * n, disp, out + k * n,
+                                c->stream));
     }
     return REG_OK;
 }
@@ -728,11 +762,13 @@ int reg_state_transport(reg_ctx* c, const float* rho0, const float* d_fwd, float
     CHECK_PTR(c, d_fwd);
     CHECK_PTR(c, rho_hist);
     const long long n = c->g.n;
+    int halo;
+    REG_TRY(op_halo(c, d_fwd, &halo));
     REG_CK(c, cudaMemcpyAsync(rho_hist, rho0, sizeof(float) * n, cudaMemcpyDeviceToDevice,
                               c->stream));
     for (int j = 0; j < c->nt; ++j) {
         Phase p(c, REG_PH_STATE, 20.0 * n);
-        REG_CK(c, launch_state_step(c->g, c->tile, rho_hist + j * n, d_fwd,
+        REG_CK(c, launch_state_step(c->g, tile_with(c, halo), rho_hist + j * n, d_fwd,
                                     rho_hist + (j + 1) * n, nullptr, nullptr, nullptr, 0, nullptr,
                                     c->stream));
     }

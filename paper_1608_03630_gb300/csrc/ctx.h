@@ -50,7 +50,9 @@ struct reg_ctx {
     int npartials;
     double* dsc;         // device scalars [32]
     double* hsc;         // pinned host mirror [32]
-    reg::Tile tile;      // tile of the x1-marching kernels
+    reg::Tile tile;      // tile of the interpolation kernels (k, wy)
+    int halo_fwd, halo_adj;   // ceil(max |X - x|) of d_fwd / d_adj (-1: unknown)
+    unsigned int* dabs;  // [2] device scratch for max |d| (float bits)
 
     // solver vectors: real [3n] each, spectral [3 nc] each
     float* sv[4];
@@ -119,6 +121,9 @@ int op_precond(reg_ctx* c, const float* r, float* z);
 int op_leray(reg_ctx* c, const float* v, float* out);
 int read_scalars(reg_ctx* c, int first, int count);   // dsc -> hsc, synchronises
 int bind_stream(reg_ctx* c, cudaStream_t s);         // launch stream + cuFFT plans
+// ceil(max |d|) over a displacement field [3n] (synchronises the stream).
+int op_halo(reg_ctx* c, const float* d, int* halo);
+reg::Tile tile_with(const reg_ctx* c, int halo);
 int ensure_solver(reg_ctx* c);
 
 // Device scalar slots.

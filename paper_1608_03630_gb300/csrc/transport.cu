@@ -330,6 +330,239 @@ k_march(Dims g, int K, const float* __restrict__ f, const float* __restrict__ d,
     epi.done(acc);
 }
 
+dim3 march_grid(const Dims& g, Tile t);
+
+// 4-byte asynchronous global -> shared copy (sm_80+ cp.async): the staging
+// loads of a whole box are all in flight before the block waits for them.
+__device__ __forceinline__ void cp_async4(float* smem_dst, const float* gmem_src) {
+    const unsigned int sa = (unsigned int)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem_src)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+// ------------------------------------------- shared-memory staged kernel
+// The block's output tile is 32 (x3) x wy (x2) x k (x1) points.  With every
+// |floor(d)| <= H, the stencils of the tile lie in the box of
+// (k + 3 + 2H) x (wy + 3 + 2H) x (35 + 2H) grid values around it; the block
+// stages that box in shared memory with coalesced loads (periodic wrap at
+// load time), then each point gathers its 64 values from shared memory:
+// consecutive lanes read consecutive words, so the gathers are conflict free
+// and no lane diverges.  A point outside the box (the bound was too small)
+// falls back to a global gather.
+
+template <class Epi>
+__device__ __forceinline__ void tile_point(const float* __restrict__ box, int E1, int E2, int E3,
+                                           int P3, int o1, int o2, int o3, const Epi& epi,
+                                           const float* __restrict__ f, const Dims& g, int i1,
+                                           int i2, int i3, float d1, float d2, float d3,
+                                           const typename Epi::Pre& pre, double& acc) {
+    const float fl1 = floorf(d1), fl2 = floorf(d2), fl3 = floorf(d3);
+    float w1[4], w2[4], w3[4];
+    lagrange4(d1 - fl1, w1);
+    lagrange4(d2 - fl2, w2);
+    lagrange4(d3 - fl3, w3);
+    const int l1 = i1 + (int)fl1 - 1 - o1;
+    const int l2 = i2 + (int)fl2 - 1 - o2;
+    const int l3 = i3 + (int)fl3 - 1 - o3;
+    const int idx = (i1 * g.n2 + i2) * g.n3 + i3;
+    float val = 0.f;
+    if (l1 >= 0 && l2 >= 0 && l3 >= 0 && l1 <= E1 - 4 && l2 <= E2 - 4 && l3 <= E3 - 4) {
+        const float* base = box + (l1 * E2 + l2) * P3 + l3;
+        const int E23 = E2 * P3;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            float r = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const float* row = base + a * E23 + b * P3;
+                float s = w3[0] * row[0];
+                s = fmaf(w3[1], row[1], s);
+                s = fmaf(w3[2], row[2], s);
+                s = fmaf(w3[3], row[3], s);
+                r = fmaf(w2[b], s, r);
+            }
+            val = fmaf(w1[a], r, val);
+        }
+    } else {
+        Stencil s;
+        make_stencil(s, g, i1, i2, i3, d1, d2, d3);
+        val = gather1(s, f);
+    }
+    epi.post(idx, val, pre, acc);
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(256)
+k_tile(Dims g, int K, int H, int E1, int E2, int E3, int P3, const float* __restrict__ f,
+       const float* __restrict__ d, Epi epi) {
+    extern __shared__ float box[];   // [E1][E2][P3], E3 columns used
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int i3 = blockIdx.x * 32 + lane;
+    const int i2 = blockIdx.y * blockDim.y + ty;
+    const int i1b = blockIdx.z * K;
+    const int o1 = i1b - 1 - H, o2 = blockIdx.y * blockDim.y - 1 - H;
+    const int o3 = blockIdx.x * 32 - 1 - H;
+    const bool active = i3 < g.n3 && i2 < g.n2;
+    const int kend = min(K, g.n1 - i1b);
+    Ahead<Epi> ah[2];
+    if (active) {
+        if (0 < kend) fetch(ah[0], d, g, epi, i1b, i2, i3);
+        if (1 < kend) fetch(ah[1], d, g, epi, i1b + 1, i2, i3);
+    }
+    // stage the box: one warp per row, lanes along x3 (columns lane, lane+32, ...)
+    {
+        const int nwarps = blockDim.y;
+        int col[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) col[c] = wrap_near(o3 + lane + 32 * c, g.n3);
+        const int rows = E1 * E2;
+        for (int r = ty; r < rows; r += nwarps) {
+            const int a = r / E2, b = r - a * E2;
+            const float* src = f + (long long)wrap_near(o1 + a, g.n1) * g.n23 +
+                               wrap_near(o2 + b, g.n2) * g.n3;
+            float* dst = box + r * P3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (lane + 32 * c < E3) cp_async4(dst + lane + 32 * c, src + col[c]);
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    double acc = 0.0;
+    if (active) {
+        for (int k = 0; k < kend; k += 2) {
+            {   // slot 0 (static index: the prefetch ring stays in registers)
+                const Ahead<Epi> cur = ah[0];
+                if (k + 2 < kend) fetch(ah[0], d, g, epi, i1b + k + 2, i2, i3);
+                tile_point(box, E1, E2, E3, P3, o1, o2, o3, epi, f, g, i1b + k, i2, i3, cur.d1,
+                           cur.d2, cur.d3, cur.pre, acc);
+            }
+            if (k + 1 < kend) {
+                const Ahead<Epi> cur = ah[1];
+                if (k + 3 < kend) fetch(ah[1], d, g, epi, i1b + k + 3, i2, i3);
+                tile_point(box, E1, E2, E3, P3, o1, o2, o3, epi, f, g, i1b + k + 1, i2, i3, cur.d1,
+                           cur.d2, cur.d3, cur.pre, acc);
+            }
+        }
+    }
+    epi.done(acc);
+}
+
+// The same kernel with the halo H and the block height WY fixed at compile
+// time: every one of the 64 shared-memory offsets of a point is then an
+// immediate, and only the base address is computed per point.
+template <class Epi, int H, int WY>
+__global__ void __launch_bounds__(32 * WY)
+k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict__ d, Epi epi) {
+    constexpr int E2 = WY + 3 + 2 * H;
+    constexpr int E3 = 35 + 2 * H;
+    constexpr int P3 = (E3 + 31) & ~31;
+    constexpr int E23 = E2 * P3;
+    extern __shared__ float box[];   // [E1][E2][P3], E3 columns used
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int E1 = K + 3 + 2 * H;
+    const int i3 = blockIdx.x * 32 + lane;
+    const int i2 = blockIdx.y * WY + ty;
+    const int i1b = blockIdx.z * K;
+    const int o1 = i1b - 1 - H, o2 = blockIdx.y * WY - 1 - H;
+    const int o3 = blockIdx.x * 32 - 1 - H;
+    const bool active = i3 < g.n3 && i2 < g.n2;
+    const int kend = min(K, g.n1 - i1b);
+    Ahead<Epi> ah[2];
+    if (active) {
+        if (0 < kend) fetch(ah[0], d, g, epi, i1b, i2, i3);
+        if (1 < kend) fetch(ah[1], d, g, epi, i1b + 1, i2, i3);
+    }
+    {
+        int col[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) col[c] = wrap_near(o3 + lane + 32 * c, g.n3);
+        for (int a = 0; a < E1; ++a) {
+            const float* plane = f + (long long)wrap_near(o1 + a, g.n1) * g.n23;
+            for (int b = ty; b < E2; b += WY) {
+                const float* src = plane + wrap_near(o2 + b, g.n2) * g.n3;
+                float* dst = box + (a * E2 + b) * P3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (lane + 32 * c < E3) cp_async4(dst + lane + 32 * c, src + col[c]);
+            }
+        }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    double acc = 0.0;
+    if (active) {
+        auto point = [&](const Ahead<Epi>& cur, int i1) {
+            const float fl1 = floorf(cur.d1), fl2 = floorf(cur.d2), fl3 = floorf(cur.d3);
+            float w1[4], w2[4], w3[4];
+            lagrange4(cur.d1 - fl1, w1);
+            lagrange4(cur.d2 - fl2, w2);
+            lagrange4(cur.d3 - fl3, w3);
+            const int l1 = i1 + (int)fl1 - 1 - o1;
+            const int l2 = i2 + (int)fl2 - 1 - o2;
+            const int l3 = i3 + (int)fl3 - 1 - o3;
+            const int idx = (i1 * g.n2 + i2) * g.n3 + i3;
+            float val = 0.f;
+            if ((unsigned)l1 <= (unsigned)(E1 - 4) && (unsigned)l2 <= (unsigned)(E2 - 4) &&
+                (unsigned)l3 <= (unsigned)(E3 - 4)) {
+                const float* base = box + (l1 * E2 + l2) * P3 + l3;
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    float r = 0.f;
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const float* row = base + a * E23 + b * P3;
+                        float sv = w3[0] * row[0];
+                        sv = fmaf(w3[1], row[1], sv);
+                        sv = fmaf(w3[2], row[2], sv);
+                        sv = fmaf(w3[3], row[3], sv);
+                        r = fmaf(w2[b], sv, r);
+                    }
+                    val = fmaf(w1[a], r, val);
+                }
+            } else {
+                Stencil st;
+                make_stencil(st, g, i1, i2, i3, cur.d1, cur.d2, cur.d3);
+                val = gather1(st, f);
+            }
+            epi.post(idx, val, cur.pre, acc);
+        };
+        for (int k = 0; k < kend; k += 2) {
+            {
+                const Ahead<Epi> cur = ah[0];
+                if (k + 2 < kend) fetch(ah[0], d, g, epi, i1b + k + 2, i2, i3);
+                point(cur, i1b + k);
+            }
+            if (k + 1 < kend) {
+                const Ahead<Epi> cur = ah[1];
+                if (k + 3 < kend) fetch(ah[1], d, g, epi, i1b + k + 3, i2, i3);
+                point(cur, i1b + k + 1);
+            }
+        }
+    }
+    epi.done(acc);
+}
+
+template <class Epi, int H, int WY>
+cudaError_t run_tile_fixed(const Dims& g, Tile t, const float* f, const float* d,
+                           const Epi& epi, cudaStream_t st) {
+    constexpr int E2 = WY + 3 + 2 * H;
+    constexpr int P3 = ((35 + 2 * H) + 31) & ~31;
+    const size_t smem = sizeof(float) * (size_t)(t.k + 3 + 2 * H) * E2 * P3;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_tile_fixed<Epi, H, WY>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(sizeof(float) * kMaxBoxFloats));
+        if (e != cudaSuccess) return e;
+    }
+    k_tile_fixed<Epi, H, WY><<<march_grid(g, t), dim3(32, WY), smem, st>>>(g, t.k, f, d, epi);
+    return cudaGetLastError();
+}
+
 dim3 march_grid(const Dims& g, Tile t) {
     return dim3((g.n3 + 31) / 32, (g.n2 + t.wy - 1) / t.wy, (g.n1 + t.k - 1) / t.k);
 }
@@ -338,8 +571,40 @@ template <class Epi>
 cudaError_t run_march(const Dims& g, Tile t, const float* f, const float* d, const Epi& epi,
                       cudaStream_t st) {
     if (t.k < 4 || (t.k & 3) || t.wy < 1 || 32 * t.wy > 256) return cudaErrorInvalidValue;
+    if (tile_staged(t) && t.wy == 8 && t.halo <= 3) {
+        if (t.halo <= 1) return run_tile_fixed<Epi, 1, 8>(g, t, f, d, epi, st);
+        if (t.halo == 2) return run_tile_fixed<Epi, 2, 8>(g, t, f, d, epi, st);
+        return run_tile_fixed<Epi, 3, 8>(g, t, f, d, epi, st);
+    }
+    if (tile_staged(t)) {
+        const int H = t.halo < 1 ? 1 : t.halo;
+        const int E1 = t.k + 3 + 2 * H, E2 = t.wy + 3 + 2 * H, E3 = 35 + 2 * H;
+        const int P3 = (E3 + 31) & ~31;
+        {
+            const size_t smem = sizeof(float) * (size_t)E1 * E2 * P3;
+            if (smem > 48 * 1024) {
+                const cudaError_t e = cudaFuncSetAttribute(
+                    k_tile<Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                    (int)(sizeof(float) * kMaxBoxFloats));
+                if (e != cudaSuccess) return e;
+            }
+            k_tile<Epi><<<march_grid(g, t), dim3(32, t.wy), smem, st>>>(g, t.k, H, E1, E2, E3, P3,
+                                                                         f, d, epi);
+            return cudaGetLastError();
+        }
+    }
     k_march<Epi><<<march_grid(g, t), dim3(32, t.wy), 0, st>>>(g, t.k, f, d, epi);
     return cudaGetLastError();
+}
+
+__global__ void k_absmax(const float* __restrict__ d, long long count, unsigned int* out) {
+    float m = 0.f;
+    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < count;
+         i += (long long)gridDim.x * kThreads)
+        m = fmaxf(m, fabsf(d[i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
 }
 
 // ------------------------------------------------------- streaming kernels
@@ -405,6 +670,26 @@ __global__ void k_from_bf16(const __nv_bfloat16* __restrict__ in, float* __restr
 }
 
 }  // namespace
+
+cudaError_t launch_absmax(const float* d, long long count, unsigned int* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned int), st);
+    if (e != cudaSuccess) return e;
+    int nb = (int)((count + kThreads - 1) / kThreads);
+    if (nb > 152 * 8) nb = 152 * 8;
+    k_absmax<<<nb, kThreads, 0, st>>>(d, count, out);
+    return cudaGetLastError();
+}
+
+// The staged kernel's box: (k + 3 + 2H) x (wy + 3 + 2H) rows of 35 + 2H
+// columns, stored with a row pitch that is a multiple of 32 words so that
+// lanes whose stencil bases differ by a row or a plane still hit distinct
+// shared-memory banks.
+bool tile_staged(const Tile& t) {
+    if (t.halo < 0) return false;
+    const int H = t.halo < 1 ? 1 : t.halo;   // halo 0 runs the H = 1 kernel
+    const long long E3 = 35 + 2 * H, P3 = (E3 + 31) & ~31LL;
+    return E3 <= 96 && (t.k + 3 + 2LL * H) * (t.wy + 3 + 2LL * H) * P3 <= kMaxBoxFloats;
+}
 
 int march_blocks(const Dims& g, Tile t) {
     const dim3 gr = march_grid(g, t);
