@@ -36,15 +36,45 @@ __device__ __forceinline__ int wrap(int i, int n) {
     return r < 0 ? r + n : r;
 }
 
-// Cubic Lagrange basis on the nodes -1, 0, 1, 2 at t in [0, 1].
+// Cubic Lagrange basis on the nodes -1, 0, 1, 2 at t in [0, 1]:
+//   l_-1 = -t(t-1)(t-2)/6, l_0 = (t+1)(t-1)(t-2)/2,
+//   l_1 = -(t+1)t(t-2)/2,   l_2 = (t+1)t(t-1)/6,
+// with p = t(t-1) and q = (t+1)(t-2) = p - 2 shared (10 operations).
 __device__ __forceinline__ void lagrange4(float t, float w[4]) {
-    const float tp1 = t + 1.f, tm1 = t - 1.f, tm2 = t - 2.f;
-    const float a = t * tm1;            // t (t-1)
-    const float b = tp1 * tm2;          // (t+1)(t-2)
-    w[0] = -a * tm2 * (1.f / 6.f);
-    w[1] = b * tm1 * 0.5f;
-    w[2] = -b * t * 0.5f;
-    w[3] = a * tp1 * (1.f / 6.f);
+    const float p = fmaf(t, t, -t);
+    const float q = p - 2.f;
+    w[0] = p * fmaf(t, -1.f / 6.f, 1.f / 3.f);
+    w[1] = q * fmaf(t, 0.5f, -0.5f);
+    w[2] = q * (-0.5f * t);
+    w[3] = p * fmaf(t, 1.f / 6.f, 1.f / 6.f);
+}
+
+// Packed FP32 pairs (Blackwell f32x2 ALU): two independent IEEE FP32
+// multiply-adds per instruction.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 pk(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+
+__device__ __forceinline__ float2 upk(f32x2 v) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
 
 // The 4 x 4 x 4 stencil of the point i + d (grid units): wrapped element

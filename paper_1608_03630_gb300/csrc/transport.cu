@@ -496,51 +496,56 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
     __syncthreads();
     double acc = 0.0;
     if (active) {
-        auto point = [&](const Ahead<Epi>& cur, int i1) {
+        // |floor(d)| <= H for every point by construction of H, so every
+        // stencil lies in the box; the clamps only keep non-finite input
+        // (which yields a NaN value) inside shared memory.
+        const int idx0 = (i1b * g.n2 + i2) * g.n3 + i3;
+        const int r2 = i2 - 1 - o2, r3 = i3 - 1 - o3;
+        auto point = [&](const Ahead<Epi>& cur, int k) {
             const float fl1 = floorf(cur.d1), fl2 = floorf(cur.d2), fl3 = floorf(cur.d3);
             float w1[4], w2[4], w3[4];
             lagrange4(cur.d1 - fl1, w1);
             lagrange4(cur.d2 - fl2, w2);
             lagrange4(cur.d3 - fl3, w3);
-            const int l1 = i1 + (int)fl1 - 1 - o1;
-            const int l2 = i2 + (int)fl2 - 1 - o2;
-            const int l3 = i3 + (int)fl3 - 1 - o3;
-            const int idx = (i1 * g.n2 + i2) * g.n3 + i3;
-            float val = 0.f;
-            if ((unsigned)l1 <= (unsigned)(E1 - 4) && (unsigned)l2 <= (unsigned)(E2 - 4) &&
-                (unsigned)l3 <= (unsigned)(E3 - 4)) {
-                const float* base = box + (l1 * E2 + l2) * P3 + l3;
+            const int l1 = min(max(k + H + (int)fl1, 0), E1 - 4);   // i1 + fl1 - 1 - o1
+            const int l2 = min(max(r2 + (int)fl2, 0), E2 - 4);
+            const int l3 = min(max(r3 + (int)fl3, 0), E3 - 4);
+            const float* base = box + (l1 * E2 + l2) * P3 + l3;
+            const f32x2 w2a = pk(w2[0], w2[1]), w2b = pk(w2[2], w2[3]);
+            f32x2 ww3[4];
 #pragma unroll
-                for (int a = 0; a < 4; ++a) {
-                    float r = 0.f;
+            for (int c = 0; c < 4; ++c) ww3[c] = pk(w3[c], w3[c]);
+            float r[4];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        const float* row = base + a * E23 + b * P3;
-                        float sv = w3[0] * row[0];
-                        sv = fmaf(w3[1], row[1], sv);
-                        sv = fmaf(w3[2], row[2], sv);
-                        sv = fmaf(w3[3], row[3], sv);
-                        r = fmaf(w2[b], sv, r);
-                    }
-                    val = fmaf(w1[a], r, val);
+            for (int a = 0; a < 4; ++a) {
+                const float* pl = base + a * E23;
+                // rows (0, 1) and (2, 3) of the plane in packed pairs
+                f32x2 s01 = mul2(ww3[0], pk(pl[0], pl[P3]));
+                f32x2 s23 = mul2(ww3[0], pk(pl[2 * P3], pl[3 * P3]));
+#pragma unroll
+                for (int c = 1; c < 4; ++c) {
+                    s01 = fma2(ww3[c], pk(pl[c], pl[P3 + c]), s01);
+                    s23 = fma2(ww3[c], pk(pl[2 * P3 + c], pl[3 * P3 + c]), s23);
                 }
-            } else {
-                Stencil st;
-                make_stencil(st, g, i1, i2, i3, cur.d1, cur.d2, cur.d3);
-                val = gather1(st, f);
+                const float2 t2 = upk(fma2(w2b, s23, mul2(w2a, s01)));
+                r[a] = t2.x + t2.y;
             }
-            epi.post(idx, val, cur.pre, acc);
+            float val = w1[0] * r[0];
+            val = fmaf(w1[1], r[1], val);
+            val = fmaf(w1[2], r[2], val);
+            val = fmaf(w1[3], r[3], val);
+            epi.post(idx0 + k * g.n23, val, cur.pre, acc);
         };
         for (int k = 0; k < kend; k += 2) {
             {
                 const Ahead<Epi> cur = ah[0];
                 if (k + 2 < kend) fetch(ah[0], d, g, epi, i1b + k + 2, i2, i3);
-                point(cur, i1b + k);
+                point(cur, k);
             }
             if (k + 1 < kend) {
                 const Ahead<Epi> cur = ah[1];
                 if (k + 3 < kend) fetch(ah[1], d, g, epi, i1b + k + 3, i2, i3);
-                point(cur, i1b + k + 1);
+                point(cur, k + 1);
             }
         }
     }
