@@ -260,6 +260,24 @@ def gpu_bench(args):
         e2e_s = (time.perf_counter() - t0) / e2e_steps
         R.close()
 
+        # the other precision, one solve, for the same stopping test
+        other = 'fp32' if args.precision == 'mixed_bf16' else 'mixed_bf16'
+        R2 = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=other, stream=stream)
+        R2.set_images(dT, dR, presmooth=True)
+        v.zero_()
+        R2.solve(v, gtol=1e-2, max_gn=50, max_pcg=500)     # warm-up (plans, graphs)
+        v.zero_()
+        R2.set_images(dT, dR, presmooth=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st_other = R2.solve(v, gtol=1e-2, max_gn=50, max_pcg=500)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        other_line = {'precision': other, 'time_to_solution_s': e0.elapsed_time(e1) / 1e3,
+                      'gn_iters': st_other['gn_iters'], 'matvecs': st_other['matvecs'],
+                      'gnorm_rel': st_other['gnorm_rel'], 'mismatch_rel': st_other['mismatch_rel']}
+        R2.close()
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -289,6 +307,8 @@ def gpu_bench(args):
         'higher_is_better': False, 'scaling': 'weak', 'vs_baseline': None,
         'dtype': 'f32', 'data': 'synthetic',
         'config': {'workload': 'phantom 256^3 nt=8 H2 beta=1e-3 %s' % args.precision,
+                   'storage': ('bf16 images, bf16 grad-rho cache in the matvec, fp32 fields'
+                               if args.precision == 'mixed_bf16' else 'fp32'),
                    'grid': list(SHAPE), 'nt': NT, 'beta': BETA, 'regularisation': KIND,
                    'gtol': 1e-2, 'precision': args.precision, 'parallelism': 'replicas',
                    'l2': 'inputs larger than L2 (working set > 4 GB), no flush'},
@@ -303,6 +323,7 @@ def gpu_bench(args):
                      'unit': 'GB/s', 'frac': achieved / peak, 'peak_source': peak_kind,
                      'bytes_per_launch': d['bytes'] / max(1, d['launches']),
                      'traffic': measured_traffic(dom, n)},
+        'other_precision': other_line,
         'gpu_launches': launches,
         'clocks': clk,
         'e2e': {'value': e2e_s, 'unit': UNIT, 'h2d_bytes_per_step': 4 * n * 2 + 12 * n,
@@ -343,7 +364,7 @@ def main():
     ap.add_argument('--steps', type=int, default=3)
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
-    ap.add_argument('--precision', default='fp32', choices=['fp32', 'mixed_bf16'])
+    ap.add_argument('--precision', default='mixed_bf16', choices=['fp32', 'mixed_bf16'])
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--profile-matvec', type=int, default=0, metavar='N',
                     help='run one gradient and two matvecs at N^3 (nt = 4) for ncu, then exit')

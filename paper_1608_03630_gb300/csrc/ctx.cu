@@ -237,6 +237,10 @@ static const __nv_bfloat16* grad_level_bf(reg_ctx* c, int j) {
 }
 static double grad_bytes(reg_ctx* c) { return c->grad_hist_bf ? 6.0 : 12.0; }
 
+// The gradient always reads the FP32 cache; the Hessian matvec reads the
+// bfloat16 copy in mixed precision.
+static bool matvec_bf(reg_ctx* c) { return c->grad_hist_bf != nullptr; }
+
 // Forward state solve (Eq. varopt:state).  keep_hist: all levels in hist
 // [(nt+1) n]; otherwise hist holds two ping-pong levels.  The last step
 // writes lam(1) = rho_R - rho(1) to lam_out (if not null) and the mismatch
@@ -316,16 +320,21 @@ static int adjoint_solve(reg_ctx* c, int phase) {
 }
 
 // out = base + sum_j w_j lam_j grad rho_j; dsc[slot] = <dotp, out>_h if dotp.
-int op_time_integral(reg_ctx* c, const float* base, float* out, const float* dotp, int slot) {
+// matvec: use the matvec's copy of the grad rho cache (bfloat16 in mixed
+// precision); the gradient passes false and reads FP32.
+int op_time_integral(reg_ctx* c, const float* base, float* out, const float* dotp, int slot,
+                     bool matvec) {
     const long long n = c->g.n;
     const int nb = blas_blocks();
     {
-        double bytes = (c->nt + 1) * (4.0 + grad_bytes(c)) * n + 12.0 * n;
+        const bool bf = matvec && matvec_bf(c);
+        double bytes = (c->nt + 1) * (4.0 + (bf ? 6.0 : 12.0)) * n + 12.0 * n;
         if (base) bytes += 12.0 * n;
         if (dotp) bytes += 12.0 * n;
         Phase p(c, REG_PH_OTHER, bytes);
-        REG_CK(c, launch_time_integral(c->g, c->nt, c->lam_hist, c->grad_hist, c->grad_hist_bf,
-                                       base, out, dotp, c->partials, nb, c->stream));
+        REG_CK(c, launch_time_integral(c->g, c->nt, c->lam_hist, c->grad_hist,
+                                       bf ? c->grad_hist_bf : nullptr, base, out, dotp,
+                                       c->partials, nb, c->stream));
     }
     if (dotp) {
         Phase p(c, REG_PH_BLAS, 0.0);
@@ -354,17 +363,16 @@ int op_linearize(reg_ctx* c, const float* v) {
     REG_TRY(state_solve(c, c->d_fwd, c->halo_fwd, c->rho_hist, true, c->lam_hist + nt * n));
     // spectral gradients of every level (cached for the matvecs)
     for (int j = 0; j <= nt; ++j) {
+        float* gj = c->grad_hist + (long long)j * 3 * n;
+        REG_TRY(op_grad(c, c->rho_hist + j * n, gj));
         if (c->grad_hist_bf) {
-            REG_TRY(op_grad(c, c->rho_hist + j * n, c->tmp3));
             Phase p(c, REG_PH_OTHER, 18.0 * n);
-            REG_CK(c, launch_to_bf16(c->tmp3, c->grad_hist_bf + (long long)j * 3 * n, 3 * n,
+            REG_CK(c, launch_to_bf16(gj, c->grad_hist_bf + (long long)j * 3 * n, 3 * n,
                                      c->stream));
-        } else {
-            REG_TRY(op_grad(c, c->rho_hist + j * n, c->grad_hist + (long long)j * 3 * n));
         }
     }
     REG_TRY(adjoint_solve(c, REG_PH_ADJOINT));
-    REG_TRY(op_time_integral(c, nullptr, c->bacc, nullptr, 0));
+    REG_TRY(op_time_integral(c, nullptr, c->bacc, nullptr, 0, false));
     c->have_lin = true;
     return REG_OK;
 }
@@ -412,7 +420,7 @@ int op_matvec_transport(reg_ctx* c, const float* vt) {
 
 int op_matvec(reg_ctx* c, const float* vt, float* out) {
     REG_TRY(op_matvec_transport(c, vt));
-    REG_TRY(op_time_integral(c, nullptr, c->bacc, nullptr, 0));
+    REG_TRY(op_time_integral(c, nullptr, c->bacc, nullptr, 0, true));
     REG_TRY(op_fft_r2c(c, vt, c->spec[0], 3));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
     SpecArgs a = spec_args(c);
@@ -493,11 +501,9 @@ static int alloc_grad_hist(reg_ctx* c) {
     const size_t cnt = (size_t)(c->nt + 1) * 3 * c->g.n;
     if (c->grad_hist) { cudaFree(c->grad_hist); c->grad_hist = nullptr; }
     if (c->grad_hist_bf) { cudaFree(c->grad_hist_bf); c->grad_hist_bf = nullptr; }
-    cudaError_t e;
-    if (c->precision == REG_MIXED_BF16)
+    cudaError_t e = cudaMalloc(&c->grad_hist, cnt * sizeof(float));
+    if (e == cudaSuccess && c->precision == REG_MIXED_BF16)
         e = cudaMalloc(&c->grad_hist_bf, cnt * sizeof(__nv_bfloat16));
-    else
-        e = cudaMalloc(&c->grad_hist, cnt * sizeof(float));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, REG_ENOMEM, "cannot allocate the grad rho cache");
