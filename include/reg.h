@@ -239,6 +239,36 @@ int reg_inner(reg_ctx* ctx, const float* a, const float* b, size_t count,
 int reg_set_tile(reg_ctx* ctx, int k, int wy);
 int reg_get_tile(const reg_ctx* ctx, int* k, int* wy);
 
+/* Autotuner: time the interpolation kernels of the current linearisation
+ * point (reg_gradient first, else REG_ENOTREADY) for a few tile shapes and
+ * keep the fastest in ctx; the choice is cached per (grid, halo) for the
+ * process.  *k, *wy (may be NULL) receive the chosen tile. */
+int reg_autotune(reg_ctx* ctx, int* k, int* wy);
+
+/* ------------------------------------------------------------- batch */
+
+/* Independent registrations of image pairs of uneven sizes solved together
+ * (one GPU).  Pair i has grid dims[3i..3i+2]; all share nt, beta, reg_kind,
+ * incompressible and precision (REG_FP32 / REG_MIXED_BF16).  Each pair gets
+ * its own context and non-blocking stream; worker host threads take pairs
+ * largest first and run their solves concurrently, so the kernels of small
+ * pairs overlap on the GPU. */
+typedef struct reg_batch reg_batch;
+int reg_batch_create(int npairs, const int* dims, int nt, double beta, int reg_kind,
+                     int incompressible, int precision, reg_batch** out);
+int reg_batch_destroy(reg_batch* batch);
+
+/* Solve every pair: v_inout[i] (device, [3 n_i]) is pair i's initial guess
+ * and solution, rho_T[i], rho_R[i] its images (device, [n_i]).  autotune != 0
+ * runs reg_autotune on each pair first (cached per grid size).  Per pair
+ * (arrays of npairs, each may be NULL): stats, latency_ms (from the call's
+ * start until that pair's stopping test), status_out (REG_OK / REG_EMAXITER
+ * / error).  Returns the first hard error, else REG_OK. */
+int reg_batch_solve(reg_batch* batch, float* const* v_inout, const float* const* rho_T,
+                    const float* const* rho_R, int presmooth, int autotune,
+                    const reg_solve_opts* opts, reg_solve_stats* stats, double* latency_ms,
+                    int* status_out);
+
 /* ------------------------------------------------------------- timing */
 
 enum {

@@ -1,0 +1,219 @@
+// Batched registration of independent image pairs of uneven sizes, and the
+// interpolation-tile autotuner.
+//
+// Every pair owns a context and a non-blocking CUDA stream; worker threads
+// take pairs from a queue ordered by cost (grid points x time steps, largest
+// first) and run the pair's solve on its stream, so the kernels of small
+// pairs overlap on the GPU.  Each pair's PCG iteration is one CUDA graph
+// replayed until its own stopping test (solver.cu).  The autotuner times the
+// interpolation kernels of a linearised context for a few tile shapes and
+// keeps the fastest; results are cached per (grid, halo) for the process.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "ctx.h"
+
+struct reg_batch {
+    std::vector<reg_ctx*> ctx;
+    std::vector<cudaStream_t> streams;
+    int workers;
+    std::string err;
+};
+
+namespace reg {
+
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
+
+// Median-free, simple timing: the mean of `reps` launches of the matvec
+// transports (nt incremental-state and nt incremental-adjoint steps).
+int time_transports(reg_ctx* c, const float* vt, int reps, float* ms) {
+    cudaEvent_t a, b;
+    REG_CK(c, cudaEventCreate(&a));
+    REG_CK(c, cudaEventCreate(&b));
+    REG_TRY(op_matvec_transport(c, vt));   // warm
+    REG_CK(c, cudaEventRecord(a, c->stream));
+    for (int r = 0; r < reps; ++r) REG_TRY(op_matvec_transport(c, vt));
+    REG_CK(c, cudaEventRecord(b, c->stream));
+    REG_CK(c, cudaEventSynchronize(b));
+    REG_CK(c, cudaEventElapsedTime(ms, a, b));
+    *ms /= reps;
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return REG_OK;
+}
+
+}  // namespace
+
+}  // namespace reg
+
+using namespace reg;
+
+extern "C" {
+
+int reg_autotune(reg_ctx* c, int* k_out, int* wy_out) {
+    if (!c) return REG_EINVAL;
+    if (c->dead) return fail(c, REG_ECUDA, "context unusable after a CUDA error");
+    if (!c->have_lin) return fail(c, REG_ENOTREADY, "reg_gradient must come first");
+    const auto key = std::make_tuple(c->g.n1, c->g.n2, c->g.n3, c->halo_fwd, c->halo_adj);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            c->tile.k = it->second.first;
+            c->tile.wy = it->second.second;
+            if (k_out) *k_out = c->tile.k;
+            if (wy_out) *wy_out = c->tile.wy;
+            return REG_OK;
+        }
+    }
+    // a smooth direction for the timing: the cached gradient of rho(t_0)
+    const float* vt = c->grad_hist;
+    const Tile keep = c->tile;
+    const bool timing = c->timing;
+    c->timing = false;
+    static const int cand[][2] = {{4, 8}, {8, 8}, {16, 8}, {8, 4}, {16, 4}};
+    float best = 1e30f;
+    int bk = keep.k, bw = keep.wy;
+    for (const auto& kw : cand) {
+        c->tile.k = kw[0];
+        c->tile.wy = kw[1];
+        float ms = 0.f;
+        const int s = time_transports(c, vt, 3, &ms);
+        if (s != REG_OK) {
+            c->tile = keep;
+            c->timing = timing;
+            return s;
+        }
+        if (ms < best) { best = ms; bk = kw[0]; bw = kw[1]; }
+    }
+    c->timing = timing;
+    c->tile = keep;
+    c->tile.k = bk;
+    c->tile.wy = bw;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mutex);
+        g_tune_cache[key] = std::make_pair(bk, bw);
+    }
+    if (k_out) *k_out = bk;
+    if (wy_out) *wy_out = bw;
+    return REG_OK;
+}
+
+int reg_batch_create(int npairs, const int* dims, int nt, double beta, int reg_kind,
+                     int incompressible, int precision, reg_batch** out) {
+    if (!out) return REG_EINVAL;
+    *out = nullptr;
+    if (npairs < 1 || !dims) return REG_EINVAL;
+    reg_batch* b = new (std::nothrow) reg_batch();
+    if (!b) return REG_ENOMEM;
+    b->workers = std::min(npairs, 8);
+    int status = REG_OK;
+    for (int i = 0; i < npairs && status == REG_OK; ++i) {
+        reg_ctx* c = nullptr;
+        status = reg_create(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], nt, beta, reg_kind,
+                            incompressible, &c);
+        if (status != REG_OK) break;
+        b->ctx.push_back(c);
+        cudaStream_t s;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            status = REG_ECUDA;
+            break;
+        }
+        b->streams.push_back(s);
+        status = reg_set_stream(c, s);
+        if (status == REG_OK && precision) status = reg_set_precision(c, precision);
+    }
+    if (status != REG_OK) {
+        for (auto c : b->ctx) reg_destroy(c);
+        for (auto s : b->streams) cudaStreamDestroy(s);
+        delete b;
+        return status;
+    }
+    *out = b;
+    return REG_OK;
+}
+
+int reg_batch_destroy(reg_batch* b) {
+    if (!b) return REG_OK;
+    for (auto c : b->ctx) reg_destroy(c);
+    for (auto s : b->streams) cudaStreamDestroy(s);
+    delete b;
+    return REG_OK;
+}
+
+int reg_batch_solve(reg_batch* b, float* const* v_inout, const float* const* rho_T,
+                    const float* const* rho_R, int presmooth, int autotune,
+                    const reg_solve_opts* opts, reg_solve_stats* stats, double* latency_ms,
+                    int* status_out) {
+    if (!b || !v_inout || !rho_T || !rho_R) return REG_EINVAL;
+    const int np = (int)b->ctx.size();
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return REG_ECUDA;
+    // cost order, largest first
+    std::vector<int> order(np);
+    for (int i = 0; i < np; ++i) order[i] = i;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        const long long cx = (long long)b->ctx[x]->g.n * b->ctx[x]->nt;
+        const long long cy = (long long)b->ctx[y]->g.n * b->ctx[y]->nt;
+        return cx > cy;
+    });
+    std::atomic<int> next(0);
+    std::vector<int> st(np, REG_OK);
+    std::vector<reg_solve_stats> local(np);
+    std::vector<double> lat(np, 0.0);
+    const auto t0 = std::chrono::steady_clock::now();
+    auto work = [&]() {
+        cudaSetDevice(dev);
+        for (;;) {
+            const int q = next.fetch_add(1);
+            if (q >= np) break;
+            const int i = order[q];
+            reg_ctx* c = b->ctx[i];
+            int s = reg_set_images(c, rho_T[i], rho_R[i], presmooth);
+            if (s == REG_OK && autotune) {
+                // linearise at the initial guess, tune, then solve
+                float* g = nullptr;
+                s = ensure_solver(c);
+                if (s == REG_OK) {
+                    g = c->sv[3];
+                    s = reg_gradient(c, v_inout[i], g, nullptr);
+                }
+                if (s == REG_OK) s = reg_autotune(c, nullptr, nullptr);
+            }
+            if (s == REG_OK || s == REG_EMAXITER) {
+                memset(&local[i], 0, sizeof(reg_solve_stats));
+                s = reg_solve(c, v_inout[i], opts, &local[i]);
+            }
+            cudaStreamSynchronize(c->stream);
+            st[i] = s;
+            lat[i] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                         .count();
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int w = 0; w < b->workers; ++w) pool.emplace_back(work);
+    for (auto& t : pool) t.join();
+    int status = REG_OK;
+    for (int i = 0; i < np; ++i) {
+        if (stats) stats[i] = local[i];
+        if (latency_ms) latency_ms[i] = lat[i];
+        if (status_out) status_out[i] = st[i];
+        if (st[i] != REG_OK && st[i] != REG_EMAXITER && status == REG_OK) status = st[i];
+    }
+    return status;
+}
+
+}  // extern "C"

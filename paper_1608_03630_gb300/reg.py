@@ -95,6 +95,10 @@ _SIGS = {
     'reg_set_tile': [_P, _I, _I],
     'reg_get_tile': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_get_timing': [_P, ctypes.POINTER(Timing)],
+    'reg_autotune': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    'reg_batch_create': [_I, _P, _I, _D, _I, _I, _I, ctypes.POINTER(_P)],
+    'reg_batch_destroy': [_P],
+    'reg_batch_solve': [_P, _P, _P, _P, _I, _I, ctypes.POINTER(SolveOpts), _P, _P, _P],
 }
 
 
@@ -326,6 +330,11 @@ class Registration:
         self._call('reg_get_tile', ctypes.byref(k), ctypes.byref(wy))
         return k.value, wy.value
 
+    def autotune(self):
+        k, wy = ctypes.c_int(), ctypes.c_int()
+        self._call('reg_autotune', ctypes.byref(k), ctypes.byref(wy))
+        return k.value, wy.value
+
     def set_timing(self, on):
         self._call('reg_set_timing', 1 if on else 0)
 
@@ -333,3 +342,50 @@ class Registration:
         t = Timing()
         self._call('reg_get_timing', ctypes.byref(t))
         return t.as_dict()
+
+
+class Batch:
+    """reg_batch_*: independent pairs of uneven sizes solved concurrently."""
+
+    def __init__(self, shapes, nt, beta, kind='H2', incompressible=False, precision='fp32'):
+        self.shapes = [tuple(int(x) for x in s) for s in shapes]
+        dims = (ctypes.c_int * (3 * len(shapes)))(*[x for s in self.shapes for x in s])
+        self._b = ctypes.c_void_p()
+        s = lib().reg_batch_create(len(shapes), ctypes.cast(dims, ctypes.c_void_p), int(nt),
+                                   float(beta), KINDS[kind], 1 if incompressible else 0,
+                                   MIXED_BF16 if precision == 'mixed_bf16' else FP32,
+                                   ctypes.byref(self._b))
+        if s != 0:
+            raise RegError(s, lib().reg_last_error(None).decode())
+
+    def solve(self, vs, rho_Ts, rho_Rs, presmooth=True, autotune=True, **opts):
+        """Solve all pairs in place; returns (statuses, stats dicts, latencies ms)."""
+        n = len(self.shapes)
+        ptrs = lambda ts, nm: (ctypes.c_void_p * n)(*[_ptr(t, None, nm).value for t in ts])
+        o = Registration.default_opts()
+        for k, v in opts.items():
+            setattr(o, k, v)
+        stats = (SolveStats * n)()
+        lat = (ctypes.c_double * n)()
+        st = (ctypes.c_int * n)()
+        torch.cuda.synchronize()
+        s = lib().reg_batch_solve(self._b, ptrs(vs, 'v'), ptrs(rho_Ts, 'rho_T'),
+                                  ptrs(rho_Rs, 'rho_R'), 1 if presmooth else 0,
+                                  1 if autotune else 0, ctypes.byref(o),
+                                  ctypes.cast(stats, ctypes.c_void_p),
+                                  ctypes.cast(lat, ctypes.c_void_p),
+                                  ctypes.cast(st, ctypes.c_void_p))
+        if s != 0:
+            raise RegError(s, 'reg_batch_solve failed')
+        return list(st), [x.as_dict() for x in stats], list(lat)
+
+    def close(self):
+        if self._b and self._b.value:
+            lib().reg_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
