@@ -142,6 +142,10 @@ typedef struct {
     int armijo_max;       /* line-search trials                           (10) */
     int use_graph;        /* capture the PCG iteration in a CUDA graph     (1) */
     int verbose;          /* print one line per Newton iteration to stderr (0) */
+    double gnorm_ref;     /* > 0: use it as ||g_0|| in the stop test and the
+                             forcing term, e.g. the gradient norm at v = 0
+                             when v_inout holds a prediction; 0: ||g|| at the
+                             initial guess                               (0) */
 } reg_solve_opts;
 
 typedef struct {
@@ -268,6 +272,65 @@ int reg_batch_solve(reg_batch* batch, float* const* v_inout, const float* const*
                     const float* const* rho_R, int presmooth, int autotune,
                     const reg_solve_opts* opts, reg_solve_stats* stats, double* latency_ms,
                     int* status_out);
+
+/* ------------------------------------------------- spectral resampling */
+
+/* Trigonometric (Fourier) resampling of ncomp scalar fields from the grid
+ * nin[0] x nin[1] x nin[2] to nout[0] x nout[1] x nout[2] (Sec. III-B1: fields
+ * are represented by their Fourier series on the periodic grid).  The
+ * coefficients with |k_j| < min(nin_j, nout_j) / 2 in every direction are
+ * kept, the rest (including the Nyquist planes) are zero, so a field
+ * band-limited to those modes is reproduced exactly at the new grid points.
+ * in: device [ncomp][nin], out: device [ncomp][nout], not overlapping.  The
+ * library caches cuFFT plans and a workspace per (sizes, ncomp) (process-wide,
+ * guarded by a mutex); calls with the same sizes share that workspace, so
+ * the caller orders them (one stream).  Asynchronous on `stream`. */
+int reg_spectral_resample(const int* nin, const int* nout, int ncomp, const float* in,
+                          float* out, void* stream);
+
+/* ------------------------------------------ learned initial velocity */
+
+/* A 3-D U-Net that maps the image pair (rho_T, rho_R), resampled to an R^3
+ * grid, to an initial velocity [cout][R^3] for reg_solve.  No counterpart in
+ * the paper, whose Gauss-Newton iteration starts from v = 0 (Sec. III-A); the
+ * solve that follows is unchanged and runs to its own stopping test.
+ *
+ * Architecture, levels L (1..6), channels ch[0..L-1] (1..128):
+ *   encoder level l:  conv3x3x3 -> ReLU -> conv3x3x3 -> ReLU = skip_l,
+ *                     then 2x average pooling for l < L-1;
+ *   decoder level l = L-2 .. 0: 2x nearest upsampling, concatenation
+ *                     [upsampled, skip_l], conv3 -> ReLU -> conv3 -> ReLU;
+ *   head: 1x1x1 conv to cout channels.  Zero padding.
+ * Parameters: one flat FP32 array, per layer in the order enc0.0, enc0.1,
+ * ..., enc(L-1).1, dec(L-2).0, dec(L-2).1, ..., dec0.1, head, each as the
+ * weights [kz][ky][kx][cin][cout] followed by the bias [cout].
+ * Arithmetic: BF16 weights and activations on the tensor cores with FP32
+ * accumulation; FP32 master weights, gradients and Adam moments; FP64 loss.
+ * Tensors: x is device [cin][R^3] (each channel [R][R][R], last index
+ * fastest), the prediction and the target are device [cout][R^3].
+ * Limits: cin, cout <= 128, R^3 <= 65535 * 64 (R <= 161). */
+typedef struct reg_unet reg_unet;
+
+/* R divisible by 2^(L-1), R >= 8; parameters zero until reg_unet_set_params. */
+int reg_unet_create(int R, int levels, const int* ch, int cin, int cout, reg_unet** out);
+int reg_unet_destroy(reg_unet* net);
+const char* reg_unet_last_error(const reg_unet* net);
+int reg_unet_set_stream(reg_unet* net, void* stream);
+int reg_unet_param_count(const reg_unet* net, size_t* count);
+/* Host arrays of reg_unet_param_count floats.  set_params also zeroes the
+ * Adam moments and step count.  Both wait for the stream. */
+int reg_unet_set_params(reg_unet* net, const float* params_host);
+int reg_unet_get_params(reg_unet* net, float* params_host);
+/* y = net(x), asynchronous. */
+int reg_unet_forward(reg_unet* net, const float* x, float* y);
+/* Mean-squared-error loss against target (host *loss if not NULL) and its
+ * gradient with respect to every parameter (host grad_host if not NULL). */
+int reg_unet_gradient(reg_unet* net, const float* x, const float* target, double* loss,
+                      float* grad_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on the loss of one sample;
+ * *loss (host, if not NULL) is the loss before the step. */
+int reg_unet_train_step(reg_unet* net, const float* x, const float* target, float lr,
+                        double* loss);
 
 /* ------------------------------------------------------------- timing */
 

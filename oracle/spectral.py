@@ -158,3 +158,28 @@ def gaussian_smooth(f, sigma):
     g = np.exp(-0.5 * ((sigma[0] * k1) ** 2 + (sigma[1] * k2) ** 2
                        + (sigma[2] * k3) ** 2))
     return apply_symbol(f, g)
+
+
+def resample(f, shape_out):
+    """Trigonometric resampling of f (scalar (N1, N2, N3) or (c, N1, N2, N3))
+    to the grid shape_out (Sec. III-B1: a field is its Fourier series on the
+    grid).  Reading: the coefficients with |k_j| < min(N_j, M_j)/2 on every
+    axis are kept and all others, the Nyquist planes included, are dropped, so
+    the result is real and a field band-limited to the kept modes is
+    reproduced exactly on the new points."""
+    f = np.asarray(f, dtype=np.float64)
+    if f.ndim == 4:
+        return np.stack([resample(c, shape_out) for c in f])
+    nin = f.shape
+    fh = np.fft.fftn(f) / f.size
+    gh = np.zeros(tuple(shape_out), dtype=complex)
+    keep = []
+    for a, b in zip(nin, shape_out):
+        k = wavenumbers(a)
+        lim = min(a, b)
+        idx_in = np.nonzero(2 * np.abs(k) < lim)[0]
+        idx_out = np.where(k[idx_in] >= 0, k[idx_in], k[idx_in] + b).astype(int)
+        keep.append((idx_in, idx_out))
+    (i1, o1), (i2, o2), (i3, o3) = keep
+    gh[np.ix_(o1, o2, o3)] = fh[np.ix_(i1, i2, i3)]
+    return np.real(np.fft.ifftn(gh) * np.prod(shape_out))

@@ -224,7 +224,10 @@ static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solv
     double J, gn;
     REG_TRY(evaluate_gradient(c, &J, &gn));
     st->gradient_evals++;
-    const double g0 = gn;
+    // the stop test and the forcing term are relative to ||g_0||: the
+    // gradient at the initial guess, or the caller's reference norm (the
+    // gradient at v = 0 when the guess is a prediction)
+    const double g0 = o->gnorm_ref > 0.0 ? o->gnorm_ref : gn;
     st->J0 = J;
     st->gnorm0 = g0;
     double jmis = c->hsc[SC_JMIS];
@@ -297,6 +300,7 @@ int reg_solve_opts_default(reg_solve_opts* o) {
     o->armijo_max = 10;
     o->use_graph = 1;
     o->verbose = 0;
+    o->gnorm_ref = 0.0;
     return REG_OK;
 }
 
@@ -308,7 +312,7 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
     reg_solve_opts o;
     reg_solve_opts_default(&o);
     if (opts) o = *opts;
-    if (!(o.gtol >= 0.0) || o.max_gn < 0 || o.max_pcg < 1 || o.armijo_max < 1 ||
+    if (!(o.gtol >= 0.0) || !(o.gnorm_ref >= 0.0) || o.max_gn < 0 || o.max_pcg < 1 || o.armijo_max < 1 ||
         !(o.armijo_shrink > 0.0 && o.armijo_shrink < 1.0))
         return fail(c, REG_EINVAL, "bad solver options");
     REG_TRY(ensure_solver(c));

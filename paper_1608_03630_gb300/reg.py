@@ -33,7 +33,7 @@ class SolveOpts(ctypes.Structure):
                 ('max_pcg', ctypes.c_int), ('forcing', ctypes.c_int),
                 ('armijo_c', ctypes.c_double), ('armijo_shrink', ctypes.c_double),
                 ('armijo_max', ctypes.c_int), ('use_graph', ctypes.c_int),
-                ('verbose', ctypes.c_int)]
+                ('verbose', ctypes.c_int), ('gnorm_ref', ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -99,6 +99,16 @@ _SIGS = {
     'reg_batch_create': [_I, _P, _I, _D, _I, _I, _I, ctypes.POINTER(_P)],
     'reg_batch_destroy': [_P],
     'reg_batch_solve': [_P, _P, _P, _P, _I, _I, ctypes.POINTER(SolveOpts), _P, _P, _P],
+    'reg_spectral_resample': [_P, _P, _I, _P, _P, _P],
+    'reg_unet_create': [_I, _I, _P, _I, _I, ctypes.POINTER(_P)],
+    'reg_unet_destroy': [_P],
+    'reg_unet_set_stream': [_P, _P],
+    'reg_unet_param_count': [_P, ctypes.POINTER(ctypes.c_size_t)],
+    'reg_unet_set_params': [_P, _P],
+    'reg_unet_get_params': [_P, _P],
+    'reg_unet_forward': [_P, _P, _P],
+    'reg_unet_gradient': [_P, _P, _P, ctypes.POINTER(_D), _P],
+    'reg_unet_train_step': [_P, _P, _P, ctypes.c_float, ctypes.POINTER(_D)],
 }
 
 
@@ -118,6 +128,8 @@ def lib():
         l.reg_last_error.restype = ctypes.c_char_p
         l.reg_state_transport_noalloc.argtypes = [_I, _I, _I, _I, _P, _P, _P, _P]
         l.reg_state_transport_noalloc.restype = ctypes.c_int
+        l.reg_unet_last_error.argtypes = [_P]
+        l.reg_unet_last_error.restype = ctypes.c_char_p
         l.reg_status_string.argtypes = [_I]
         l.reg_status_string.restype = ctypes.c_char_p
         _lib = l
@@ -383,6 +395,137 @@ class Batch:
         if self._b and self._b.value:
             lib().reg_batch_destroy(self._b)
             self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def spectral_resample(x, shape_out, stream=None):
+    """reg_spectral_resample: Fourier resampling of x (c, n1, n2, n3) or
+    (n1, n2, n3) to the grid shape_out; returns a new CUDA tensor."""
+    scalar = x.dim() == 3
+    xs = x.unsqueeze(0) if scalar else x
+    c = xs.shape[0]
+    nin = (ctypes.c_int * 3)(*xs.shape[1:])
+    nout = (ctypes.c_int * 3)(*[int(v) for v in shape_out])
+    out = torch.empty((c,) + tuple(int(v) for v in shape_out), device=x.device,
+                      dtype=torch.float32)
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    s = lib().reg_spectral_resample(ctypes.cast(nin, _P), ctypes.cast(nout, _P), int(c),
+                                    _ptr(xs, None, 'x'), _ptr(out, None, 'out'),
+                                    ctypes.c_void_p(stream.cuda_stream))
+    if s != 0:
+        raise RegError(s, 'reg_spectral_resample failed')
+    return out[0] if scalar else out
+
+
+class UNet:
+    """reg_unet_*: the 3-D U-Net of the learned initial velocity.
+
+    x is a CUDA float32 tensor (cin, R, R, R); predictions and targets are
+    (cout, R, R, R).  Parameters are a flat float32 numpy array in the order
+    of include/reg.h (per layer: weights [kz][ky][kx][cin][cout], bias)."""
+
+    def __init__(self, R, channels=(16, 32, 64, 128), cin=2, cout=3):
+        self.R, self.channels, self.cin, self.cout = int(R), tuple(channels), cin, cout
+        ch = (ctypes.c_int * len(self.channels))(*self.channels)
+        self._u = ctypes.c_void_p()
+        s = lib().reg_unet_create(self.R, len(self.channels), ctypes.cast(ch, _P), cin, cout,
+                                  ctypes.byref(self._u))
+        if s != 0:
+            raise RegError(s, 'reg_unet_create failed')
+        n = ctypes.c_size_t()
+        self._call('reg_unet_param_count', ctypes.byref(n))
+        self.nparams = n.value
+
+    def _call(self, name, *args):
+        lib().reg_unet_set_stream(self._u, ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+        s = getattr(lib(), name)(self._u, *args)
+        if s != 0:
+            raise RegError(s, lib().reg_unet_last_error(self._u).decode())
+
+    def layer_shapes(self):
+        """(name, weight shape, bias shape) per layer, in parameter order."""
+        ch, L = self.channels, len(self.channels)
+        out, prev = [], self.cin
+        for l in range(L):
+            out.append(('enc%d.0' % l, (3, 3, 3, prev, ch[l]), (ch[l],)))
+            out.append(('enc%d.1' % l, (3, 3, 3, ch[l], ch[l]), (ch[l],)))
+            prev = ch[l]
+        for l in range(L - 2, -1, -1):
+            out.append(('dec%d.0' % l, (3, 3, 3, ch[l + 1] + ch[l], ch[l]), (ch[l],)))
+            out.append(('dec%d.1' % l, (3, 3, 3, ch[l], ch[l]), (ch[l],)))
+        out.append(('head', (1, 1, 1, ch[0], self.cout), (self.cout,)))
+        return out
+
+    def pack(self, params):
+        """Flat float32 array from a dict {'name.w': ..., 'name.b': ...}."""
+        import numpy as np
+        parts = []
+        for name, ws, bs in self.layer_shapes():
+            parts.append(np.asarray(params[name + '.w'], dtype=np.float32).reshape(-1))
+            parts.append(np.asarray(params[name + '.b'], dtype=np.float32).reshape(-1))
+        flat = np.concatenate(parts)
+        assert flat.size == self.nparams
+        return flat
+
+    def unpack(self, flat):
+        import numpy as np
+        out, o = {}, 0
+        for name, ws, bs in self.layer_shapes():
+            nw, nb = int(np.prod(ws)), int(np.prod(bs))
+            out[name + '.w'] = flat[o:o + nw].reshape(ws)
+            o += nw
+            out[name + '.b'] = flat[o:o + nb].reshape(bs)
+            o += nb
+        return out
+
+    def set_params(self, flat):
+        import numpy as np
+        a = np.ascontiguousarray(flat, dtype=np.float32)
+        assert a.size == self.nparams
+        self._call('reg_unet_set_params', a.ctypes.data_as(_P))
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.nparams, dtype=np.float32)
+        self._call('reg_unet_get_params', a.ctypes.data_as(_P))
+        return a
+
+    def _x(self, x):
+        return _ptr(x, (self.cin, self.R, self.R, self.R), 'x')
+
+    def forward(self, x, out=None):
+        if out is None:
+            out = torch.empty((self.cout, self.R, self.R, self.R), device=x.device)
+        self._call('reg_unet_forward', self._x(x), _ptr(out, (self.cout,) + (self.R,) * 3, 'y'))
+        return out
+
+    def gradient(self, x, target):
+        """(loss, flat FP32 gradient) of the mean squared error."""
+        import numpy as np
+        g = np.empty(self.nparams, dtype=np.float32)
+        loss = ctypes.c_double()
+        self._call('reg_unet_gradient', self._x(x),
+                   _ptr(target, (self.cout,) + (self.R,) * 3, 'target'), ctypes.byref(loss),
+                   g.ctypes.data_as(_P))
+        return loss.value, g
+
+    def train_step(self, x, target, lr, want_loss=True):
+        loss = ctypes.c_double()
+        self._call('reg_unet_train_step', self._x(x),
+                   _ptr(target, (self.cout,) + (self.R,) * 3, 'target'), ctypes.c_float(lr),
+                   ctypes.byref(loss) if want_loss else None)
+        return loss.value if want_loss else None
+
+    def close(self):
+        if self._u and self._u.value:
+            lib().reg_unet_destroy(self._u)
+            self._u = ctypes.c_void_p()
 
     def __del__(self):
         try:

@@ -25,6 +25,10 @@ Problems
   1.5 voxels and given additive N(0, 0.01^2) noise.
 * ``bandlimited`` -- random real fields with Fourier support |k|_2 <= kmax and
   unit RMS per component (search directions, test velocities).
+* ``phantom_problem_torch`` -- the phantom recipe above in torch on any
+  device, seeded through ``torch.Generator`` (a different random stream from
+  the NumPy version: same distribution, not the same draws), for the
+  thousands of pairs that train the learned initial velocity.
 """
 
 import numpy as np
@@ -145,3 +149,51 @@ def phantom_problem(shape, seed, max_disp_vox=8.0, kmax=6, sigma_vox=1.5,
         rho_R = rho_R + noise * np.random.default_rng(seed + 2).standard_normal(shape)
         rho_T = rho_T + noise * np.random.default_rng(seed + 3).standard_normal(shape)
     return rho_T, rho_R, u
+
+
+def phantom_problem_torch(shape, seed, device='cpu', max_disp_vox=8.0, kmax=6, sigma_vox=1.5,
+                          noise=0.01):
+    """(rho_T, rho_R, u) of the phantom recipe as float32 torch tensors on
+    `device`: ellipsoid geometry from NumPy's generator at `seed` (as
+    ``phantom_problem``), the displacement and the noise from a torch
+    generator seeded with `seed`."""
+    import torch
+    f64 = torch.float64
+    centre, axes = _ellipsoid_params(seed)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    n1, n2, n3 = shape
+    k1 = torch.fft.fftfreq(n1, 1.0 / n1, dtype=f64, device=device)[:, None, None]
+    k2 = torch.fft.fftfreq(n2, 1.0 / n2, dtype=f64, device=device)[None, :, None]
+    k3 = torch.fft.rfftfreq(n3, 1.0 / n3, dtype=f64, device=device)[None, None, :]
+    mask = (k1 ** 2 + k2 ** 2 + k3 ** 2) <= kmax * kmax
+    u = []
+    for _ in range(3):
+        w = torch.randn(shape, generator=gen, dtype=f64, device=device)
+        f = torch.fft.irfftn(torch.fft.rfftn(w) * mask, s=shape)
+        u.append(f / torch.sqrt(torch.mean(f * f)))
+    u = torch.stack(u)
+    u *= max_disp_vox * (TWO_PI / max(shape)) / torch.sqrt(torch.sum(u * u, dim=0)).max()
+    ax = [TWO_PI * torch.arange(n, dtype=f64, device=device) / n for n in shape]
+    x = torch.meshgrid(*ax, indexing='ij')
+
+    def phantom(p):
+        out = torch.zeros(shape, dtype=f64, device=device)
+        d = [torch.remainder(p[j] - float(centre[j]) + np.pi, TWO_PI) - np.pi for j in range(3)]
+        for scale, value in ((1.0, 0.2), (0.72, 0.5), (0.45, 0.9)):
+            r2 = sum((d[j] / (scale * float(axes[j]))) ** 2 for j in range(3))
+            out = torch.where(r2 <= 1.0, torch.full_like(out, value), out)
+        return out
+
+    g = torch.exp(-0.5 * (TWO_PI * sigma_vox) ** 2 *
+                  ((k1 / n1) ** 2 + (k2 / n2) ** 2 + (k3 / n3) ** 2))
+
+    def blur(f):
+        return torch.fft.irfftn(torch.fft.rfftn(f) * g, s=shape)
+
+    rho_R = blur(phantom(x))
+    rho_T = blur(phantom([x[j] + u[j] for j in range(3)]))
+    if noise > 0:
+        rho_R = rho_R + noise * torch.randn(shape, generator=gen, dtype=f64, device=device)
+        rho_T = rho_T + noise * torch.randn(shape, generator=gen, dtype=f64, device=device)
+    return rho_T.float(), rho_R.float(), u.float()

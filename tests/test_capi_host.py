@@ -74,3 +74,31 @@ def test_null_context_is_rejected(lib):
     assert lib.reg_set_stream(None, None) == 1
     assert lib.reg_hessian_matvec(None, None, None) == 1
     assert lib.reg_solve(None, None, None, None) == 1
+
+
+def test_unet_and_resample_reject_bad_arguments_before_touching_the_gpu(lib):
+    out = ctypes.c_void_p()
+    ch = (ctypes.c_int * 4)(16, 32, 64, 128)
+    cases = [(64, 0, ch, 2, 3),      # no levels
+             (64, 7, ch, 2, 3),      # too many levels
+             (60, 4, ch, 2, 3),      # R not divisible by 2^(L-1)
+             (4, 1, ch, 2, 3),       # R < 8
+             (64, 4, None, 2, 3),    # no channel list
+             (64, 4, ch, 0, 3),      # cin < 1
+             (64, 4, ch, 2, 200),    # cout > 128
+             (256, 4, ch, 2, 3)]     # R^3 above the GEMM grid limit
+    for R, L, c, ci, co in cases:
+        s = lib.reg_unet_create(R, L, ctypes.cast(c, ctypes.c_void_p) if c else None, ci, co,
+                                ctypes.byref(out))
+        assert s == 1, (R, L, ci, co, s)
+        assert out.value is None
+    bad = (ctypes.c_int * 4)(16, 0, 64, 128)
+    assert lib.reg_unet_create(64, 4, ctypes.cast(bad, ctypes.c_void_p), 2, 3,
+                               ctypes.byref(out)) == 1
+    n = (ctypes.c_int * 3)(8, 8, 8)
+    z = (ctypes.c_int * 3)(8, 0, 8)
+    p = ctypes.c_void_p(16)
+    assert lib.reg_spectral_resample(None, n, 1, p, p, None) == 1
+    assert lib.reg_spectral_resample(n, z, 1, p, p, None) == 1
+    assert lib.reg_spectral_resample(n, n, 0, p, p, None) == 1
+    assert lib.reg_spectral_resample(n, n, 1, None, p, None) == 1
