@@ -1,20 +1,26 @@
 """Benchmark: 256^3 registration time to solution on one GB300.
 
-A step is one complete inexact Gauss-Newton-Krylov registration (every step
+A step is one complete registration of the synthetic 256^3 brain-like
+phantom pair (nt = 8, H2, beta = 1e-3) by the full method: the U-Net's
+initial velocity (input images resampled to 64^3, prediction band-limited and
+resampled to 256^3), then the inexact Gauss-Newton-Krylov solve (every step
 of the path: semi-Lagrangian points, transports, spectral operators,
-gradient, Hessian matvecs, preconditioner, PCG, Armijo) of the synthetic
-256^3 brain-like phantom pair (nt = 8, H2, beta = 1e-3, FP32 interpolation
-and FFTs, FP64 reductions), from v = 0 to ||g|| <= 1e-2 ||g_0||.  Inputs are
-resident in HBM when the timed region starts; the working set (several GB)
-is far larger than the 129 MB L2, so no flush is needed between steps.
+gradient, Hessian matvecs, preconditioner, PCG, Armijo) in mixed precision
+(bf16 images and grad-rho copy, FP32 interpolation and FFTs, FP64
+reductions) to ||g|| <= 1e-2 ||g(v = 0)||.  --init zero --precision fp32 is
+the plain FP32 solver from v = 0; every other form is timed once after the
+main measurement ("arms").  Inputs are resident in HBM when the timed region
+starts; the working set (several GB) is far larger than the 129 MB L2, so no
+flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--init learned|zero] [--precision mixed_bf16|fp32]
 
 Prints one JSON line.  The timed region runs with the library's per-launch
-CUDA events on (they are captured into the PCG graph and read after every
-replay), which give the per-phase device times and the roofline figures.
-With --impl reference the FP64 CPU oracle is timed instead (see
-cpu_reference()).
+CUDA events on (the PCG iteration is then a graph replayed by the host, the
+events captured in it), which give the per-phase device times and the
+roofline figures.  With --impl reference the FP64 CPU oracle is timed
+instead (see cpu_reference()).
 """
 
 import argparse
@@ -38,6 +44,7 @@ NT = 8
 BETA = 1e-3
 KIND = 'H2'
 SEED = 3000
+WEIGHTS = os.path.join(ROOT, 'paper_1608_03630_gb300', 'weights', 'unet_r64.npz')
 PHASE_NAMES = ('departure', 'state', 'adjoint', 'incstate', 'incadj', 'interp', 'fft',
                'spectral', 'blas', 'other')
 
@@ -96,20 +103,21 @@ class ClockSampler:
                 'samples': len(sm)}
 
 
-def measured_traffic(phase, points):
+def measured_traffic(phase, points, precision):
     """DRAM bytes per launch of an interpolation kernel, from the committed
-    ncu summary (bytes per point at 192^3, scaled to `points`), or None when
-    the kernel source has changed since the capture."""
+    ncu summary (bytes per point at 192^3 for this precision, scaled to
+    `points`), or None when the kernel source has changed since the capture
+    or the kernel was not captured."""
     import hashlib
     import re
     try:
-        with open(os.path.join(ROOT, 'profiles', 'traffic_march_phantom192.md')) as f:
+        with open(os.path.join(ROOT, 'profiles', 'traffic_tile_phantom192.md')) as f:
             text = f.read()
         with open(os.path.join(ROOT, 'paper_1608_03630_gb300', 'csrc', 'transport.cu'), 'rb') as f:
             sha = hashlib.sha1(f.read()).hexdigest()[:12]
         if ('sha1 ' + sha) not in text:
             return None
-        m = re.search(r'traffic_bytes_per_point %s: ([0-9.]+)' % phase, text)
+        m = re.search(r'traffic_bytes_per_point %s %s: ([0-9.]+)' % (phase, precision), text)
         return float(m.group(1)) * points if m else None
     except OSError:
         return None
@@ -195,6 +203,13 @@ def cpu_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def unet_launches(channels):
+    """Kernels of one U-Net forward: input packing, 4L - 1 convolutions,
+    L - 1 poolings, upsamplings and skip copies, output unpacking."""
+    L = len(channels)
+    return 1 + (4 * L - 1) + 3 * (L - 1) + 1
+
+
 def gpu_bench(args):
     import torch
     import torch.distributed as dist
@@ -205,21 +220,38 @@ def gpu_bench(args):
         dist.init_process_group('nccl')
     torch.cuda.set_device(local)
     __graft_entry__.build()
-    from paper_1608_03630_gb300 import reg
+    from paper_1608_03630_gb300 import learned_init, reg
 
     rho_T, rho_R = make_inputs()
+    n = SHAPE[0] * SHAPE[1] * SHAPE[2]
+    learned = args.init == 'learned'
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         dT = torch.from_numpy(rho_T).cuda()
         dR = torch.from_numpy(rho_R).cuda()
         v = torch.zeros((3,) + SHAPE, device='cuda')
+        zero = torch.zeros((3,) + SHAPE, device='cuda')
+        gbuf = torch.empty((3,) + SHAPE, device='cuda')
+        net, info = learned_init.load(WEIGHTS) if learned else (None, None)
         R = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=args.precision,
                              stream=stream)
 
-        def step():
+        def solve_from_images(ctx, init):
+            """One registration from images on the device: for the learned
+            guess, ||g(0)|| for the stopping test, the network's prediction,
+            then the solve to ||g|| <= 1e-2 ||g(0)||."""
+            ctx.set_images(dT, dR, presmooth=True)
+            if init == 'learned':
+                ctx.gradient(zero, out=gbuf)
+                gref = ctx.inner(gbuf, gbuf) ** 0.5
+                v.copy_(learned_init.predict(net, info['scale'], dT, dR, SHAPE[0], info['kc'],
+                                             info['alpha']))
+                return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500, gnorm_ref=gref)
             v.zero_()
-            R.set_images(dT, dR, presmooth=True)
-            return R.solve(v, gtol=1e-2, max_gn=50, max_pcg=500)
+            return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500)
+
+        def step():
+            return solve_from_images(R, args.init)
 
         for _ in range(args.warmup):
             step()
@@ -247,7 +279,8 @@ def gpu_bench(args):
             elapsed_ms = float(t.item())
             dist.barrier()
 
-        # end to end through the host-buffer entry point (H2D images + v, D2H v)
+        # end to end through the public API: pinned host images in, the
+        # velocity back to pinned host memory, every step
         hT = torch.from_numpy(rho_T).pin_memory()
         hR = torch.from_numpy(rho_R).pin_memory()
         hv = torch.zeros((3,) + SHAPE).pin_memory()
@@ -255,34 +288,43 @@ def gpu_bench(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            hv.zero_()
-            R.solve_host(hT, hR, hv, presmooth=True, gtol=1e-2, max_gn=50, max_pcg=500)
+            dT.copy_(hT, non_blocking=True)
+            dR.copy_(hR, non_blocking=True)
+            solve_from_images(R, args.init)
+            hv.copy_(v, non_blocking=True)
+            torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
-        R.close()
 
-        # the other precision, one solve, for the same stopping test
-        other = 'fp32' if args.precision == 'mixed_bf16' else 'mixed_bf16'
-        R2 = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=other, stream=stream)
-        R2.set_images(dT, dR, presmooth=True)
-        v.zero_()
-        R2.solve(v, gtol=1e-2, max_gn=50, max_pcg=500)     # warm-up (plans, graphs)
-        v.zero_()
-        R2.set_images(dT, dR, presmooth=True)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, st_other = R2.solve(v, gtol=1e-2, max_gn=50, max_pcg=500)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        other_line = {'precision': other, 'time_to_solution_s': e0.elapsed_time(e1) / 1e3,
-                      'gn_iters': st_other['gn_iters'], 'matvecs': st_other['matvecs'],
-                      'gnorm_rel': st_other['gnorm_rel'], 'mismatch_rel': st_other['mismatch_rel']}
-        R2.close()
+        # the other forms of the method, one timed solve each after a warm-up,
+        # to the same stopping test (the plain FP32 solver is the target's
+        # comparison)
+        arms = {}
+        ctxs = {args.precision: R}
+        for name, init, prec in (('plain_fp32', 'zero', 'fp32'),
+                                 ('zero_mixed_bf16', 'zero', 'mixed_bf16'),
+                                 ('learned_fp32', 'learned', 'fp32'),
+                                 ('learned_mixed_bf16', 'learned', 'mixed_bf16')):
+            if (init == args.init and prec == args.precision) or (init == 'learned' and not net):
+                continue
+            if prec not in ctxs:
+                ctxs[prec] = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=prec,
+                                              stream=stream)
+            solve_from_images(ctxs[prec], init)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, st = solve_from_images(ctxs[prec], init)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            arms[name] = {'time_to_solution_s': e0.elapsed_time(e1) / 1e3,
+                          'gn_iters': st['gn_iters'], 'matvecs': st['matvecs'],
+                          'gnorm_rel': st['gnorm_rel'], 'mismatch_rel': st['mismatch_rel']}
+        for c in ctxs.values():
+            c.close()
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return
-    n = SHAPE[0] * SHAPE[1] * SHAPE[2]
     per_step_s = elapsed_ms / 1e3 / args.steps
     value = per_step_s / world          # whole job: seconds per registration
     last = stats[-1]
@@ -299,22 +341,32 @@ def gpu_bench(args):
     sb = timing['spectral']['bytes']
     sms = timing['spectral']['ms']
     launches = sum(int(v['launches']) for k, v in timing.items() if k != 'fft')
+    if learned:
+        # per step: the network forward and three Fourier resamplings
+        launches += args.steps * (unet_launches(net.channels) + 3)
     counts = {'gradient_evals': last['gradient_evals'], 'matvecs': last['matvecs'],
               'objective_evals': last['objective_evals']}
+    form = '%s guess, %s' % (args.init, args.precision)
     line = {
         'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world,
         'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': per_step_s * 1e3,
         'higher_is_better': False, 'scaling': 'weak', 'vs_baseline': None,
         'dtype': 'f32', 'data': 'synthetic',
-        'config': {'workload': 'phantom 256^3 nt=8 H2 beta=1e-3 %s' % args.precision,
+        'config': {'workload': 'phantom 256^3 nt=8 H2 beta=1e-3, %s' % form,
+                   'init': (('U-Net (64^3, 16/32/64/128, bf16) prediction, modes |k|<%s, '
+                             'x%.2f' % (info['kc'], info['alpha'])) if learned else 'v = 0'),
                    'storage': ('bf16 images, bf16 grad-rho cache in the matvec, fp32 fields'
                                if args.precision == 'mixed_bf16' else 'fp32'),
                    'grid': list(SHAPE), 'nt': NT, 'beta': BETA, 'regularisation': KIND,
-                   'gtol': 1e-2, 'precision': args.precision, 'parallelism': 'replicas',
+                   'gtol': '1e-2 of ||g(v=0)||', 'precision': args.precision,
+                   'parallelism': 'replicas',
                    'l2': 'inputs larger than L2 (working set > 4 GB), no flush'},
         'solve': {'gn_iters': last['gn_iters'], 'pcg_iters': last['pcg_iters'],
                   'matvecs': last['matvecs'], 'gnorm_rel': last['gnorm_rel'],
                   'mismatch_rel': last['mismatch_rel']},
+        'arms': arms,
+        'speedup_vs_plain_fp32': (arms['plain_fp32']['time_to_solution_s'] / value
+                                  if 'plain_fp32' in arms else 1.0),
         'matvecs_per_s': matvecs / (elapsed_ms / 1e3),
         'interp_gbs': ib / (ims / 1e3) / 1e9 if ims > 0 else None,
         'spectral_gbs': sb / (sms / 1e3) / 1e9 if sms > 0 else None,
@@ -322,21 +374,20 @@ def gpu_bench(args):
         'roofline': {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': peak,
                      'unit': 'GB/s', 'frac': achieved / peak, 'peak_source': peak_kind,
                      'bytes_per_launch': d['bytes'] / max(1, d['launches']),
-                     'traffic': measured_traffic(dom, n)},
-        'other_precision': other_line,
+                     'traffic': measured_traffic(dom, n, args.precision)},
         'gpu_launches': launches,
         'clocks': clk,
-        'e2e': {'value': e2e_s, 'unit': UNIT, 'h2d_bytes_per_step': 4 * n * 2 + 12 * n,
+        'e2e': {'value': e2e_s, 'unit': UNIT, 'h2d_bytes_per_step': 4 * n * 2,
                 'd2h_bytes_per_step': 12 * n},
     }
     if world == 1 and not args.no_cpu_baseline:
-        line['cpu_baseline'] = cpu_oracle_sample(args.precision, counts)
+        line['cpu_baseline'] = cpu_oracle_sample(form, counts)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def profile_matvec(n, nt, count):
+def profile_matvec(n, nt, count, precision):
     """A short, fixed launch sequence for ncu captures: one gradient and
     `count` Hessian matvecs of the phantom problem at n^3 (no timing)."""
     import torch
@@ -347,7 +398,7 @@ def profile_matvec(n, nt, count):
     shape = (n, n, n)
     rho_T, rho_R, u = synth.phantom_problem(shape, SEED)
     w = synth.bandlimited(shape, 6, 1001)
-    R = reg.Registration(shape, nt, BETA, KIND, False)
+    R = reg.Registration(shape, nt, BETA, KIND, False, precision=precision)
     R.set_images(torch.from_numpy(rho_T.astype(np.float32)).cuda(),
                  torch.from_numpy(rho_R.astype(np.float32)).cuda(), True)
     R.gradient(torch.from_numpy((0.5 * u).astype(np.float32)).cuda())
@@ -411,6 +462,8 @@ def main():
     ap.add_argument('--warmup', type=int, default=3)
     ap.add_argument('--impl', default='gpu', choices=['gpu', 'reference'])
     ap.add_argument('--precision', default='mixed_bf16', choices=['fp32', 'mixed_bf16'])
+    ap.add_argument('--init', default='learned', choices=['learned', 'zero'],
+                    help='initial velocity: the trained U-Net prediction or v = 0')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='phantom256', choices=['phantom256', 'batched'])
     ap.add_argument('--pairs', type=int, default=48)
@@ -418,7 +471,7 @@ def main():
                     help='run one gradient and two matvecs at N^3 (nt = 4) for ncu, then exit')
     args = ap.parse_args()
     if args.profile_matvec:
-        profile_matvec(args.profile_matvec, 4, 2)
+        profile_matvec(args.profile_matvec, 4, 2, args.precision)
     elif args.workload == 'batched' and args.impl != 'reference':
         batched_bench(args)
     elif args.impl == 'reference':

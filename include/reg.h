@@ -140,7 +140,13 @@ typedef struct {
     double armijo_c;      /* sufficient-decrease constant               (1e-4) */
     double armijo_shrink; /* step reduction factor                       (0.5) */
     int armijo_max;       /* line-search trials                           (10) */
-    int use_graph;        /* capture the PCG iteration in a CUDA graph     (1) */
+    int use_graph;        /* 2: the whole PCG solve is one CUDA graph with a
+                             device-side while-loop (stopping tests on the
+                             GPU, one host wait per Newton step); 1: one
+                             graph per PCG iteration, tests on the host;
+                             0: plain launches.  2 falls back to 1 when
+                             phase timing is on or the driver refuses the
+                             conditional node                            (2) */
     int verbose;          /* print one line per Newton iteration to stderr (0) */
     double gnorm_ref;     /* > 0: use it as ||g_0|| in the stop test and the
                              forcing term, e.g. the gradient norm at v = 0
@@ -238,8 +244,10 @@ int reg_inner(reg_ctx* ctx, const float* a, const float* b, size_t count,
 /* ------------------------------------------------------------- tuning */
 
 /* Tile of the interpolation kernels: each thread walks k points (multiple of
- * 4, 4..64) along x1 and a block is 32 x wy threads (wy in 1, 2, 4, 8) over
- * (x3, x2).  The default is k = 16, wy = 8.  Results do not depend on the tile. */
+ * 4, 4..64) along x1 and a block is 32 x wy threads (wy in 1, 2, 4, 8, 16)
+ * over (x3, x2).  wy = 16 runs only the shared-memory staged kernel (max
+ * displacement up to 3 cells; beyond that the call uses wy = 8).  The default
+ * is k = 8, wy = 8.  Results do not depend on the tile. */
 int reg_set_tile(reg_ctx* ctx, int k, int wy);
 int reg_get_tile(const reg_ctx* ctx, int* k, int* wy);
 

@@ -83,7 +83,7 @@ int reg_autotune(reg_ctx* c, int* k_out, int* wy_out) {
     const Tile keep = c->tile;
     const bool timing = c->timing;
     c->timing = false;
-    static const int cand[][2] = {{4, 8}, {8, 8}, {16, 8}, {8, 4}, {16, 4}};
+    static const int cand[][2] = {{4, 8}, {8, 8}, {16, 8}, {8, 4}, {16, 4}, {8, 16}, {16, 16}};
     float best = 1e30f;
     int bk = keep.k, bw = keep.wy;
     for (const auto& kw : cand) {

@@ -145,6 +145,9 @@ struct Tile {
 
 // Largest shared-memory box (floats) of the staged interpolation kernel.
 constexpr int kMaxBoxFloats = 18432;
+// Blocks of 16 rows (512 threads) stage up to this many floats (110 KB: two
+// resident blocks, 32 warps, per SM).
+constexpr int kMaxBoxFloats16 = 28224;
 
 // out[0] = max over i < count of |d[i]| as float bits (d: 3 components).
 cudaError_t launch_absmax(const float* d, long long count, unsigned int* out, cudaStream_t st);

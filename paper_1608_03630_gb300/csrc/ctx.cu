@@ -224,8 +224,13 @@ int op_halo(reg_ctx* c, const float* d, int* halo) {
 Tile tile_with(const reg_ctx* c, int halo) {
     Tile t = c->tile;
     t.halo = halo;
+    // 16-row blocks exist only as the fixed-halo staged kernel (halo <= 3)
+    if (t.wy == 16 && halo > 3) t.wy = 8;
     while (!tile_staged(t) && t.k > 4) t.k = ((t.k / 2) + 3) & ~3;
-    if (!tile_staged(t)) t = c->tile;   // register-window kernel, configured tile
+    if (!tile_staged(t)) {   // register-window kernel, configured tile
+        t = c->tile;
+        if (t.wy == 16) t.wy = 8;
+    }
     return t;
 }
 
@@ -536,7 +541,7 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
     c->stream = nullptr;
     const long long n = c->g.n;
     const long long nc = c->g.nc;
-    c->tile.k = 16;
+    c->tile.k = 8;
     c->tile.wy = 8;
     c->halo_fwd = c->halo_adj = -1;
     // partial sums: the largest marching grid (k = 4, wy = 1), or up to
@@ -843,8 +848,9 @@ int reg_inner(reg_ctx* c, const float* a, const float* b, size_t count, double* 
 
 int reg_set_tile(reg_ctx* c, int k, int wy) {
     CHECK_CTX(c);
-    if (k < 4 || k > 64 || (k & 3) || !(wy == 1 || wy == 2 || wy == 4 || wy == 8))
-        return fail(c, REG_EINVAL, "tile: k must be a multiple of 4 in [4, 64], wy in {1,2,4,8}");
+    if (k < 4 || k > 64 || (k & 3) || !(wy == 1 || wy == 2 || wy == 4 || wy == 8 || wy == 16))
+        return fail(c, REG_EINVAL,
+                    "tile: k must be a multiple of 4 in [4, 64], wy in {1,2,4,8,16}");
     c->tile.k = k;
     c->tile.wy = wy;
     return REG_OK;

@@ -131,7 +131,9 @@ int ensure_solver(reg_ctx* c);
 enum {
     SC_JMIS = 0, SC_JREG = 1, SC_J = 2, SC_TMP = 3,
     SC_RZ = 4, SC_PQ = 5, SC_RR = 6, SC_RZNEW = 7, SC_GG = 8, SC_GS = 9,
-    SC_INNER = 10, SC_ZERO = 11, SC_PAP = 12, SC_PB = 13
+    SC_INNER = 10, SC_ZERO = 11, SC_PAP = 12, SC_PB = 13,
+    // device-controlled PCG loop: iteration count, exit flag, tol^2, cap
+    SC_IT = 20, SC_FLAG = 21, SC_TOL2 = 22, SC_MAXIT = 23
 };
 
 }  // namespace reg

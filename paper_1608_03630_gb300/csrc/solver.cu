@@ -13,9 +13,13 @@
 // Per PCG iteration the matvec needs p in physical space (one C2R of three
 // fields) for the transports and b~ in Fourier space (one R2C); every inner
 // product is taken by Parseval in FP64.  The scalars live in device memory:
-// one iteration is a fixed launch sequence, captured once into a CUDA graph
-// (use_graph = 1) and replayed; the host reads p.Hp and ||r|| once per
-// iteration for the curvature and stopping tests.
+// one iteration is a fixed launch sequence.  use_graph = 2 (default): the
+// whole PCG solve is one CUDA graph, the iteration's launches as the body of
+// a conditional while-node whose condition a one-thread kernel sets from the
+// device scalars (curvature, residual, finiteness, iteration cap), so the
+// host waits once per Newton step.  use_graph = 1: the iteration is a graph
+// replayed by the host, which reads p.Hp and ||r|| after each one.
+// use_graph = 0: plain launches.
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -77,7 +81,85 @@ static int pcg_iteration(reg_ctx* c) {
 
 struct PcgResult { int iters; bool neg_curv; bool converged; };
 
-static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, int verbose,
+enum { PCG_RUN = 0, PCG_CONVERGED = 1, PCG_NEGCURV = 2, PCG_NONFINITE = 3, PCG_MAXIT = 4 };
+
+__global__ void k_pcg_setup(double* dsc, double tol2, int max_it) {
+    dsc[SC_IT] = 0.0;
+    dsc[SC_FLAG] = PCG_RUN;
+    dsc[SC_TOL2] = tol2;
+    dsc[SC_MAXIT] = max_it;
+}
+
+// The stopping tests of one PCG iteration, in the host loop's order; a zero
+// condition ends the graph's while-loop.  The cap max_it bounds the loop.
+__global__ void k_pcg_control(double* dsc, cudaGraphConditionalHandle h) {
+    const double it = dsc[SC_IT] + 1.0;
+    dsc[SC_IT] = it;
+    const double pq = dsc[SC_PQ], rr = dsc[SC_RR];
+    int flag = PCG_RUN;
+    if (!isfinite(pq) || !isfinite(rr)) flag = PCG_NONFINITE;
+    else if (pq <= 0.0) flag = PCG_NEGCURV;
+    else if (rr <= dsc[SC_TOL2]) flag = PCG_CONVERGED;
+    else if (it >= dsc[SC_MAXIT]) flag = PCG_MAXIT;
+    dsc[SC_FLAG] = flag;
+    cudaGraphSetConditional(h, flag == PCG_RUN ? 1u : 0u);
+}
+
+// The PCG loop as one executable graph (a while-node around the iteration),
+// or nullptr (with the context's error state untouched) when the driver does
+// not take it.
+static cudaGraphExec_t build_pcg_loop(reg_ctx* c) {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle h;
+    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess &&
+              cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) ==
+                  cudaSuccess;
+    cudaGraph_t body = nullptr;
+    if (ok) {
+        cudaGraphNodeParams p = {};
+        p.type = cudaGraphNodeTypeConditional;
+        p.conditional.handle = h;
+        p.conditional.type = cudaGraphCondTypeWhile;
+        p.conditional.size = 1;
+        cudaGraphNode_t node;
+        ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) == cudaSuccess;
+        if (ok) body = p.conditional.phGraph_out[0];
+    }
+    if (ok) {
+        cudaStream_t user = c->stream;
+        ok = bind_stream(c, c->capture_stream) == REG_OK;
+        if (ok && cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                                cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            int s = pcg_iteration(c);
+            if (s == REG_OK) {
+                k_pcg_control<<<1, 1, 0, c->stream>>>(c->dsc, h);
+                if (cudaGetLastError() != cudaSuccess) s = REG_ECUDA;
+            }
+            cudaGraph_t captured = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(c->stream, &captured);
+            ok = s == REG_OK && e == cudaSuccess;
+        } else {
+            ok = false;
+        }
+        if (bind_stream(c, user) != REG_OK) ok = false;
+    }
+    if (ok && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        exec = nullptr;
+        ok = false;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        c->dead = false;   // a refused capture is not a device fault
+        c->err.clear();
+    }
+    return exec;
+}
+
+static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verbose,
                      PcgResult* res) {
     const int nb = blas_blocks();
     const int proj = c->incompressible;
@@ -96,6 +178,34 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, bool use_graph, int ver
         fprintf(stderr, "  pcg 0  rr %.6e  rz %.6e  pap %.6e  tol %.6e\n", c->hsc[SC_RR],
                 c->hsc[SC_RZ], c->hsc[SC_PAP], tol);
     if (std::sqrt(c->hsc[SC_RR]) <= tol) { res->converged = true; return REG_OK; }
+
+    if (use_graph >= 2 && !c->timing && verbose <= 1) {
+        cudaGraphExec_t loop = build_pcg_loop(c);
+        if (loop) {
+            int status = REG_OK;
+            k_pcg_setup<<<1, 1, 0, c->stream>>>(c->dsc, tol * tol, max_it);
+            cudaError_t e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaGraphLaunch(loop, c->stream);
+            if (e != cudaSuccess) status = fail_cuda(c, e, "PCG loop launch", __LINE__);
+            if (status == REG_OK) status = read_scalars(c, 0, SC_MAXIT + 1);
+            cudaGraphExecDestroy(loop);
+            if (status != REG_OK) return status;
+            res->iters = (int)c->hsc[SC_IT];
+            const int flag = (int)c->hsc[SC_FLAG];
+            if (flag == PCG_NONFINITE) return fail(c, REG_ENONFINITE, "non-finite value in PCG");
+            res->converged = flag == PCG_CONVERGED;
+            if (flag == PCG_NEGCURV) {
+                res->neg_curv = true;
+                if (res->iters == 1) {
+                    // first direction: the preconditioned steepest-descent step
+                    e = launch_sp_direction(c->g, S[S_R], S[S_S], nullptr, c->dsc, SC_ZERO, SC_RZ,
+                                            1, c->beta, c->kind, proj, c->partials, nb, c->stream);
+                    if (e != cudaSuccess) return fail_cuda(c, e, "launch_sp_direction", __LINE__);
+                }
+            }
+            return REG_OK;
+        }
+    }
 
     cudaGraphExec_t exec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -237,7 +347,7 @@ static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solv
         const double ratio = gn / g0;
         const double eta = std::fmin(0.5, o->forcing == 1 ? std::sqrt(ratio) : ratio);
         PcgResult pr;
-        REG_TRY(pcg_solve(c, eta * gn, o->max_pcg, o->use_graph != 0, o->verbose, &pr));
+        REG_TRY(pcg_solve(c, eta * gn, o->max_pcg, o->use_graph, o->verbose, &pr));
         st->pcg_iters += pr.iters;
         st->matvecs += pr.iters;
         st->negative_curvature += pr.neg_curv ? 1 : 0;
@@ -298,7 +408,7 @@ int reg_solve_opts_default(reg_solve_opts* o) {
     o->armijo_c = 1e-4;
     o->armijo_shrink = 0.5;
     o->armijo_max = 10;
-    o->use_graph = 1;
+    o->use_graph = 2;
     o->verbose = 0;
     o->gnorm_ref = 0.0;
     return REG_OK;

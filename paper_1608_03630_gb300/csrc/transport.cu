@@ -559,9 +559,10 @@ cudaError_t run_tile_fixed(const Dims& g, Tile t, const float* f, const float* d
     constexpr int P3 = ((35 + 2 * H) + 31) & ~31;
     const size_t smem = sizeof(float) * (size_t)(t.k + 3 + 2 * H) * E2 * P3;
     if (smem > 48 * 1024) {
+        const int cap = WY >= 16 ? kMaxBoxFloats16 : kMaxBoxFloats;
         const cudaError_t e = cudaFuncSetAttribute(k_tile_fixed<Epi, H, WY>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)(sizeof(float) * kMaxBoxFloats));
+                                                   (int)(sizeof(float) * cap));
         if (e != cudaSuccess) return e;
     }
     k_tile_fixed<Epi, H, WY><<<march_grid(g, t), dim3(32, WY), smem, st>>>(g, t.k, f, d, epi);
@@ -575,7 +576,15 @@ dim3 march_grid(const Dims& g, Tile t) {
 template <class Epi>
 cudaError_t run_march(const Dims& g, Tile t, const float* f, const float* d, const Epi& epi,
                       cudaStream_t st) {
-    if (t.k < 4 || (t.k & 3) || t.wy < 1 || 32 * t.wy > 256) return cudaErrorInvalidValue;
+    if (t.k < 4 || (t.k & 3) || t.wy < 1) return cudaErrorInvalidValue;
+    if (t.wy == 16) {
+        // 16-row blocks exist only as the fixed-halo staged kernel
+        if (!tile_staged(t) || t.halo > 3) return cudaErrorInvalidValue;
+        if (t.halo <= 1) return run_tile_fixed<Epi, 1, 16>(g, t, f, d, epi, st);
+        if (t.halo == 2) return run_tile_fixed<Epi, 2, 16>(g, t, f, d, epi, st);
+        return run_tile_fixed<Epi, 3, 16>(g, t, f, d, epi, st);
+    }
+    if (32 * t.wy > 256) return cudaErrorInvalidValue;
     if (tile_staged(t) && t.wy == 8 && t.halo <= 3) {
         if (t.halo <= 1) return run_tile_fixed<Epi, 1, 8>(g, t, f, d, epi, st);
         if (t.halo == 2) return run_tile_fixed<Epi, 2, 8>(g, t, f, d, epi, st);
@@ -693,7 +702,8 @@ bool tile_staged(const Tile& t) {
     if (t.halo < 0) return false;
     const int H = t.halo < 1 ? 1 : t.halo;   // halo 0 runs the H = 1 kernel
     const long long E3 = 35 + 2 * H, P3 = (E3 + 31) & ~31LL;
-    return E3 <= 96 && (t.k + 3 + 2LL * H) * (t.wy + 3 + 2LL * H) * P3 <= kMaxBoxFloats;
+    const long long cap = t.wy >= 16 ? kMaxBoxFloats16 : kMaxBoxFloats;
+    return E3 <= 96 && (t.k + 3 + 2LL * H) * (t.wy + 3 + 2LL * H) * P3 <= cap;
 }
 
 int march_blocks(const Dims& g, Tile t) {

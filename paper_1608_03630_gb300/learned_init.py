@@ -15,7 +15,9 @@ voxels;
 H2 regularisation, beta = 1e-3, nt = 8.  Training pairs are generated and
 solved at ``gen`` points per axis; the network input is (rho_T, rho_R) and its
 target the solution velocity, both resampled to ``res`` points per axis and
-the target divided by a fixed scale (the RMS of the training velocities).  A
+the target divided by a fixed scale (the RMS of the training velocities).  The
+prediction keeps only the Fourier modes |k_j| < kc and is multiplied by alpha,
+(kc, alpha) chosen on pairs of their own by the objective J(v0) / J(0).  A
 held-out pair at the evaluation grid is solved twice, from v = 0 and from the
 upsampled prediction, both to ||g|| <= gtol ||g(v = 0)||, so both stop at the
 same absolute gradient norm.
@@ -187,50 +189,102 @@ def train(net, X, V, scale, epochs, lr, seed=0, val=None, budget_s=None, log=pri
     return hist
 
 
-def evaluate(net, scale, seeds, n, nt=8, beta=1e-3, gtol=1e-2, log=print):
-    """Zero versus learned initial guess on held-out pairs at n^3."""
-    res = net.R
+def predict(net, scale, rho_T, rho_R, n, kc=None, alpha=1.0):
+    """Initial velocity at n^3: the network at its grid, times alpha * scale,
+    keeping the Fourier modes |k_j| < kc (the H2-regularised solutions carry
+    almost all their energy there; the network's error outside them would
+    cost beta |k|^4 in the objective), resampled to n^3."""
+    y = net.forward(net_input(rho_T, rho_R, net.R))
+    y.mul_(alpha * scale)
+    if kc is not None and 2 * kc < net.R:
+        y = reg.spectral_resample(y, (2 * kc,) * 3)
+    if y.shape[1] != n:
+        y = reg.spectral_resample(y, (n, n, n))
+    return y.contiguous()
+
+
+def select_cutoff(net, scale, seeds, n, cutoffs=(4, 6, 8, 12, 16, 32), alphas=(0.6, 0.8, 1.0),
+                  nt=8, beta=1e-3, log=print):
+    """The (kc, alpha) with the smallest mean J(v0) / J(0) over the pairs
+    `seeds` at n^3 (pairs used for nothing else)."""
     shape = (n, n, n)
     ctx = reg.Registration(shape, nt, beta, 'H2')
-    out = []
+    table = {}
     for seed in seeds:
         rho_T, rho_R, _ = phantom(n, seed)
         rho_T, rho_R = rho_T.contiguous(), rho_R.contiguous()
         ctx.set_images(rho_T, rho_R, presmooth=True)
-        zero = torch.zeros((3,) + shape, device='cuda')
-        g, _ = ctx.gradient(zero)
-        gref = math.sqrt(ctx.inner(g, g))
-        rec = {'seed': int(seed)}
-        for mode in ('zero', 'learned'):
+        j0 = ctx.objective(torch.zeros((3,) + shape, device='cuda'))
+        for kc in cutoffs:
+            base = predict(net, scale, rho_T, rho_R, n, kc, 1.0)
+            for a in alphas:
+                table.setdefault((kc, a), []).append(ctx.objective((a * base).contiguous()) / j0)
+    ctx.close()
+    mean = {k: float(np.mean(v)) for k, v in table.items()}
+    best = min(mean, key=mean.get)
+    if log:
+        log('J(v0)/J(0) by (kc, alpha): ' +
+            ', '.join('%s: %.3f' % (k, v) for k, v in sorted(mean.items())))
+    return best, {'%d,%.2f' % k: v for k, v in mean.items()}
+
+
+ARMS = (('plain', 'zero', 'fp32'), ('learned_fp32', 'learned', 'fp32'),
+        ('mixed', 'zero', 'mixed_bf16'), ('learned_mixed', 'learned', 'mixed_bf16'))
+
+
+def evaluate(net, scale, seeds, n, kc=None, alpha=1.0, nt=8, beta=1e-3, gtol=1e-2,
+             arms=ARMS, log=print):
+    """Each arm (name, initial guess 'zero' | 'learned', precision) solves the
+    held-out pairs at n^3 to ||g|| <= gtol ||g(0)||, g(0) the FP32 gradient at
+    v = 0.  Per arm and pair: the solver's statistics, the wall time from the
+    images on the device to the solution (network, resampling and solve), and
+    the final v checked in FP32 (J_fp32, gnorm_rel_fp32)."""
+    shape = (n, n, n)
+    ctxs = {p: reg.Registration(shape, nt, beta, 'H2', precision=p)
+            for p in sorted({a[2] for a in arms} | {'fp32'})}
+    c32 = ctxs['fp32']
+    out = []
+    for seed in seeds:
+        rho_T, rho_R, _ = phantom(n, seed)
+        rho_T, rho_R = rho_T.contiguous(), rho_R.contiguous()
+        for c in ctxs.values():
+            c.set_images(rho_T, rho_R, presmooth=True)
+        g, _ = c32.gradient(torch.zeros((3,) + shape, device='cuda'))
+        gref = math.sqrt(c32.inner(g, g))
+        rec = {'seed': int(seed), 'gnorm_ref': gref}
+        for name, init, prec in arms:
+            ctx = ctxs[prec]
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            if mode == 'zero':
+            if init == 'zero':
                 v = torch.zeros((3,) + shape, device='cuda')
             else:
-                y = net.forward(net_input(rho_T, rho_R, res))
-                y.mul_(scale)
-                v = y if n == res else reg.spectral_resample(y, shape)
-                v = v.contiguous()
+                v = predict(net, scale, rho_T, rho_R, n, kc, alpha)
             s, st = ctx.solve(v, gtol=gtol, gnorm_ref=gref)
             torch.cuda.synchronize()
             st['seconds'] = time.perf_counter() - t0
             st['status'] = s
-            rec[mode] = st
+            gv, jv = c32.gradient(v)
+            st['J_fp32'] = jv
+            st['gnorm_rel_fp32'] = math.sqrt(c32.inner(gv, gv)) / gref
+            rec[name] = st
         out.append(rec)
         if log:
-            z, l = rec['zero'], rec['learned']
-            log('eval seed %d: zero gn %d mv %d %.3f s mis %.4f | learned gn %d mv %d %.3f s '
-                'mis %.4f' % (seed, z['gn_iters'], z['matvecs'], z['seconds'], z['mismatch_rel'],
-                              l['gn_iters'], l['matvecs'], l['seconds'], l['mismatch_rel']))
-    ctx.close()
+            log('eval seed %d: ' % seed + ' | '.join(
+                '%s gn %d mv %d %.3f s J %.5e' % (name, rec[name]['gn_iters'],
+                                                  rec[name]['matvecs'], rec[name]['seconds'],
+                                                  rec[name]['J_fp32'])
+                for name, _, _ in arms))
+    for c in ctxs.values():
+        c.close()
     return out
 
 
-def summarise(evals):
-    def agg(mode, key):
-        return float(np.mean([e[mode][key] for e in evals]))
-    keys = ('gn_iters', 'pcg_iters', 'matvecs', 'seconds', 'mismatch_rel', 'gnorm_rel')
-    return {mode: {k: agg(mode, k) for k in keys} for mode in ('zero', 'learned')}
+def summarise(evals, arms=ARMS):
+    keys = ('gn_iters', 'pcg_iters', 'matvecs', 'seconds', 'mismatch_rel', 'gnorm_rel',
+            'J_fp32', 'gnorm_rel_fp32')
+    return {name: {k: float(np.mean([e[name][k] for e in evals])) for k in keys}
+            for name, _, _ in arms}
 
 
 def he_normal(net, seed):
@@ -244,18 +298,23 @@ def he_normal(net, seed):
     return np.concatenate(parts).astype(np.float32)
 
 
-def save_params(path, net, scale, meta):
+def save_params(path, net, scale, meta, kc=None, alpha=1.0):
     np.savez(path, params=net.get_params().astype(np.float16), scale=np.float64(scale),
              channels=np.array(net.channels), res=np.int64(net.R),
+             kc=np.int64(0 if kc is None else kc), alpha=np.float64(alpha),
              meta=np.array(json.dumps(meta)))
 
 
 def load(path):
-    """A trained reg.UNet and its velocity scale from save_params' file."""
+    """(net, info) from save_params' file: a reg.UNet holding the trained
+    parameters and {'scale', 'kc', 'alpha', 'meta'} for predict()."""
     d = np.load(path)
     net = reg.UNet(int(d['res']), tuple(int(c) for c in d['channels']))
     net.set_params(d['params'].astype(np.float32))
-    return net, float(d['scale'])
+    kc = int(d['kc']) if 'kc' in d and int(d['kc']) > 0 else None
+    alpha = float(d['alpha']) if 'alpha' in d else 1.0
+    return net, {'scale': float(d['scale']), 'kc': kc, 'alpha': alpha,
+                 'meta': json.loads(str(d['meta']))}
 
 
 def main(argv=None):
@@ -271,9 +330,13 @@ def main(argv=None):
     ap.add_argument('--lr', type=float, default=1e-3)
     ap.add_argument('--eval', type=int, default=50)
     ap.add_argument('--eval-n', type=int, default=256)
+    ap.add_argument('--select', type=int, default=8,
+                    help='pairs (at the evaluation grid) that choose the cutoff and scale')
+    ap.add_argument('--select-seed', type=int, default=7300)
     ap.add_argument('--eval-large', type=int, default=0, help='grid of one more held-out pair')
     ap.add_argument('--eval-large-seed', type=int, default=7100)
     ap.add_argument('--train-seed', type=int, default=5000)
+    ap.add_argument('--val-seed', type=int, default=7200)
     ap.add_argument('--eval-seed', type=int, default=7000)
     ap.add_argument('--out', default='learned_init_out')
     ap.add_argument('--load', default=None, help='skip training: evaluate these parameters')
@@ -287,18 +350,21 @@ def main(argv=None):
         logf.flush()
 
     report = {'args': vars(a)}
+    meta, info = {}, None
     if a.load:
-        net, scale = load(a.load)
+        net, info = load(a.load)
+        scale, meta = info['scale'], info['meta']
     else:
         ch = tuple(int(c) for c in a.channels.split(','))
         t0 = time.perf_counter()
-        X, V, gstats = generate(a.pairs + a.val, a.gen, a.res, a.train_seed, log=log)
+        X, V, gstats = generate(a.pairs, a.gen, a.res, a.train_seed, log=log)
+        Xv, Vv, _ = generate(a.val, a.gen, a.res, a.val_seed, log=None)
         report['generate_seconds'] = time.perf_counter() - t0
         report['generate'] = {
             'converged': int(sum(1 for s in gstats if s['status'] == 0)),
             'mean_gn': float(np.mean([s['gn_iters'] for s in gstats])),
             'mean_matvecs': float(np.mean([s['matvecs'] for s in gstats]))}
-        Xt, Vt = X[:a.pairs], V[:a.pairs]
+        Xt, Vt = X, V
         scale = float(torch.sqrt(torch.mean(Vt * Vt)))
         net = reg.UNet(a.res, ch)
         net.set_params(he_normal(net, seed=1))
@@ -306,23 +372,29 @@ def main(argv=None):
         report['unet_timing'] = time_unet(net)
         log('unet timing ' + json.dumps(report['unet_timing']))
         report['history'] = train(net, Xt, Vt, scale, a.epochs, a.lr,
-                                  val=(X[a.pairs:], V[a.pairs:]), budget_s=a.budget, log=log)
+                                  val=(Xv, Vv), budget_s=a.budget, log=log)
         report['train_seconds'] = time.perf_counter() - t0
         epochs = len(report['history'])
         report['train_steps'] = epochs * a.pairs
-        save_params(os.path.join(a.out, 'unet_r%d.npz' % a.res), net, scale,
-                    {'pairs': a.pairs, 'gen': a.gen, 'epochs': epochs,
-                     'train_seed': a.train_seed})
-        del X, V, Xt, Vt
+        meta = {'pairs': a.pairs, 'gen': a.gen, 'epochs': epochs, 'train_seed': a.train_seed}
+        save_params(os.path.join(a.out, 'unet_r%d.npz' % a.res), net, scale, meta)
+        del X, V, Xt, Vt, Xv, Vv
         torch.cuda.empty_cache()
     report['scale'] = scale
+    kc, alpha = (info['kc'], info['alpha']) if a.load else (None, 1.0)
+    if a.select > 0:
+        (kc, alpha), table = select_cutoff(net, scale, range(a.select_seed, a.select_seed + a.select),
+                                           a.eval_n, log=log)
+        report['select'] = {'kc': kc, 'alpha': alpha, 'J_ratio': table}
+        save_params(os.path.join(a.out, 'unet_r%d.npz' % net.R), net, scale, meta, kc, alpha)
     if a.eval > 0:
-        ev = evaluate(net, scale, range(a.eval_seed, a.eval_seed + a.eval), a.eval_n, log=log)
+        ev = evaluate(net, scale, range(a.eval_seed, a.eval_seed + a.eval), a.eval_n, kc, alpha,
+                      log=log)
         report['eval'] = ev
         report['eval_summary'] = summarise(ev)
         log('summary ' + json.dumps(report['eval_summary']))
     if a.eval_large > 0:
-        ev = evaluate(net, scale, [a.eval_large_seed], a.eval_large, log=log)
+        ev = evaluate(net, scale, [a.eval_large_seed], a.eval_large, kc, alpha, log=log)
         report['eval_large'] = ev
     with open(os.path.join(a.out, 'report.json'), 'w') as f:
         json.dump(report, f, indent=1)

@@ -43,19 +43,22 @@ def test_pipeline_runs_at_small_size(li):
     hist = li.train(net, X[:4], V[:4], scale, epochs=3, lr=1e-3, val=(X[4:], V[4:]), log=None)
     assert len(hist) == 3 and all(np.isfinite(h['train_loss']) for h in hist)
     ev = li.evaluate(net, scale, [200], 32, log=None)
-    for mode in ('zero', 'learned'):
-        assert ev[0][mode]['status'] == 0
-        assert ev[0][mode]['gnorm'] <= 1e-2 * ev[0]['zero']['gnorm0'] * (1 + 1e-9)
+    for name, _, _ in li.ARMS:
+        assert ev[0][name]['status'] == 0
+        assert ev[0][name]['gnorm'] <= 1e-2 * ev[0]['gnorm_ref'] * (1 + 1e-9)
+        assert ev[0][name]['gnorm_rel_fp32'] < 2e-2
 
 
 @pytest.mark.skipif(not os.path.exists(WEIGHTS), reason='no trained parameters in the package')
 def test_learned_guess_saves_matvecs_on_held_out_pairs(li):
-    net, scale = li.load(WEIGHTS)
-    ev = li.evaluate(net, scale, [7000, 7001, 7002], 256, log=None)
-    zero = sum(e['zero']['matvecs'] for e in ev)
+    net, info = li.load(WEIGHTS)
+    arms = (('plain', 'zero', 'fp32'), ('learned', 'learned', 'fp32'))
+    ev = li.evaluate(net, info['scale'], [7000, 7001, 7002], 256, info['kc'], info['alpha'],
+                     arms=arms, log=None)
+    zero = sum(e['plain']['matvecs'] for e in ev)
     learned = sum(e['learned']['matvecs'] for e in ev)
     for e in ev:
-        assert e['zero']['status'] == 0 and e['learned']['status'] == 0
+        assert e['plain']['status'] == 0 and e['learned']['status'] == 0
         # same stopping norm, so the same accuracy
-        assert e['learned']['mismatch_rel'] < 1.2 * e['zero']['mismatch_rel']
+        assert e['learned']['J_fp32'] < 1.02 * e['plain']['J_fp32']
     assert learned < zero, (learned, zero)

@@ -247,15 +247,37 @@ def test_three_gauss_newton_steps_match_the_oracle(reg):
 
 
 def test_graph_and_eager_pcg_agree(reg):
+    """Plain launches, one graph per PCG iteration, and the device-controlled
+    while-loop graph run the same kernels in the same order: same counts,
+    same iterate."""
     shape = (24, 24, 24)
     rho_T, rho_R, _ = synth.sinusoid_problem(shape, 0.5)
     out = []
-    for use_graph in (0, 1):
+    for use_graph in (0, 1, 2):
         R = reg.Registration(shape, 4, 1e-3)
         R.set_images(dev(rho_T), dev(rho_R))
         v = torch.zeros((3,) + shape, device='cuda')
         _, st = R.solve(v, gtol=1e-2, max_gn=4, use_graph=use_graph)
         out.append((host(v), st))
         R.close()
-    assert out[0][1]['pcg_iters'] == out[1][1]['pcg_iters']
-    assert rel(out[1][0], out[0][0]) < 1e-6
+    for o in out[1:]:
+        assert o[1]['pcg_iters'] == out[0][1]['pcg_iters']
+        assert o[1]['gn_iters'] == out[0][1]['gn_iters']
+        assert rel(o[0], out[0][0]) < 1e-6
+
+
+def test_device_pcg_loop_respects_the_iteration_cap(reg):
+    shape = (24, 24, 24)
+    rho_T, rho_R, _ = synth.sinusoid_problem(shape, 0.5)
+    res = []
+    for use_graph in (1, 2):
+        R = reg.Registration(shape, 4, 1e-3)
+        R.set_images(dev(rho_T), dev(rho_R))
+        v = torch.zeros((3,) + shape, device='cuda')
+        s, st = R.solve(v, gtol=1e-6, max_gn=3, max_pcg=2, use_graph=use_graph)
+        R.close()
+        res.append((s, st, host(v)))
+    for s, st, _ in res:
+        assert st['pcg_iters'] <= 2 * st['gn_iters']
+    assert res[0][1]['pcg_iters'] == res[1][1]['pcg_iters']
+    assert rel(res[1][2], res[0][2]) < 1e-6
