@@ -6,7 +6,7 @@ initial velocity (input images resampled to 64^3, prediction band-limited and
 resampled to 256^3), then the inexact Gauss-Newton-Krylov solve (every step
 of the path: semi-Lagrangian points, transports, spectral operators,
 gradient, Hessian matvecs, preconditioner, PCG, Armijo) in mixed precision
-(bf16 images and grad-rho copy, FP32 interpolation and FFTs, FP64
+(bf16 images, bf16 grad-rho copy for the matvec time integral, FP32 interpolation and FFTs, FP64
 reductions) to ||g|| <= 1e-2 ||g(v = 0)||.  --init zero --precision fp32 is
 the plain FP32 solver from v = 0; every other form is timed once after the
 main measurement ("arms").  Inputs are resident in HBM when the timed region
@@ -310,11 +310,14 @@ def gpu_bench(args):
                 ctxs[prec] = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=prec,
                                               stream=stream)
             solve_from_images(ctxs[prec], init)
+            # phase timing on, as in the main measurement: like for like
+            ctxs[prec].set_timing(True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             _, st = solve_from_images(ctxs[prec], init)
             e1.record(stream)
             torch.cuda.synchronize()
+            ctxs[prec].set_timing(False)
             arms[name] = {'time_to_solution_s': e0.elapsed_time(e1) / 1e3,
                           'gn_iters': st['gn_iters'], 'matvecs': st['matvecs'],
                           'gnorm_rel': st['gnorm_rel'], 'mismatch_rel': st['mismatch_rel']}
@@ -355,7 +358,7 @@ def gpu_bench(args):
         'config': {'workload': 'phantom 256^3 nt=8 H2 beta=1e-3, %s' % form,
                    'init': (('U-Net (64^3, 16/32/64/128, bf16) prediction, modes |k|<%s, '
                              'x%.2f' % (info['kc'], info['alpha'])) if learned else 'v = 0'),
-                   'storage': ('bf16 images, bf16 grad-rho cache in the matvec, fp32 fields'
+                   'storage': ('bf16 images, bf16 grad-rho copy in the matvec time integral, fp32 fields'
                                if args.precision == 'mixed_bf16' else 'fp32'),
                    'grid': list(SHAPE), 'nt': NT, 'beta': BETA, 'regularisation': KIND,
                    'gtol': '1e-2 of ||g(v=0)||', 'precision': args.precision,

@@ -63,11 +63,12 @@ enum { REG_H1 = 1, REG_H2 = 2, REG_H1DIV = 3 };
 
 /* Storage precision of the images and the cached state gradients.
  *  REG_FP32        everything FP32 (reductions FP64);
- *  REG_MIXED_BF16  rho_T and rho_R stored in bfloat16, and the Gauss-Newton
- *                  Hessian matvec reads a bfloat16 copy of the cached
- *                  grad rho(t_j); the gradient, the objective and the stopping
- *                  test keep the FP32 cache; interpolation and FFTs in FP32;
- *                  reductions in FP64. */
+ *  REG_MIXED_BF16  rho_T and rho_R stored in bfloat16, and the time
+ *                  integral of the Gauss-Newton Hessian matvec reads a
+ *                  bfloat16 copy of the cached grad rho(t_j); the transports,
+ *                  the gradient, the objective and the stopping test keep the
+ *                  FP32 cache; interpolation and FFTs in FP32; reductions in
+ *                  FP64. */
 enum { REG_FP32 = 0, REG_MIXED_BF16 = 1 };
 
 /* ---------------------------------------------------------------- context */

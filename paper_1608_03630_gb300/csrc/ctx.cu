@@ -237,13 +237,9 @@ Tile tile_with(const reg_ctx* c, int halo) {
 static const float* grad_level(reg_ctx* c, int j) {
     return c->grad_hist ? c->grad_hist + (long long)j * 3 * c->g.n : nullptr;
 }
-static const __nv_bfloat16* grad_level_bf(reg_ctx* c, int j) {
-    return c->grad_hist_bf ? c->grad_hist_bf + (long long)j * 3 * c->g.n : nullptr;
-}
-static double grad_bytes(reg_ctx* c) { return c->grad_hist_bf ? 6.0 : 12.0; }
 
-// The gradient always reads the FP32 cache; the Hessian matvec reads the
-// bfloat16 copy in mixed precision.
+// The gradient always reads the FP32 cache; the Hessian matvec's time
+// integral reads the bfloat16 copy in mixed precision.
 static bool matvec_bf(reg_ctx* c) { return c->grad_hist_bf != nullptr; }
 
 // Forward state solve (Eq. varopt:state).  keep_hist: all levels in hist
@@ -400,24 +396,27 @@ int op_gradient(reg_ctx* c, const float* v, float* gout, int slot_J) {
     return REG_OK;
 }
 
+// The incremental state steps read the FP32 grad-rho cache in both
+// precisions: they are bound by shared-memory bandwidth, so the bfloat16
+// copy's smaller loads save nothing there and its conversions cost issue
+// slots (measured 4 % slower at 256^3).  The time integral, bound by HBM,
+// reads the bfloat16 copy in mixed precision.
 int op_matvec_transport(reg_ctx* c, const float* vt) {
     const Dims& g = c->g;
     const long long n = g.n;
     const int nt = c->nt;
     const float dt = (float)(1.0 / nt);
-    const double gb = grad_bytes(c);
+    const double gb = 12.0;
     float* u[2] = {reinterpret_cast<float*>(c->buf[0]), reinterpret_cast<float*>(c->buf[1])};
     {
         Phase p(c, REG_PH_INCSTATE, (16.0 + gb) * n);
-        REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), grad_level_bf(c, 0), dt, u[0],
-                                       c->stream));
+        REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), nullptr, dt, u[0], c->stream));
     }
     for (int j = 0; j < nt; ++j) {
         const bool fin = (j == nt - 1);
         Phase p(c, REG_PH_INCSTATE, (32.0 + gb) * n);
         REG_CK(c, launch_incstate_step(g, tile_with(c, c->halo_fwd), u[j & 1], c->d_fwd, vt,
-                                       grad_level(c, j + 1),
-                                       grad_level_bf(c, j + 1), dt, fin ? 1 : 0,
+                                       grad_level(c, j + 1), nullptr, dt, fin ? 1 : 0,
                                        fin ? c->lam_hist + nt * n : u[(j + 1) & 1], c->stream));
     }
     return adjoint_solve(c, REG_PH_INCADJ);

@@ -1,10 +1,12 @@
-"""Mixed precision (bfloat16 images and bfloat16 grad rho cache in the matvec).
+"""Mixed precision (bfloat16 images; bfloat16 grad rho copy in the matvec's
+time integral).
 
 The gradient, objective and stopping test stay FP32 (FP64 reductions), so a
 mixed-precision solve must reach the same stopping test and the same final
-mismatch as the FP32 solve.  The Gauss-Newton matvec reads bfloat16 copies of
-grad rho(t_j) (8-bit mantissa, relative rounding 2^-9 ~ 2e-3 per value); its
-error against the FP64 oracle is reported and bounded by a few times that.
+mismatch as the FP32 solve.  The Gauss-Newton matvec's time integral reads
+bfloat16 copies of grad rho(t_j) (8-bit mantissa, relative rounding 2^-9 ~ 2e-3
+per value); its error against the FP64 oracle is reported and bounded by a
+few times that.
 """
 
 import numpy as np
