@@ -63,12 +63,11 @@ enum { REG_H1 = 1, REG_H2 = 2, REG_H1DIV = 3 };
 
 /* Storage precision of the images and the cached state gradients.
  *  REG_FP32        everything FP32 (reductions FP64);
- *  REG_MIXED_BF16  rho_T and rho_R stored in bfloat16, and the time
- *                  integral of the Gauss-Newton Hessian matvec reads a
- *                  bfloat16 copy of the cached grad rho(t_j); the transports,
- *                  the gradient, the objective and the stopping test keep the
- *                  FP32 cache; interpolation and FFTs in FP32; reductions in
- *                  FP64. */
+ *  REG_MIXED_BF16  rho_T and rho_R stored in bfloat16 (rounded once in
+ *                  reg_set_images, widened where a step reads them);
+ *                  every transported field, the grad rho cache,
+ *                  interpolation and FFTs in FP32; reductions, the
+ *                  objective and the stopping test in FP64. */
 enum { REG_FP32 = 0, REG_MIXED_BF16 = 1 };
 
 /* ---------------------------------------------------------------- context */

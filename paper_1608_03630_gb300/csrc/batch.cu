@@ -37,14 +37,15 @@ std::mutex g_tune_mutex;
 std::map<std::tuple<int, int, int, int, int>, std::pair<int, int>> g_tune_cache;
 
 // Median-free, simple timing: the mean of `reps` launches of the matvec
-// transports (nt incremental-state and nt incremental-adjoint steps).
+// transports (nt incremental-state and nt incremental-adjoint steps, the
+// latter with the time integral).
 int time_transports(reg_ctx* c, const float* vt, int reps, float* ms) {
     cudaEvent_t a, b;
     REG_CK(c, cudaEventCreate(&a));
     REG_CK(c, cudaEventCreate(&b));
-    REG_TRY(op_matvec_transport(c, vt));   // warm
+    REG_TRY(op_matvec_transport(c, vt, nullptr, 0));   // warm
     REG_CK(c, cudaEventRecord(a, c->stream));
-    for (int r = 0; r < reps; ++r) REG_TRY(op_matvec_transport(c, vt));
+    for (int r = 0; r < reps; ++r) REG_TRY(op_matvec_transport(c, vt, nullptr, 0));
     REG_CK(c, cudaEventRecord(b, c->stream));
     REG_CK(c, cudaEventSynchronize(b));
     REG_CK(c, cudaEventElapsedTime(ms, a, b));

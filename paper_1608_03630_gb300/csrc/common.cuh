@@ -166,30 +166,30 @@ cudaError_t launch_state_step(const Dims& g, Tile t, const float* rho_in, const 
                               double* partials, int max_partials, int* nblk_out,
                               cudaStream_t st);
 // Adjoint / incremental-adjoint tau-step lam_out = c(x) I[lam_in](x + d)
-// (c == nullptr: divergence-free velocity, c = 1).
-cudaError_t launch_adjoint_step(const Dims& g, Tile t, const float* lam_in, const float* d,
-                                const float* c, float* lam_out, cudaStream_t st);
+// (c == nullptr: divergence-free velocity, c = 1), fused with the trapezoid
+// time integral b = sum_j w_j lam_j grad rho_j: lam_out may be null (last
+// step), and at every point b += w lam_out grad.  lam_first != nullptr (first
+// step): b starts from w_first lam_first grad_first instead of its stored
+// value.  dotp != nullptr (last step): per-block FP64 partials of <dotp, b>
+// into partials[0 .. *nblk_out).
+cudaError_t launch_adjoint_acc(const Dims& g, Tile t, const float* lam_in, const float* d,
+                               const float* c, float* lam_out, const float* grad, float w,
+                               float* b, const float* lam_first, const float* grad_first,
+                               float w_first, const float* dotp, double* partials,
+                               int max_partials, int* nblk_out, cudaStream_t st);
 // c(x) = 1 + dt/2 (dX + dv + dt dX dv), dv = div v(x), dX = I[div v](x + d_adj).
 cudaError_t launch_adjoint_coef(const Dims& g, Tile t, const float* divv, const float* d_adj,
                                 float dt, float* c, cudaStream_t st);
 // Incremental state, carried as u_j = rho~_j + dt/2 f_j, f = -v~ . grad rho(t_j):
 //   u_{j+1} = I[u_j](x + d) + dt f_{j+1}(x);  final step writes
 //   lam~(1) = -(I[u_{nt-1}](x + d) + dt/2 f_nt(x)) instead.
-// grad_j1 is grad rho(t_{j+1}) (fp32, or bf16 when grad_bf != nullptr).
+// grad_j1 is grad rho(t_{j+1}).
 cudaError_t launch_incstate_step(const Dims& g, Tile t, const float* u_in, const float* d,
-                                 const float* vt, const float* grad_j1,
-                                 const __nv_bfloat16* grad_j1_bf, float dt, int final_step,
+                                 const float* vt, const float* grad_j1, float dt, int final_step,
                                  float* out, cudaStream_t st);
 // u_0 = -dt/2 v~ . grad rho(t_0)
-cudaError_t launch_incstate_init(const Dims& g, const float* vt, const float* grad0,
-                                 const __nv_bfloat16* grad0_bf, float dt, float* u0,
-                                 cudaStream_t st);
-// out[c] = base[c] + sum_j w_j lam_j grad_j[c]  (trapezoid weights, base may be
-// null); with dotp != nullptr also per-block partials of <dotp, out>.
-cudaError_t launch_time_integral(const Dims& g, int nt, const float* lam, const float* grad,
-                                 const __nv_bfloat16* grad_bf, const float* base, float* out,
-                                 const float* dotp, double* partials, int nblk,
-                                 cudaStream_t st);
+cudaError_t launch_incstate_init(const Dims& g, const float* vt, const float* grad0, float dt,
+                                 float* u0, cudaStream_t st);
 // Deformation displacement step: u_{j+1} = I[u_j](X) + dt/2 (I[-v](X) - v(x)).
 cudaError_t launch_deformation_step(const Dims& g, const float* u_in, const float* v,
                                     const float* d, float dt, float* u_out,

@@ -238,9 +238,6 @@ static const float* grad_level(reg_ctx* c, int j) {
     return c->grad_hist ? c->grad_hist + (long long)j * 3 * c->g.n : nullptr;
 }
 
-// The gradient always reads the FP32 cache; the Hessian matvec's time
-// integral reads the bfloat16 copy in mixed precision.
-static bool matvec_bf(reg_ctx* c) { return c->grad_hist_bf != nullptr; }
 
 // Forward state solve (Eq. varopt:state).  keep_hist: all levels in hist
 // [(nt+1) n]; otherwise hist holds two ping-pong levels.  The last step
@@ -308,34 +305,33 @@ int op_objective(reg_ctx* c, const float* v, int slot_J) {
 }
 
 // Adjoint (or incremental adjoint) from lam_hist[nt] down to lam_hist[0].
-static int adjoint_solve(reg_ctx* c, int phase) {
+// Adjoint (or incremental adjoint) solve from lam_hist[nt] = lam(1), fused
+// with the trapezoid time integral of Eq. gradient / Eq. inc-control: every
+// tau-step stores lam_j (except the last) and accumulates
+// b = sum_j w_j lam_j grad rho_j into out at its output points; with dotp,
+// dsc[slot] = <dotp, b>_h.
+static int adjoint_solve(reg_ctx* c, int phase, float* out, const float* dotp, int slot) {
     const long long n = c->g.n;
+    const int nt = c->nt;
     const bool comp = !c->incompressible;
-    for (int j = c->nt - 1; j >= 0; --j) {
-        Phase p(c, phase, (comp ? 24.0 : 20.0) * n);
-        REG_CK(c, launch_adjoint_step(c->g, tile_with(c, c->halo_adj), c->lam_hist + (j + 1) * n,
-                                      c->d_adj,
-                                      comp ? c->coef : nullptr, c->lam_hist + j * n, c->stream));
-    }
-    return REG_OK;
-}
-
-// out = base + sum_j w_j lam_j grad rho_j; dsc[slot] = <dotp, out>_h if dotp.
-// matvec: use the matvec's copy of the grad rho cache (bfloat16 in mixed
-// precision); the gradient passes false and reads FP32.
-int op_time_integral(reg_ctx* c, const float* base, float* out, const float* dotp, int slot,
-                     bool matvec) {
-    const long long n = c->g.n;
-    const int nb = blas_blocks();
-    {
-        const bool bf = matvec && matvec_bf(c);
-        double bytes = (c->nt + 1) * (4.0 + (bf ? 6.0 : 12.0)) * n + 12.0 * n;
-        if (base) bytes += 12.0 * n;
-        if (dotp) bytes += 12.0 * n;
-        Phase p(c, REG_PH_OTHER, bytes);
-        REG_CK(c, launch_time_integral(c->g, c->nt, c->lam_hist, c->grad_hist,
-                                       bf ? c->grad_hist_bf : nullptr, base, out, dotp,
-                                       c->partials, nb, c->stream));
+    const float dt = 1.f / (float)nt;
+    int nb = 0;
+    for (int j = nt - 1; j >= 0; --j) {
+        const bool first = (j == nt - 1), last = (j == 0);
+        const float w = last ? 0.5f * dt : dt;
+        // X 12, lam 4, c 4, lam_j 4 (not after the last step); grad_j 12; b
+        // written 12 and read 12 (first step: lam(1) 4 and grad rho(1) 12
+        // instead); dotp 12
+        double bytes = (comp ? 24.0 : 20.0) - (last ? 4.0 : 0.0) + 24.0 +
+                       (first ? 16.0 : 12.0) + (last && dotp ? 12.0 : 0.0);
+        Phase p(c, phase, bytes * n);
+        REG_CK(c, launch_adjoint_acc(c->g, tile_with(c, c->halo_adj), c->lam_hist + (j + 1) * n,
+                                     c->d_adj, comp ? c->coef : nullptr,
+                                     last ? nullptr : c->lam_hist + j * n, grad_level(c, j), w,
+                                     out, first ? c->lam_hist + nt * n : nullptr,
+                                     first ? grad_level(c, nt) : nullptr, 0.5f * dt,
+                                     last ? dotp : nullptr, c->partials, c->npartials, &nb,
+                                     c->stream));
     }
     if (dotp) {
         Phase p(c, REG_PH_BLAS, 0.0);
@@ -366,14 +362,8 @@ int op_linearize(reg_ctx* c, const float* v) {
     for (int j = 0; j <= nt; ++j) {
         float* gj = c->grad_hist + (long long)j * 3 * n;
         REG_TRY(op_grad(c, c->rho_hist + j * n, gj));
-        if (c->grad_hist_bf) {
-            Phase p(c, REG_PH_OTHER, 18.0 * n);
-            REG_CK(c, launch_to_bf16(gj, c->grad_hist_bf + (long long)j * 3 * n, 3 * n,
-                                     c->stream));
-        }
     }
-    REG_TRY(adjoint_solve(c, REG_PH_ADJOINT));
-    REG_TRY(op_time_integral(c, nullptr, c->bacc, nullptr, 0, false));
+    REG_TRY(adjoint_solve(c, REG_PH_ADJOINT, c->bacc, nullptr, 0));
     c->have_lin = true;
     return REG_OK;
 }
@@ -396,12 +386,7 @@ int op_gradient(reg_ctx* c, const float* v, float* gout, int slot_J) {
     return REG_OK;
 }
 
-// The incremental state steps read the FP32 grad-rho cache in both
-// precisions: they are bound by shared-memory bandwidth, so the bfloat16
-// copy's smaller loads save nothing there and its conversions cost issue
-// slots (measured 4 % slower at 256^3).  The time integral, bound by HBM,
-// reads the bfloat16 copy in mixed precision.
-int op_matvec_transport(reg_ctx* c, const float* vt) {
+int op_matvec_transport(reg_ctx* c, const float* vt, const float* dotp, int slot) {
     const Dims& g = c->g;
     const long long n = g.n;
     const int nt = c->nt;
@@ -410,21 +395,20 @@ int op_matvec_transport(reg_ctx* c, const float* vt) {
     float* u[2] = {reinterpret_cast<float*>(c->buf[0]), reinterpret_cast<float*>(c->buf[1])};
     {
         Phase p(c, REG_PH_INCSTATE, (16.0 + gb) * n);
-        REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), nullptr, dt, u[0], c->stream));
+        REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), dt, u[0], c->stream));
     }
     for (int j = 0; j < nt; ++j) {
         const bool fin = (j == nt - 1);
         Phase p(c, REG_PH_INCSTATE, (32.0 + gb) * n);
         REG_CK(c, launch_incstate_step(g, tile_with(c, c->halo_fwd), u[j & 1], c->d_fwd, vt,
-                                       grad_level(c, j + 1), nullptr, dt, fin ? 1 : 0,
+                                       grad_level(c, j + 1), dt, fin ? 1 : 0,
                                        fin ? c->lam_hist + nt * n : u[(j + 1) & 1], c->stream));
     }
-    return adjoint_solve(c, REG_PH_INCADJ);
+    return adjoint_solve(c, REG_PH_INCADJ, c->bacc, dotp, slot);
 }
 
 int op_matvec(reg_ctx* c, const float* vt, float* out) {
-    REG_TRY(op_matvec_transport(c, vt));
-    REG_TRY(op_time_integral(c, nullptr, c->bacc, nullptr, 0, true));
+    REG_TRY(op_matvec_transport(c, vt, nullptr, 0));
     REG_TRY(op_fft_r2c(c, vt, c->spec[0], 3));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
     SpecArgs a = spec_args(c);
@@ -485,7 +469,7 @@ static void free_ctx(reg_ctx* c) {
     for (int i = 0; i < 4; ++i)
         if (c->plans[i]) cufftDestroy(i == 0 ? c->r2c1 : i == 1 ? c->c2r1 : i == 2 ? c->r2c3 : c->c2r3);
     void* ptrs[] = {c->rho_T, c->rho_R, c->img_bf, c->d_fwd, c->d_adj, c->divv, c->rho_hist,
-                    c->grad_hist, c->grad_hist_bf, c->lam_hist, c->coef, c->buf[0], c->buf[1],
+                    c->grad_hist, c->lam_hist, c->coef, c->buf[0], c->buf[1],
                     c->bacc, c->tmp3, c->spec[0], c->spec[1], c->partials, c->dsc, c->dabs};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -504,10 +488,7 @@ static void free_ctx(reg_ctx* c) {
 static int alloc_grad_hist(reg_ctx* c) {
     const size_t cnt = (size_t)(c->nt + 1) * 3 * c->g.n;
     if (c->grad_hist) { cudaFree(c->grad_hist); c->grad_hist = nullptr; }
-    if (c->grad_hist_bf) { cudaFree(c->grad_hist_bf); c->grad_hist_bf = nullptr; }
-    cudaError_t e = cudaMalloc(&c->grad_hist, cnt * sizeof(float));
-    if (e == cudaSuccess && c->precision == REG_MIXED_BF16)
-        e = cudaMalloc(&c->grad_hist_bf, cnt * sizeof(__nv_bfloat16));
+    const cudaError_t e = cudaMalloc(&c->grad_hist, cnt * sizeof(float));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, REG_ENOMEM, "cannot allocate the grad rho cache");
@@ -653,7 +634,6 @@ int reg_set_precision(reg_ctx* c, int precision) {
     c->precision = precision;
     c->have_lin = false;
     c->have_images = false;
-    REG_TRY(alloc_grad_hist(c));
     if (precision == REG_MIXED_BF16 && !c->img_bf) {
         if (cudaMalloc(&c->img_bf, sizeof(__nv_bfloat16) * 2 * c->g.n) != cudaSuccess) {
             cudaGetLastError();

@@ -37,7 +37,6 @@ struct reg_ctx {
     float* divv;         // [n] (compressible)
     float* rho_hist;     // [(nt+1) n]
     float* grad_hist;    // [(nt+1) 3n] grad rho(t_j), FP32 (gradient and FP32 matvec)
-    __nv_bfloat16* grad_hist_bf;  // [(nt+1) 3n] bfloat16 copy read by the mixed matvec
 
     // scratch
     float* lam_hist;     // [(nt+1) n] adjoint / incremental-adjoint levels
@@ -114,10 +113,10 @@ int op_objective(reg_ctx* c, const float* v, int slot_J);
 // dsc[SC_JMIS] = 1/2 ||rho(1) - rho_R||^2_h for v (scratch buffers only).
 int op_mismatch(reg_ctx* c, const float* v);
 int op_matvec(reg_ctx* c, const float* vt, float* out);
-// The transports of one GN matvec: lam_hist receives lam~(t_0..t_nt).
-int op_matvec_transport(reg_ctx* c, const float* vt);
-int op_time_integral(reg_ctx* c, const float* base, float* out, const float* dotp, int slot,
-                     bool matvec);
+// The transports of one GN matvec with the time integral fused into the
+// incremental adjoint steps: bacc = b~ = sum_j w_j lam~_j grad rho_j; with
+// dotp, dsc[slot] = <dotp, b~>_h.
+int op_matvec_transport(reg_ctx* c, const float* vt, const float* dotp, int slot);
 int op_precond(reg_ctx* c, const float* r, float* z);
 int op_leray(reg_ctx* c, const float* v, float* out);
 int read_scalars(reg_ctx* c, int first, int count);   // dsc -> hsc, synchronises

@@ -63,8 +63,7 @@ static int pcg_iteration(reg_ctx* c) {
     float2** S = c->ss;
     float* p = c->sv[R_P];
     REG_TRY(op_fft_c2r(c, S[S_PC], p, 3));
-    REG_TRY(op_matvec_transport(c, p));
-    REG_TRY(op_time_integral(c, nullptr, c->bacc, p, SC_PB, true));
+    REG_TRY(op_matvec_transport(c, p, p, SC_PB));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
     REG_CK(c, launch_sp_update(c->g, S[S_S], S[S_R], S[S_P], c->spec[1], c->dsc, SC_RZ, SC_PAP,
                                SC_PB, SC_PQ, c->beta, c->kind, proj, c->partials, nb,

@@ -29,9 +29,6 @@ constexpr int kThreads = 256;
 inline int nblocks(long long n) { return (int)((n + kThreads - 1) / kThreads); }
 
 __device__ __forceinline__ float ld(const float* p, long long i) { return __ldg(p + i); }
-__device__ __forceinline__ float ld(const __nv_bfloat16* p, long long i) {
-    return __bfloat162float(p[i]);
-}
 
 // ------------------------------------------------------ plain gather kernels
 
@@ -225,13 +222,61 @@ struct EpiStateFinal {       // out = val; lam = rho_R - val; sum (val - rho_R)^
     }
 };
 
-struct EpiAdjoint {          // lam_out = c(x) val
+// Adjoint step fused with the time integral b = sum_j w_j lam_j grad rho_j
+// (trapezoid rule): lam_j = c(x) val is stored for the next step (out may be
+// null after the last one) and b at the output point gains w lam_j grad_j.
+// init (first step): b starts from w_first lam_first grad_first at the point
+// (the level the solve starts from) instead of its stored value.  dotp (last
+// step): per-block FP64 partial sums of <dotp, b>.
+struct EpiAdjAcc {
     float* out;
     const float* c;          // may be null (c = 1)
-    struct Pre { float c; };
-    __device__ Pre pre(int idx) const { return {c ? __ldg(c + idx) : 1.f}; }
-    __device__ void post(int idx, float val, const Pre& p, double&) const { out[idx] = p.c * val; }
-    __device__ void done(double) const {}
+    const float* grad;       // grad rho_j [3n]
+    float* b;                // [3n], read and written at the output point
+    long long n;
+    float w;
+    const float* lam_first;  // init only (else null)
+    const float* grad_first;
+    float w_first;
+    const float* dotp;       // last step only (else null)
+    double* partials;
+    struct Pre { float c, g0, g1, g2, b0, b1, b2; };
+    __device__ Pre pre(int idx) const {
+        Pre p;
+        p.c = c ? __ldg(c + idx) : 1.f;
+        p.g0 = ld(grad, idx);
+        p.g1 = ld(grad, n + idx);
+        p.g2 = ld(grad, 2 * n + idx);
+        if (lam_first) {
+            const float l = w_first * __ldg(lam_first + idx);
+            p.b0 = l * ld(grad_first, idx);
+            p.b1 = l * ld(grad_first, n + idx);
+            p.b2 = l * ld(grad_first, 2 * n + idx);
+        } else {
+            p.b0 = b[idx];
+            p.b1 = b[n + idx];
+            p.b2 = b[2 * n + idx];
+        }
+        return p;
+    }
+    __device__ void post(int idx, float val, const Pre& p, double& acc) const {
+        const float lam = p.c * val;
+        if (out) out[idx] = lam;
+        const float l = w * lam;
+        const float b0 = fmaf(l, p.g0, p.b0), b1 = fmaf(l, p.g1, p.b1), b2 = fmaf(l, p.g2, p.b2);
+        b[idx] = b0;
+        b[n + idx] = b1;
+        b[2 * n + idx] = b2;
+        if (dotp)
+            acc += (double)dotp[idx] * b0 + (double)dotp[n + idx] * b1 +
+                   (double)dotp[2 * n + idx] * b2;
+    }
+    __device__ void done(double acc) const {
+        if (!dotp) return;   // uniform over the grid
+        const double s = block_sum(acc);
+        if (threadIdx.x == 0 && threadIdx.y == 0)
+            partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+    }
 };
 
 struct EpiCoef {             // c = 1 + dt/2 (dX + dv + dt dX dv), val = dX
@@ -246,11 +291,10 @@ struct EpiCoef {             // c = 1 + dt/2 (dX + dv + dt dX dv), val = dX
     __device__ void done(double) const {}
 };
 
-template <typename GT>
 struct EpiIncState {         // u_{j+1} = val + dt f_{j+1}; final: lam~ = -(val + dt/2 f_nt)
     float* out;
     const float* vt;
-    const GT* gj1;
+    const float* gj1;
     long long n;
     float dt;
     int final_step;
@@ -623,9 +667,8 @@ __global__ void k_absmax(const float* __restrict__ d, long long count, unsigned 
 
 // ------------------------------------------------------- streaming kernels
 
-template <typename GT>
 __global__ void __launch_bounds__(kThreads)
-k_incstate_init(Dims g, const float* __restrict__ vt, const GT* __restrict__ g0, float dt,
+k_incstate_init(Dims g, const float* __restrict__ vt, const float* __restrict__ g0, float dt,
                 float* __restrict__ u0) {
     const int idx = blockIdx.x * kThreads + threadIdx.x;
     if (idx >= g.n) return;
@@ -635,39 +678,6 @@ k_incstate_init(Dims g, const float* __restrict__ vt, const GT* __restrict__ g0,
     u0[idx] = 0.5f * dt * f0;
 }
 
-// out[c] = base[c] + sum_j w_j lam_j grad_j[c] (trapezoid w), optional <dotp, out>.
-template <typename GT>
-__global__ void __launch_bounds__(kThreads)
-k_time_integral(Dims g, int nt, const float* __restrict__ lam, const GT* __restrict__ grad,
-                const float* __restrict__ base, float* __restrict__ out,
-                const float* __restrict__ dotp, double* __restrict__ partials) {
-    const long long n = g.n;
-    const float dt = 1.f / (float)nt;
-    double acc = 0.0;
-    for (long long idx = (long long)blockIdx.x * kThreads + threadIdx.x; idx < n;
-         idx += (long long)gridDim.x * kThreads) {
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f;
-        if (base) { s0 = base[idx]; s1 = base[n + idx]; s2 = base[2 * n + idx]; }
-        for (int j = 0; j <= nt; ++j) {
-            const float w = (j == 0 || j == nt) ? 0.5f * dt : dt;
-            const float l = w * __ldg(lam + (long long)j * n + idx);
-            const GT* gj = grad + (long long)j * 3 * n;
-            s0 = fmaf(l, ld(gj, idx), s0);
-            s1 = fmaf(l, ld(gj, n + idx), s1);
-            s2 = fmaf(l, ld(gj, 2 * n + idx), s2);
-        }
-        out[idx] = s0;
-        out[n + idx] = s1;
-        out[2 * n + idx] = s2;
-        if (dotp)
-            acc += (double)dotp[idx] * s0 + (double)dotp[n + idx] * s1 +
-                   (double)dotp[2 * n + idx] * s2;
-    }
-    if (dotp) {
-        const double s = block_sum(acc);
-        if (threadIdx.x == 0) partials[blockIdx.x] = s;
-    }
-}
 
 __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
                           long long count) {
@@ -738,9 +748,18 @@ cudaError_t launch_state_step(const Dims& g, Tile t, const float* rho_in, const 
 // Eq. (sml-advection) for the adjoint source f = lam div v with
 // f_0 = nu_0 (div v)(X): lam_new = nu_0 + dt/2 (nu_0 dX + (nu_0 + dt nu_0 dX) dv)
 // = c(x) nu_0 with c = 1 + dt/2 (dX + dv + dt dX dv), fixed for a given v.
-cudaError_t launch_adjoint_step(const Dims& g, Tile t, const float* lam_in, const float* d,
-                                const float* c, float* lam_out, cudaStream_t st) {
-    return run_march(g, t, lam_in, d, EpiAdjoint{lam_out, c}, st);
+cudaError_t launch_adjoint_acc(const Dims& g, Tile t, const float* lam_in, const float* d,
+                               const float* c, float* lam_out, const float* grad, float w,
+                               float* b, const float* lam_first, const float* grad_first,
+                               float w_first, const float* dotp, double* partials,
+                               int max_partials, int* nblk_out, cudaStream_t st) {
+    const int nb = march_blocks(g, t);
+    if (dotp && nb > max_partials) return cudaErrorInvalidValue;
+    if (nblk_out) *nblk_out = nb;
+    return run_march(g, t, lam_in, d,
+                     EpiAdjAcc{lam_out, c, grad, b, g.n, w, lam_first, grad_first, w_first, dotp,
+                               partials},
+                     st);
 }
 
 cudaError_t launch_adjoint_coef(const Dims& g, Tile t, const float* divv, const float* d_adj,
@@ -752,39 +771,17 @@ cudaError_t launch_adjoint_coef(const Dims& g, Tile t, const float* divv, const 
 // The interpolant is linear in the field, so with u_j = rho~_j + dt/2 f_j:
 // rho~_{j+1} = I[u_j](X) + dt/2 f_{j+1}(x) and u_{j+1} = I[u_j](X) + dt f_{j+1}(x).
 cudaError_t launch_incstate_step(const Dims& g, Tile t, const float* u_in, const float* d,
-                                 const float* vt, const float* grad_j1,
-                                 const __nv_bfloat16* grad_j1_bf, float dt, int final_step,
+                                 const float* vt, const float* grad_j1, float dt, int final_step,
                                  float* out, cudaStream_t st) {
-    if (grad_j1_bf)
-        return run_march(g, t, u_in, d,
-                         EpiIncState<__nv_bfloat16>{out, vt, grad_j1_bf, g.n, dt, final_step},
-                         st);
-    return run_march(g, t, u_in, d, EpiIncState<float>{out, vt, grad_j1, g.n, dt, final_step},
-                     st);
+    return run_march(g, t, u_in, d, EpiIncState{out, vt, grad_j1, g.n, dt, final_step}, st);
 }
 
-cudaError_t launch_incstate_init(const Dims& g, const float* vt, const float* grad0,
-                                 const __nv_bfloat16* grad0_bf, float dt, float* u0,
-                                 cudaStream_t st) {
-    if (grad0_bf)
-        k_incstate_init<<<nblocks(g.n), kThreads, 0, st>>>(g, vt, grad0_bf, dt, u0);
-    else
-        k_incstate_init<<<nblocks(g.n), kThreads, 0, st>>>(g, vt, grad0, dt, u0);
+cudaError_t launch_incstate_init(const Dims& g, const float* vt, const float* grad0, float dt,
+                                 float* u0, cudaStream_t st) {
+    k_incstate_init<<<nblocks(g.n), kThreads, 0, st>>>(g, vt, grad0, dt, u0);
     return cudaGetLastError();
 }
 
-cudaError_t launch_time_integral(const Dims& g, int nt, const float* lam, const float* grad,
-                                 const __nv_bfloat16* grad_bf, const float* base, float* out,
-                                 const float* dotp, double* partials, int nblk,
-                                 cudaStream_t st) {
-    if (grad_bf)
-        k_time_integral<<<nblk, kThreads, 0, st>>>(g, nt, lam, grad_bf, base, out, dotp,
-                                                   partials);
-    else
-        k_time_integral<<<nblk, kThreads, 0, st>>>(g, nt, lam, grad, base, out, dotp,
-                                                   partials);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_deformation_step(const Dims& g, const float* u_in, const float* v,
                                     const float* d, float dt, float* u_out,

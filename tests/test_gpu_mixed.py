@@ -1,12 +1,11 @@
-"""Mixed precision (bfloat16 images; bfloat16 grad rho copy in the matvec's
-time integral).
+"""Mixed precision: rho_T and rho_R stored in bfloat16, every other field,
+interpolation and FFTs in FP32, reductions FP64.
 
-The gradient, objective and stopping test stay FP32 (FP64 reductions), so a
-mixed-precision solve must reach the same stopping test and the same final
-mismatch as the FP32 solve.  The Gauss-Newton matvec's time integral reads
-bfloat16 copies of grad rho(t_j) (8-bit mantissa, relative rounding 2^-9 ~ 2e-3
-per value); its error against the FP64 oracle is reported and bounded by a
-few times that.
+The gradient, objective and stopping test see the bfloat16-rounded images,
+so a mixed-precision solve reaches the same stopping test as the FP32 solve
+and a final mismatch within the images' rounding (relative 2^-9 ~ 2e-3 per
+value).  With images that are already exactly representable in bfloat16, the
+gradient and the matvec match the FP64 oracle as closely as the FP32 path.
 """
 
 import numpy as np
