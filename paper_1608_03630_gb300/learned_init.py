@@ -57,10 +57,20 @@ def net_input(rho_T, rho_R, res):
     return x.contiguous()
 
 
-def generate(n_pairs, gen, res, seed0, nt=8, beta=1e-3, chunk=16, log=print):
+def band_limit(v, kc, res):
+    """v (3, m^3) keeping the Fourier modes |k_j| < kc, on the res^3 grid."""
+    if kc is not None and 2 * kc < v.shape[1]:
+        v = reg.spectral_resample(v, (2 * kc,) * 3)
+    if v.shape[1] != res:
+        v = reg.spectral_resample(v, (res,) * 3)
+    return v
+
+
+def generate(n_pairs, gen, res, seed0, nt=8, beta=1e-3, chunk=16, target_kc=None, log=print):
     """Solve n_pairs phantom pairs at gen^3; returns (X, V, stats): X the
     network inputs (n, 2, res^3), V the solutions resampled to res^3
-    (n, 3, res^3), stats one dict per pair."""
+    (n, 3, res^3; only the modes |k_j| < target_kc if given), stats one dict
+    per pair."""
     X = torch.empty((n_pairs, 2, res, res, res), device='cuda')
     V = torch.empty((n_pairs, 3, res, res, res), device='cuda')
     shape = (gen, gen, gen)
@@ -80,7 +90,7 @@ def generate(n_pairs, gen, res, seed0, nt=8, beta=1e-3, chunk=16, log=print):
         st, ss, _ = batch.solve(vs, rts, rrs, presmooth=True, autotune=False)
         for i in range(m):
             X[c0 + i] = net_input(rts[i], rrs[i], res)
-            V[c0 + i] = vs[i] if gen == res else reg.spectral_resample(vs[i], (res,) * 3)
+            V[c0 + i] = band_limit(vs[i], target_kc, res)
             ss[i]['status'] = st[i]
             ss[i]['seed'] = seed0 + c0 + i
             stats.append(ss[i])
@@ -196,11 +206,7 @@ def predict(net, scale, rho_T, rho_R, n, kc=None, alpha=1.0):
     cost beta |k|^4 in the objective), resampled to n^3."""
     y = net.forward(net_input(rho_T, rho_R, net.R))
     y.mul_(alpha * scale)
-    if kc is not None and 2 * kc < net.R:
-        y = reg.spectral_resample(y, (2 * kc,) * 3)
-    if y.shape[1] != n:
-        y = reg.spectral_resample(y, (n, n, n))
-    return y.contiguous()
+    return band_limit(y, kc, n).contiguous()
 
 
 def select_cutoff(net, scale, seeds, n, cutoffs=(4, 6, 8, 12, 16, 32), alphas=(0.6, 0.8, 1.0),
@@ -329,6 +335,8 @@ def main(argv=None):
     ap.add_argument('--gen', type=int, default=128, help='grid of the training solves')
     ap.add_argument('--res', type=int, default=64, help='network grid')
     ap.add_argument('--channels', default='16,32,64,128')
+    ap.add_argument('--target-kc', type=int, default=None,
+                    help='train on targets keeping only the modes |k_j| < this')
     ap.add_argument('--epochs', type=int, default=8, help='at most this many epochs')
     ap.add_argument('--budget', type=float, default=None,
                     help='training seconds (fewer epochs if they do not fit)')
@@ -362,8 +370,9 @@ def main(argv=None):
     else:
         ch = tuple(int(c) for c in a.channels.split(','))
         t0 = time.perf_counter()
-        X, V, gstats = generate(a.pairs, a.gen, a.res, a.train_seed, log=log)
-        Xv, Vv, _ = generate(a.val, a.gen, a.res, a.val_seed, log=None)
+        X, V, gstats = generate(a.pairs, a.gen, a.res, a.train_seed, target_kc=a.target_kc,
+                                log=log)
+        Xv, Vv, _ = generate(a.val, a.gen, a.res, a.val_seed, target_kc=a.target_kc, log=None)
         report['generate_seconds'] = time.perf_counter() - t0
         report['generate'] = {
             'converged': int(sum(1 for s in gstats if s['status'] == 0)),
@@ -381,7 +390,8 @@ def main(argv=None):
         report['train_seconds'] = time.perf_counter() - t0
         epochs = len(report['history'])
         report['train_steps'] = epochs * a.pairs
-        meta = {'pairs': a.pairs, 'gen': a.gen, 'epochs': epochs, 'train_seed': a.train_seed}
+        meta = {'pairs': a.pairs, 'gen': a.gen, 'epochs': epochs, 'train_seed': a.train_seed,
+                'target_kc': a.target_kc}
         save_params(os.path.join(a.out, 'unet_r%d.npz' % a.res), net, scale, meta)
         del X, V, Xt, Vt, Xv, Vv
         torch.cuda.empty_cache()
