@@ -102,15 +102,6 @@ void release_graph_timing(reg_ctx* c) {
     c->graph_pairs.clear();
 }
 
-// RAII helper around one launch.
-struct Phase {
-    reg_ctx* c; int ph; double bytes; cudaEvent_t ev;
-    Phase(reg_ctx* c_, int ph_, double bytes_) : c(c_), ph(ph_), bytes(bytes_) {
-        phase_begin(c, &ev);
-    }
-    ~Phase() { phase_end(c, ph, ev, bytes); }
-};
-
 // ------------------------------------------------------------- operations
 
 int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj) {

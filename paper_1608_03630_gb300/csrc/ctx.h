@@ -92,6 +92,14 @@ int fail_cuda(reg_ctx* c, cudaError_t e, const char* what, int line);
 // Phase timing: begin() before a launch, end() after it (no-ops when off).
 void phase_begin(reg_ctx* c, cudaEvent_t* ev);
 void phase_end(reg_ctx* c, int phase, cudaEvent_t ev, double bytes);
+// RAII helper around one launch.
+struct Phase {
+    reg_ctx* c; int ph; double bytes; cudaEvent_t ev;
+    Phase(reg_ctx* c_, int ph_, double bytes_) : c(c_), ph(ph_), bytes(bytes_) {
+        phase_begin(c, &ev);
+    }
+    ~Phase() { phase_end(c, ph, ev, bytes); }
+};
 // After a replay of a captured graph has completed: add its event pairs.
 int harvest_graph_timing(reg_ctx* c);
 // When the graph is destroyed: return its events to the pool.

@@ -40,6 +40,7 @@ enum { S_V = 0, S_VT = 1, S_G = 2, S_S = 3, S_R = 4, S_P = 5, S_PC = 6 };
 static int finalize_to(reg_ctx* c, int t, int nb, double scale, int slot) {
     if ((long long)(t + 1) * nb > c->npartials)
         return fail(c, REG_EINVAL, "partial-sum slot out of range");
+    Phase ph(c, REG_PH_BLAS, 0.0);
     REG_CK(c, launch_finalize(c->partials + (long long)t * nb, nb, scale, c->dsc + slot,
                               c->stream));
     return REG_OK;
@@ -65,13 +66,19 @@ static int pcg_iteration(reg_ctx* c) {
     REG_TRY(op_fft_c2r(c, S[S_PC], p, 3));
     REG_TRY(op_matvec_transport(c, p, p, SC_PB));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
-    REG_CK(c, launch_sp_update(c->g, S[S_S], S[S_R], S[S_P], c->spec[1], c->dsc, SC_RZ, SC_PAP,
-                               SC_PB, SC_PQ, c->beta, c->kind, proj, c->partials, nb,
-                               c->stream));
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 6.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_update(c->g, S[S_S], S[S_R], S[S_P], c->spec[1], c->dsc, SC_RZ, SC_PAP,
+                                   SC_PB, SC_PQ, c->beta, c->kind, proj, c->partials, nb,
+                                   c->stream));
+    }
     REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
     REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZNEW));
-    REG_CK(c, launch_sp_direction(c->g, S[S_R], S[S_P], S[S_PC], c->dsc, SC_RZNEW, SC_RZ, 0,
-                                  c->beta, c->kind, proj, c->partials, nb, c->stream));
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 4.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_direction(c->g, S[S_R], S[S_P], S[S_PC], c->dsc, SC_RZNEW, SC_RZ, 0,
+                                      c->beta, c->kind, proj, c->partials, nb, c->stream));
+    }
     REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_PAP));
     REG_CK(c, cudaMemcpyAsync(c->dsc + SC_RZ, c->dsc + SC_RZNEW, sizeof(double),
                               cudaMemcpyDeviceToDevice, c->stream));
@@ -167,8 +174,11 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
     res->neg_curv = false;
     res->converged = false;
     // r = -g, s = 0, p = M P r
-    REG_CK(c, launch_sp_init(c->g, S[S_G], S[S_R], S[S_S], S[S_P], S[S_PC], c->beta, c->kind,
-                             proj, c->partials, nb, c->stream));
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 5.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_init(c->g, S[S_G], S[S_R], S[S_S], S[S_P], S[S_PC], c->beta, c->kind,
+                                 proj, c->partials, nb, c->stream));
+    }
     REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
     REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZ));
     REG_TRY(finalize_to(c, 2, nb, kTwoPi3, SC_PAP));
@@ -289,8 +299,11 @@ static int evaluate_gradient(reg_ctx* c, double* J, double* gnorm) {
     REG_TRY(to_physical(c, S[S_V], v));
     REG_TRY(op_linearize(c, v));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
-    REG_CK(c, launch_sp_gradient(c->g, S[S_V], c->spec[1], S[S_G], c->beta, c->kind,
-                                 c->incompressible, c->partials, nb, c->stream));
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_gradient(c->g, S[S_V], c->spec[1], S[S_G], c->beta, c->kind,
+                                     c->incompressible, c->partials, nb, c->stream));
+    }
     REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_GG));
     REG_TRY(finalize_to(c, 1, nb, 0.5 * c->beta * kTwoPi3, SC_JREG));
     REG_TRY(read_scalars(c, SC_JMIS, 9));
@@ -305,8 +318,11 @@ static int evaluate_gradient(reg_ctx* c, double* J, double* gnorm) {
 static int evaluate_trial(reg_ctx* c, double alpha, double* J) {
     const int nb = blas_blocks();
     float2** S = c->ss;
-    REG_CK(c, launch_sp_axpy(c->g, S[S_VT], c->spec[0], S[S_V], S[S_S], (float)alpha, c->kind, 0,
-                             c->partials, nb, c->stream));
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_axpy(c->g, S[S_VT], c->spec[0], S[S_V], S[S_S], (float)alpha, c->kind, 0,
+                                 c->partials, nb, c->stream));
+    }
     REG_TRY(finalize_to(c, 0, nb, 0.5 * c->beta * kTwoPi3, SC_JREG));
     float* v = c->sv[R_V];
     REG_TRY(op_fft_c2r(c, c->spec[0], v, 3));
@@ -323,7 +339,10 @@ static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solv
     float2** S = c->ss;
     // v_hat = F v / n (projected when incompressible)
     REG_TRY(op_fft_r2c(c, v_io, c->spec[0], 3));
-    REG_CK(c, launch_sp_normalise(c->g, c->spec[0], S[S_V], c->incompressible, c->stream));
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_normalise(c->g, c->spec[0], S[S_V], c->incompressible, c->stream));
+    }
     // ||rho_T - rho_R|| for the relative mismatch
     REG_CK(c, launch_axpby_out(c->tmp3, c->rho_T, c->rho_R, 1.f, -1.f, n, c->stream));
     REG_TRY(op_inner(c, c->tmp3, c->tmp3, n, SC_TMP));
@@ -350,7 +369,10 @@ static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solv
         st->pcg_iters += pr.iters;
         st->matvecs += pr.iters;
         st->negative_curvature += pr.neg_curv ? 1 : 0;
-        REG_CK(c, launch_sp_dot(c->g, S[S_G], S[S_S], c->partials, nb, c->stream));
+        {
+            Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
+            REG_CK(c, launch_sp_dot(c->g, S[S_G], S[S_S], c->partials, nb, c->stream));
+        }
         REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_GS));
         REG_TRY(read_scalars(c, SC_GS, 1));
         const double slope = c->hsc[SC_GS];
