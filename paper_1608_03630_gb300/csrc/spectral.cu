@@ -137,13 +137,14 @@ k_spec_energy(Dims g, const float2* __restrict__ v, int kind, double* partials) 
          idx += gridDim.x * kThreads) {
         const Wave w = wave(g, idx);
         const float A = reg_symbol(w, kind) * w.herm;
-        double s = 0.0;
+        float s = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const float2 x = v[c * nc + idx];
-            s += (double)x.x * x.x + (double)x.y * x.y;
+            s = fmaf(x.x, x.x, s);
+            s = fmaf(x.y, x.y, s);
         }
-        acc += (double)A * s;
+        acc += (double)(A * s);
     }
     __shared__ double red[kThreads / 32];
 #pragma unroll
@@ -169,9 +170,19 @@ __device__ __forceinline__ float mprec(float A, float beta) {
     return A > 0.f ? 1.f / (beta * A) : 1.f / beta;
 }
 
-__device__ __forceinline__ double herm_sq(const Wave& w, float2 a, float2 b, float2 c) {
-    return (double)w.herm * ((double)a.x * a.x + (double)a.y * a.y + (double)b.x * b.x +
-                             (double)b.y * b.y + (double)c.x * c.x + (double)c.y * c.y);
+// herm |(a, b, c)|^2 of one coefficient: the products in FP32 (one rounding
+// of an FP32 value's square, relative 6e-8), the sums over the spectrum in
+// FP64 by the callers.  GB300 runs FP64 arithmetic at a small fraction of
+// FP32, and a per-coefficient FP64 product chain was a measurable part of
+// these bandwidth-bound kernels.
+__device__ __forceinline__ float herm_sq(const Wave& w, float2 a, float2 b, float2 c) {
+    float s = a.x * a.x;
+    s = fmaf(a.y, a.y, s);
+    s = fmaf(b.x, b.x, s);
+    s = fmaf(b.y, b.y, s);
+    s = fmaf(c.x, c.x, s);
+    s = fmaf(c.y, c.y, s);
+    return w.herm * s;
 }
 
 template <int NS>
@@ -213,10 +224,10 @@ k_sp_init(Dims g, const float2* __restrict__ gh, float2* __restrict__ r, float2*
         if (project) leray3(w, a, b, c);
         const float A = reg_symbol(w, kind);
         const float m = mprec(A, beta);
-        const double e = herm_sq(w, a, b, c);
+        const float e = herm_sq(w, a, b, c);
         acc[0] += e;
-        acc[1] += (double)m * e;
-        acc[2] += (double)beta * A * (double)m * m * e;
+        acc[1] += (double)(m * e);
+        acc[2] += (double)(beta * A * m * m * e);
         a = scale2(a, m); b = scale2(b, m); c = scale2(c, m);
         p[idx] = a; p[nc + idx] = b; p[2 * nc + idx] = c;
         pc[idx] = a; pc[nc + idx] = b; pc[2 * nc + idx] = c;
@@ -259,9 +270,9 @@ k_sp_update(Dims g, float2* __restrict__ s, float2* __restrict__ r, const float2
             r[k * nc + idx] = rr[k];
         }
         if (project) leray3(w, rr[0], rr[1], rr[2]);
-        const double e = herm_sq(w, rr[0], rr[1], rr[2]);
+        const float e = herm_sq(w, rr[0], rr[1], rr[2]);
         acc[0] += e;
-        acc[1] += (double)mprec(A, beta) * e;
+        acc[1] += (double)(mprec(A, beta) * e);
     }
     store_partials<2>(acc, partials);
 }
@@ -292,7 +303,7 @@ k_sp_direction(Dims g, const float2* __restrict__ r, float2* __restrict__ p,
             if (pc) pc[k * nc + idx] = pv;
             z[k] = pv;
         }
-        acc[0] += (double)beta * A * herm_sq(w, z[0], z[1], z[2]);
+        acc[0] += (double)(beta * A * herm_sq(w, z[0], z[1], z[2]));
     }
     store_partials<1>(acc, partials);
 }
@@ -317,7 +328,7 @@ k_sp_gradient(Dims g, const float2* __restrict__ v, const float2* __restrict__ B
         const float2 g2 = make_float2(fmaf(bA, v2.x, b2.x), fmaf(bA, v2.y, b2.y));
         gout[idx] = g0; gout[nc + idx] = g1; gout[2 * nc + idx] = g2;
         acc[0] += herm_sq(w, g0, g1, g2);
-        acc[1] += (double)A * herm_sq(w, v0, v1, v2);
+        acc[1] += (double)(A * herm_sq(w, v0, v1, v2));
     }
     store_partials<2>(acc, partials);
 }
@@ -347,7 +358,7 @@ k_sp_axpy(Dims g, float2* __restrict__ out, float2* __restrict__ copy, const flo
             out[k * nc + idx] = o[k];
             if (copy) copy[k * nc + idx] = o[k];
         }
-        acc[0] += (double)reg_symbol(w, kind) * herm_sq(w, o[0], o[1], o[2]);
+        acc[0] += (double)(reg_symbol(w, kind) * herm_sq(w, o[0], o[1], o[2]));
     }
     store_partials<1>(acc, partials);
 }
@@ -359,13 +370,14 @@ k_sp_dot(Dims g, const float2* __restrict__ a, const float2* __restrict__ b, dou
     double acc[1] = {0.0};
     SPEC_LOOP {
         const Wave w = wave(g, idx);
-        double s = 0.0;
+        float s = 0.f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float2 x = a[k * nc + idx], y = b[k * nc + idx];
-            s += (double)x.x * y.x + (double)x.y * y.y;
+            s = fmaf(x.x, y.x, s);
+            s = fmaf(x.y, y.y, s);
         }
-        acc[0] += (double)w.herm * s;
+        acc[0] += (double)(w.herm * s);
     }
     store_partials<1>(acc, partials);
 }

@@ -213,7 +213,7 @@ struct EpiStateFinal {       // out = val; lam = rho_R - val; sum (val - rho_R)^
         out[idx] = val;
         const float l = p.r - val;
         if (lam) lam[idx] = l;
-        acc += (double)l * (double)l;
+        acc += (double)(l * l);
     }
     __device__ void done(double acc) const {
         const double s = block_sum(acc);
@@ -268,8 +268,7 @@ struct EpiAdjAcc {
         b[n + idx] = b1;
         b[2 * n + idx] = b2;
         if (dotp)
-            acc += (double)dotp[idx] * b0 + (double)dotp[n + idx] * b1 +
-                   (double)dotp[2 * n + idx] * b2;
+            acc += (double)fmaf(dotp[idx], b0, fmaf(dotp[n + idx], b1, dotp[2 * n + idx] * b2));
     }
     __device__ void done(double acc) const {
         if (!dotp) return;   // uniform over the grid
