@@ -152,6 +152,9 @@ typedef struct {
                              forcing term, e.g. the gradient norm at v = 0
                              when v_inout holds a prediction; 0: ||g|| at the
                              initial guess                               (0) */
+    double precond_shift; /* >= 0: PCG preconditioner M = 1/(beta A + shift);
+                             0 is the paper's inverse regularisation
+                             operator (Sec. III-A)                       (0) */
 } reg_solve_opts;
 
 typedef struct {

@@ -228,18 +228,19 @@ cudaError_t launch_spectral(const Dims& g, SpecOp op, const SpecArgs& a, cudaStr
 cudaError_t launch_spec_energy(const Dims& g, const float2* v, int kind, double* partials,
                                int nblk, cudaStream_t st);
 // Spectral Krylov kernels (normalised half-spectrum coefficients, 3 fields).
-// Partials: slot t of block b at partials[t * nblk + b].
+// Partials: slot t of block b at partials[t * nblk + b].  The preconditioner
+// is M = 1 / (beta A + shift) (shift 0: the inverse regularisation operator).
 cudaError_t launch_sp_init(const Dims& g, const float2* gh, float2* r, float2* s, float2* p,
-                           float2* pc, double beta, int kind, int project, double* partials,
-                           int nblk, cudaStream_t st);
+                           float2* pc, double beta, double shift, int kind, int project,
+                           double* partials, int nblk, cudaStream_t st);
 cudaError_t launch_sp_update(const Dims& g, float2* s, float2* r, const float2* p,
                              const float2* B, double* sc, int irz, int ipap, int ipb, int ipq,
-                             double beta, int kind, int project, double* partials, int nblk,
-                             cudaStream_t st);
+                             double beta, double shift, int kind, int project,
+                             double* partials, int nblk, cudaStream_t st);
 cudaError_t launch_sp_direction(const Dims& g, const float2* r, float2* p, float2* pc,
                                 const double* sc, int irznew, int irz, int zero_beta,
-                                double beta, int kind, int project, double* partials, int nblk,
-                                cudaStream_t st);
+                                double beta, double shift, int kind, int project,
+                                double* partials, int nblk, cudaStream_t st);
 cudaError_t launch_sp_gradient(const Dims& g, const float2* v, const float2* B, float2* gout,
                                double beta, int kind, int project, double* partials, int nblk,
                                cudaStream_t st);

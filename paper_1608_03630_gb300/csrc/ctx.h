@@ -49,6 +49,7 @@ struct reg_ctx {
     int npartials;
     double* dsc;         // device scalars [32]
     double* hsc;         // pinned host mirror [32]
+    double pshift;       // shift of the solver's spectral preconditioner (reg_solve)
     reg::Tile tile;      // tile of the interpolation kernels (k, wy)
     int halo_fwd, halo_adj;   // ceil(max |X - x|) of d_fwd / d_adj (-1: unknown)
     unsigned int* dabs;  // [2] device scratch for max |d| (float bits)

@@ -69,15 +69,16 @@ static int pcg_iteration(reg_ctx* c) {
     {
         Phase ph(c, REG_PH_SPECTRAL, 6.0 * 24.0 * (double)c->g.nc);
         REG_CK(c, launch_sp_update(c->g, S[S_S], S[S_R], S[S_P], c->spec[1], c->dsc, SC_RZ, SC_PAP,
-                                   SC_PB, SC_PQ, c->beta, c->kind, proj, c->partials, nb,
-                                   c->stream));
+                                   SC_PB, SC_PQ, c->beta, c->pshift, c->kind, proj, c->partials,
+                                   nb, c->stream));
     }
     REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
     REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZNEW));
     {
         Phase ph(c, REG_PH_SPECTRAL, 4.0 * 24.0 * (double)c->g.nc);
         REG_CK(c, launch_sp_direction(c->g, S[S_R], S[S_P], S[S_PC], c->dsc, SC_RZNEW, SC_RZ, 0,
-                                      c->beta, c->kind, proj, c->partials, nb, c->stream));
+                                      c->beta, c->pshift, c->kind, proj, c->partials, nb,
+                                      c->stream));
     }
     REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_PAP));
     REG_CK(c, cudaMemcpyAsync(c->dsc + SC_RZ, c->dsc + SC_RZNEW, sizeof(double),
@@ -176,8 +177,8 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
     // r = -g, s = 0, p = M P r
     {
         Phase ph(c, REG_PH_SPECTRAL, 5.0 * 24.0 * (double)c->g.nc);
-        REG_CK(c, launch_sp_init(c->g, S[S_G], S[S_R], S[S_S], S[S_P], S[S_PC], c->beta, c->kind,
-                                 proj, c->partials, nb, c->stream));
+        REG_CK(c, launch_sp_init(c->g, S[S_G], S[S_R], S[S_S], S[S_P], S[S_PC], c->beta,
+                                 c->pshift, c->kind, proj, c->partials, nb, c->stream));
     }
     REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
     REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZ));
@@ -208,7 +209,8 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
                 if (res->iters == 1) {
                     // first direction: the preconditioned steepest-descent step
                     e = launch_sp_direction(c->g, S[S_R], S[S_S], nullptr, c->dsc, SC_ZERO, SC_RZ,
-                                            1, c->beta, c->kind, proj, c->partials, nb, c->stream);
+                                            1, c->beta, c->pshift, c->kind, proj, c->partials, nb,
+                                            c->stream);
                     if (e != cudaSuccess) return fail_cuda(c, e, "launch_sp_direction", __LINE__);
                 }
             }
@@ -277,8 +279,9 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
                 // first direction: the preconditioned steepest-descent step
                 // s = M P r (r is still -g: the update was skipped)
                 const cudaError_t e = launch_sp_direction(c->g, S[S_R], S[S_S], nullptr, c->dsc,
-                                                          SC_ZERO, SC_RZ, 1, c->beta, c->kind,
-                                                          proj, c->partials, nb, c->stream);
+                                                          SC_ZERO, SC_RZ, 1, c->beta, c->pshift,
+                                                          c->kind, proj, c->partials, nb,
+                                                          c->stream);
                 if (e != cudaSuccess) status = fail_cuda(c, e, "launch_sp_direction", __LINE__);
             }
             break;
@@ -432,6 +435,7 @@ int reg_solve_opts_default(reg_solve_opts* o) {
     o->use_graph = 2;
     o->verbose = 0;
     o->gnorm_ref = 0.0;
+    o->precond_shift = 0.0;
     return REG_OK;
 }
 
@@ -443,10 +447,11 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
     reg_solve_opts o;
     reg_solve_opts_default(&o);
     if (opts) o = *opts;
-    if (!(o.gtol >= 0.0) || !(o.gnorm_ref >= 0.0) || o.max_gn < 0 || o.max_pcg < 1 || o.armijo_max < 1 ||
+    if (!(o.gtol >= 0.0) || !(o.gnorm_ref >= 0.0) || !(o.precond_shift >= 0.0) || o.max_gn < 0 || o.max_pcg < 1 || o.armijo_max < 1 ||
         !(o.armijo_shrink > 0.0 && o.armijo_shrink < 1.0))
         return fail(c, REG_EINVAL, "bad solver options");
     REG_TRY(ensure_solver(c));
+    c->pshift = o.precond_shift;
     reg_solve_stats local;
     memset(&local, 0, sizeof local);
     const int s = solve_impl(c, v_inout, &o, &local);

@@ -166,8 +166,10 @@ k_spec_energy(Dims g, const float2* __restrict__ v, int kind, double* partials) 
 // <a, b>_h = (2 pi)^3 sum_k herm(k) Re(conj(a_k) b_k) (Parseval).  Each kernel
 // writes per-block FP64 partials, slot t at partials[t * gridDim.x + block].
 
-__device__ __forceinline__ float mprec(float A, float beta) {
-    return A > 0.f ? 1.f / (beta * A) : 1.f / beta;
+// Spectral preconditioner 1 / (beta A + shift) (shift 0: the inverse
+// regularisation operator, with 1 / beta at k = 0).
+__device__ __forceinline__ float mprec(float A, float beta, float shift) {
+    return A > 0.f ? 1.f / fmaf(beta, A, shift) : 1.f / (beta + shift);
 }
 
 // herm |(a, b, c)|^2 of one coefficient: the products in FP32 (one rounding
@@ -210,7 +212,8 @@ __device__ __forceinline__ void store_partials(double (&acc)[NS], double* partia
 // r = -g, s = 0, z = M P r, p = pc = z; partials: |P r|^2, M |P r|^2, beta A |p|^2.
 __global__ void __launch_bounds__(kThreads)
 k_sp_init(Dims g, const float2* __restrict__ gh, float2* __restrict__ r, float2* __restrict__ s,
-          float2* __restrict__ p, float2* __restrict__ pc, float beta, int kind, int project,
+          float2* __restrict__ p, float2* __restrict__ pc, float beta, float shift, int kind,
+          int project,
           double* partials) {
     const long long nc = g.nc;
     double acc[3] = {0.0, 0.0, 0.0};
@@ -223,7 +226,7 @@ k_sp_init(Dims g, const float2* __restrict__ gh, float2* __restrict__ r, float2*
         s[idx] = zero; s[nc + idx] = zero; s[2 * nc + idx] = zero;
         if (project) leray3(w, a, b, c);
         const float A = reg_symbol(w, kind);
-        const float m = mprec(A, beta);
+        const float m = mprec(A, beta, shift);
         const float e = herm_sq(w, a, b, c);
         acc[0] += e;
         acc[1] += (double)(m * e);
@@ -241,7 +244,7 @@ k_sp_init(Dims g, const float2* __restrict__ gh, float2* __restrict__ r, float2*
 __global__ void __launch_bounds__(kThreads)
 k_sp_update(Dims g, float2* __restrict__ s, float2* __restrict__ r, const float2* __restrict__ p,
             const float2* __restrict__ B, double* sc, int irz, int ipap, int ipb, int ipq,
-            float beta, int kind, int project, float inv_n, double* partials) {
+            float beta, float shift, int kind, int project, float inv_n, double* partials) {
     const long long nc = g.nc;
     const double pq = sc[ipap] + sc[ipb];
     const float alpha = pq > 0.0 ? (float)(sc[irz] / pq) : 0.f;
@@ -272,7 +275,7 @@ k_sp_update(Dims g, float2* __restrict__ s, float2* __restrict__ r, const float2
         if (project) leray3(w, rr[0], rr[1], rr[2]);
         const float e = herm_sq(w, rr[0], rr[1], rr[2]);
         acc[0] += e;
-        acc[1] += (double)(mprec(A, beta) * e);
+        acc[1] += (double)(mprec(A, beta, shift) * e);
     }
     store_partials<2>(acc, partials);
 }
@@ -282,7 +285,7 @@ k_sp_update(Dims g, float2* __restrict__ s, float2* __restrict__ r, const float2
 __global__ void __launch_bounds__(kThreads)
 k_sp_direction(Dims g, const float2* __restrict__ r, float2* __restrict__ p,
                float2* __restrict__ pc, const double* __restrict__ sc, int irznew, int irz,
-               int zero_beta, float beta, int kind, int project, double* partials) {
+               int zero_beta, float beta, float shift, int kind, int project, double* partials) {
     const long long nc = g.nc;
     const double den = sc[irz];
     const float bk = (zero_beta || den == 0.0) ? 0.f : (float)(sc[irznew] / den);
@@ -292,7 +295,7 @@ k_sp_direction(Dims g, const float2* __restrict__ r, float2* __restrict__ p,
         float2 a = r[idx], b = r[nc + idx], c = r[2 * nc + idx];
         if (project) leray3(w, a, b, c);
         const float A = reg_symbol(w, kind);
-        const float m = mprec(A, beta);
+        const float m = mprec(A, beta, shift);
         float2 z[3] = {scale2(a, m), scale2(b, m), scale2(c, m)};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -398,27 +401,30 @@ k_sp_normalise(Dims g, const float2* in, float2* out, int project, float inv_n) 
 }  // namespace
 
 cudaError_t launch_sp_init(const Dims& g, const float2* gh, float2* r, float2* s, float2* p,
-                           float2* pc, double beta, int kind, int project, double* partials,
-                           int nblk, cudaStream_t st) {
-    k_sp_init<<<nblk, kThreads, 0, st>>>(g, gh, r, s, p, pc, (float)beta, kind, project, partials);
+                           float2* pc, double beta, double shift, int kind, int project,
+                           double* partials, int nblk, cudaStream_t st) {
+    k_sp_init<<<nblk, kThreads, 0, st>>>(g, gh, r, s, p, pc, (float)beta, (float)shift, kind,
+                                         project, partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sp_update(const Dims& g, float2* s, float2* r, const float2* p,
                              const float2* B, double* sc, int irz, int ipap, int ipb, int ipq,
-                             double beta, int kind, int project, double* partials, int nblk,
-                             cudaStream_t st) {
+                             double beta, double shift, int kind, int project,
+                             double* partials, int nblk, cudaStream_t st) {
     k_sp_update<<<nblk, kThreads, 0, st>>>(g, s, r, p, B, sc, irz, ipap, ipb, ipq, (float)beta,
-                                           kind, project, 1.0f / (float)g.n, partials);
+                                           (float)shift, kind, project, 1.0f / (float)g.n,
+                                           partials);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sp_direction(const Dims& g, const float2* r, float2* p, float2* pc,
                                 const double* sc, int irznew, int irz, int zero_beta,
-                                double beta, int kind, int project, double* partials, int nblk,
-                                cudaStream_t st) {
+                                double beta, double shift, int kind, int project,
+                                double* partials, int nblk, cudaStream_t st) {
     k_sp_direction<<<nblk, kThreads, 0, st>>>(g, r, p, pc, sc, irznew, irz, zero_beta,
-                                              (float)beta, kind, project, partials);
+                                              (float)beta, (float)shift, kind, project,
+                                              partials);
     return cudaGetLastError();
 }
 

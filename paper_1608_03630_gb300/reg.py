@@ -33,7 +33,8 @@ class SolveOpts(ctypes.Structure):
                 ('max_pcg', ctypes.c_int), ('forcing', ctypes.c_int),
                 ('armijo_c', ctypes.c_double), ('armijo_shrink', ctypes.c_double),
                 ('armijo_max', ctypes.c_int), ('use_graph', ctypes.c_int),
-                ('verbose', ctypes.c_int), ('gnorm_ref', ctypes.c_double)]
+                ('verbose', ctypes.c_int), ('gnorm_ref', ctypes.c_double),
+                ('precond_shift', ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):

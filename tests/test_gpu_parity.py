@@ -281,3 +281,20 @@ def test_device_pcg_loop_respects_the_iteration_cap(reg):
         assert st['pcg_iters'] <= 2 * st['gn_iters']
     assert res[0][1]['pcg_iters'] == res[1][1]['pcg_iters']
     assert rel(res[1][2], res[0][2]) < 1e-6
+
+
+def test_shifted_preconditioner_reaches_the_same_stopping_test(reg):
+    """precond_shift > 0 changes only the PCG preconditioner, M = 1/(beta A +
+    shift): the solve reaches the same stopping test and objective."""
+    shape = (32, 32, 32)
+    rho_T, rho_R, _ = synth.sinusoid_problem(shape, 1.0)
+    R = reg.Registration(shape, 4, 1e-3)
+    R.set_images(dev(rho_T), dev(rho_R))
+    res = {}
+    for sh in (0.0, 3e-3):
+        v = torch.zeros((3,) + shape, device='cuda')
+        s, st = R.solve(v, gtol=1e-2, precond_shift=sh)
+        assert s == 0 and st['gnorm_rel'] <= 1e-2
+        res[sh] = st
+    R.close()
+    assert abs(res[3e-3]['J'] - res[0.0]['J']) < 1e-3 * res[0.0]['J']
