@@ -244,6 +244,22 @@ int reg_gaussian_smooth(reg_ctx* ctx, const float* f, float* out,
 int reg_inner(reg_ctx* ctx, const float* a, const float* b, size_t count,
               double* out);
 
+/* ---------------------------------------------------- deformation check */
+
+/* Displacement u = y(x, 1) - x of the deformation map of v [3n]: y solves
+ * d_t y + v . grad y = 0, y(0) = x (Sec. II-A), so u solves
+ * d_t u + v . grad u = -v, u(0) = 0, advanced by the context's nt
+ * semi-Lagrangian steps with the source -v (Eq. sml-advection) on the
+ * forward points of v.  u: device [3n], not overlapping v.  Overwrites the
+ * context's points, so a reg_hessian_matvec needs a new reg_gradient. */
+int reg_deformation(reg_ctx* ctx, const float* v, float* u);
+
+/* det(grad y) = det(I + grad u) [n] with spectral derivatives; close to 1
+ * everywhere for a divergence-free v (the incompressible check).  Needs
+ * nt >= 2 (it borrows the grad rho cache, and a reg_hessian_matvec then
+ * needs a new reg_gradient). */
+int reg_jacobian_det(reg_ctx* ctx, const float* u, float* det);
+
 /* ------------------------------------------------------------- tuning */
 
 /* Tile of the interpolation kernels: each thread walks k points (multiple of

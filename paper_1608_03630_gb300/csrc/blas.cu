@@ -84,6 +84,22 @@ __global__ void k_axpby_out(float* __restrict__ out, const float* __restrict__ x
         out[i] = fmaf(a, x[i], b * y[i]);
 }
 
+// det(I + grad u) at every point, gu[(3 c + j) n + i] = d_j u_c
+__global__ void k_jacobian_det(const float* __restrict__ gu, float* __restrict__ det,
+                               long long n) {
+    const long long stride = (long long)gridDim.x * kThreads;
+    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+        float m[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) m[c][j] = gu[(3 * c + j) * n + i] + (c == j ? 1.f : 0.f);
+        det[i] = m[0][0] * (m[1][1] * m[2][2] - m[1][2] * m[2][1]) -
+                 m[0][1] * (m[1][0] * m[2][2] - m[1][2] * m[2][0]) +
+                 m[0][2] * (m[1][0] * m[2][1] - m[1][1] * m[2][0]);
+    }
+}
+
 __global__ void k_scale(float* __restrict__ y, float alpha, long long count) {
     const long long stride = (long long)gridDim.x * kThreads;
     for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < count; i += stride)
@@ -140,6 +156,11 @@ cudaError_t launch_axpy(float* y, const float* x, float alpha, long long count,
 cudaError_t launch_axpby_out(float* out, const float* x, const float* y, float a, float b,
                              long long count, cudaStream_t st) {
     k_axpby_out<<<grid_for(count), kThreads, 0, st>>>(out, x, y, a, b, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_jacobian_det(const float* gu, float* det, long long n, cudaStream_t st) {
+    k_jacobian_det<<<grid_for(n), kThreads, 0, st>>>(gu, det, n);
     return cudaGetLastError();
 }
 

@@ -190,6 +190,9 @@ cudaError_t launch_incstate_step(const Dims& g, Tile t, const float* u_in, const
 // u_0 = -dt/2 v~ . grad rho(t_0)
 cudaError_t launch_incstate_init(const Dims& g, const float* vt, const float* grad0, float dt,
                                  float* u0, cudaStream_t st);
+// det(I + grad u) pointwise from the nine derivative fields
+// gu[(3 c + j) n ..] = d_j u_c.
+cudaError_t launch_jacobian_det(const float* gu, float* det, long long n, cudaStream_t st);
 // Deformation displacement step: u_{j+1} = I[u_j](X) + dt/2 (I[-v](X) - v(x)).
 cudaError_t launch_deformation_step(const Dims& g, const float* u_in, const float* v,
                                     const float* d, float dt, float* u_out,

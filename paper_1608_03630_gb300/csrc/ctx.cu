@@ -720,6 +720,43 @@ int reg_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj) {
     return op_departure(c, v, d_fwd, d_adj);
 }
 
+int reg_deformation(reg_ctx* c, const float* v, float* u) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, v);
+    CHECK_PTR(c, u);
+    if (u == v) return fail(c, REG_EINVAL, "v and u overlap");
+    const long long n = c->g.n;
+    c->have_lin = false;   // d_fwd / d_adj are overwritten
+    REG_TRY(op_departure(c, v, c->d_fwd, c->d_adj));
+    // ping-pong between u and tmp3 so that the last step writes u
+    float* bufs[2] = {u, c->tmp3};
+    const int nt = c->nt;
+    float* first_in = bufs[nt % 2];
+    REG_CK(c, cudaMemsetAsync(first_in, 0, sizeof(float) * 3 * n, c->stream));
+    for (int j = 0; j < nt; ++j) {
+        const float* in = bufs[(nt - j) % 2];
+        float* out = bufs[(nt - 1 - j) % 2];
+        Phase p(c, REG_PH_OTHER, 12.0 * 3 * n);
+        REG_CK(c, launch_deformation_step(c->g, in, v, c->d_fwd, (float)(1.0 / nt), out,
+                                          c->stream));
+    }
+    return REG_OK;
+}
+
+int reg_jacobian_det(reg_ctx* c, const float* u, float* det) {
+    CHECK_CTX(c);
+    CHECK_PTR(c, u);
+    CHECK_PTR(c, det);
+    if (c->nt < 2) return fail(c, REG_ENOTIMPL, "reg_jacobian_det needs nt >= 2 (scratch space)");
+    const long long n = c->g.n;
+    c->have_lin = false;   // the grad rho cache holds the derivatives
+    float* gu = c->grad_hist;   // (nt + 1) 3n >= 9n floats
+    for (int comp = 0; comp < 3; ++comp) REG_TRY(op_grad(c, u + comp * n, gu + comp * 3 * n));
+    Phase p(c, REG_PH_OTHER, 40.0 * n);
+    REG_CK(c, launch_jacobian_det(gu, det, n, c->stream));
+    return REG_OK;
+}
+
 int reg_interp(reg_ctx* c, const float* field, int nfields, const float* disp, float* out) {
     CHECK_CTX(c);
     CHECK_PTR(c, field);

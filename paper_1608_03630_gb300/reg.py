@@ -101,6 +101,8 @@ _SIGS = {
     'reg_batch_destroy': [_P],
     'reg_batch_solve': [_P, _P, _P, _P, _I, _I, ctypes.POINTER(SolveOpts), _P, _P, _P],
     'reg_spectral_resample': [_P, _P, _I, _P, _P, _P],
+    'reg_deformation': [_P, _P, _P],
+    'reg_jacobian_det': [_P, _P, _P],
     'reg_unet_create': [_I, _I, _P, _I, _I, ctypes.POINTER(_P)],
     'reg_unet_destroy': [_P],
     'reg_unet_set_stream': [_P, _P],
@@ -303,6 +305,18 @@ class Registration:
         self._call('reg_state_transport', _ptr(rho0, self.shape, 'rho0'),
                    _ptr(d_fwd, self.vshape, 'd_fwd'), _ptr(hist))
         return hist
+
+    def deformation(self, v, out=None):
+        """u = y(x, 1) - x of the deformation map of v (reg_deformation)."""
+        u = self._new(self.vshape) if out is None else out
+        self._call('reg_deformation', _ptr(v, self.vshape, 'v'), _ptr(u, self.vshape, 'u'))
+        return u
+
+    def jacobian_det(self, u, out=None):
+        """det(I + grad u) (reg_jacobian_det)."""
+        d = self._new(self.shape) if out is None else out
+        self._call('reg_jacobian_det', _ptr(u, self.vshape, 'u'), _ptr(d, self.shape, 'det'))
+        return d
 
     def spectral_grad(self, f):
         o = self._new(self.vshape)

@@ -298,3 +298,29 @@ def test_shifted_preconditioner_reaches_the_same_stopping_test(reg):
         res[sh] = st
     R.close()
     assert abs(res[3e-3]['J'] - res[0.0]['J']) < 1e-3 * res[0.0]['J']
+
+
+@pytest.mark.parametrize('shape', [(20, 24, 28), (17, 23, 30)])
+def test_deformation_and_jacobian_match_the_oracle(reg, shape):
+    nt = 4
+    v = f32(0.8 * synth.bandlimited(shape, 3, 77))
+    R = reg.Registration(shape, nt, 1e-3)
+    u = host(R.deformation(dev(v)))
+    u_ref = otr.deformation_displacement(v, otr.departure(v, 1.0 / nt), nt)
+    assert rel(u, u_ref) < 1e-5
+    det = host(R.jacobian_det(dev(u)))
+    det_ref = otr.jacobian_determinant(f32(u))
+    assert np.abs(det - det_ref).max() < 1e-5 * np.abs(det_ref).max()
+    R.close()
+
+
+def test_divergence_free_velocity_keeps_the_jacobian_at_one(reg):
+    """The incompressible check at 128^3: the deformation map of the exactly
+    divergence-free v* (scale 1) has det(grad y) = 1 up to discretisation
+    (max |det - 1| <= 1e-2)."""
+    shape = (128, 128, 128)
+    R = reg.Registration(shape, 8, 1e-3)
+    u = R.deformation(dev(synth.vstar(shape, 1.0)))
+    det = host(R.jacobian_det(u))
+    R.close()
+    assert np.abs(det - 1.0).max() <= 1e-2
