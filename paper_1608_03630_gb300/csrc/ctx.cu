@@ -469,6 +469,7 @@ static void free_ctx(reg_ctx* c) {
     for (int i = 0; i < 8; ++i)
         if (c->ss[i]) cudaFree(c->ss[i]);
     if (c->hsc) cudaFreeHost(c->hsc);
+    if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     for (auto& p : c->pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
     for (auto& p : c->graph_pairs) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }

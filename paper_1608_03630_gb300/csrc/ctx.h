@@ -50,6 +50,11 @@ struct reg_ctx {
     double* dsc;         // device scalars [32]
     double* hsc;         // pinned host mirror [32]
     double pshift;       // shift of the solver's spectral preconditioner (reg_solve)
+    // the device-controlled PCG graph, reused while the kernels it captured
+    // stay the same: key = (halo_fwd, halo_adj, tile k, tile wy), pshift
+    cudaGraphExec_t pcg_exec;
+    int pcg_key[4];
+    double pcg_key_shift;
     reg::Tile tile;      // tile of the interpolation kernels (k, wy)
     int halo_fwd, halo_adj;   // ceil(max |X - x|) of d_fwd / d_adj (-1: unknown)
     unsigned int* dabs;  // [2] device scratch for max |d| (float bits)

@@ -190,7 +190,20 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
     if (std::sqrt(c->hsc[SC_RR]) <= tol) { res->converged = true; return REG_OK; }
 
     if (use_graph >= 2 && !c->timing && verbose <= 1) {
-        cudaGraphExec_t loop = build_pcg_loop(c);
+        // reuse the captured loop while its kernels and launch shapes are
+        // unchanged (they depend on the halos and the tile only)
+        const int key[4] = {c->halo_fwd, c->halo_adj, c->tile.k, c->tile.wy};
+        if (c->pcg_exec && (memcmp(key, c->pcg_key, sizeof key) != 0 ||
+                            c->pcg_key_shift != c->pshift)) {
+            cudaGraphExecDestroy(c->pcg_exec);
+            c->pcg_exec = nullptr;
+        }
+        if (!c->pcg_exec) {
+            c->pcg_exec = build_pcg_loop(c);
+            memcpy(c->pcg_key, key, sizeof key);
+            c->pcg_key_shift = c->pshift;
+        }
+        cudaGraphExec_t loop = c->pcg_exec;
         if (loop) {
             int status = REG_OK;
             k_pcg_setup<<<1, 1, 0, c->stream>>>(c->dsc, tol * tol, max_it);
@@ -198,7 +211,6 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
             if (e == cudaSuccess) e = cudaGraphLaunch(loop, c->stream);
             if (e != cudaSuccess) status = fail_cuda(c, e, "PCG loop launch", __LINE__);
             if (status == REG_OK) status = read_scalars(c, 0, SC_MAXIT + 1);
-            cudaGraphExecDestroy(loop);
             if (status != REG_OK) return status;
             res->iters = (int)c->hsc[SC_IT];
             const int flag = (int)c->hsc[SC_FLAG];
