@@ -108,7 +108,6 @@ def conv_flops(net):
     convolution and the data gradient of every one but the first."""
     fwd = 0.0
     first = 0.0
-    L = len(net.channels)
     for name, ws, _ in net.layer_shapes():
         lvl = 0 if name == 'head' else int(name[3:name.index('.')])
         vox = (net.R >> lvl) ** 3
@@ -116,7 +115,6 @@ def conv_flops(net):
         fwd += f
         if name == 'enc0.0':
             first = f
-    del L
     return fwd, 3.0 * fwd - first
 
 
