@@ -261,7 +261,7 @@ def gpu_bench(args):
                 ctx.gradient(zero, out=gbuf)
                 gref = ctx.inner(gbuf, gbuf) ** 0.5
                 v.copy_(learned_init.predict(net, info['scale'], dT, dR, SHAPE[0], info['kc'],
-                                             info['alpha']))
+                                             info['alpha'], info['stages'], ctx))
                 return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500, gnorm_ref=gref)
             v.zero_()
             return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500)
@@ -373,8 +373,11 @@ def gpu_bench(args):
     launches = sum(int(v['launches']) for k, v in timing.items() if k != 'fft')
     launches += sum(s['gn_iters'] + s['pcg_iters'] for s in stats)
     if learned:
-        # per step: the network forward and three Fourier resamplings
-        launches += args.steps * (unet_launches(net.channels) + 3)
+        # per step and prediction stage: the network forward and three
+        # Fourier resamplings; from the second stage on also the points of
+        # the guess, their |D| reduction and the nt state steps
+        st = info['stages']
+        launches += args.steps * (st * (unet_launches(net.channels) + 3) + (st - 1) * (NT + 2))
     counts = {'gradient_evals': last['gradient_evals'], 'matvecs': last['matvecs'],
               'objective_evals': last['objective_evals']}
     form = '%s guess, %s' % (args.init, args.precision)
@@ -385,7 +388,8 @@ def gpu_bench(args):
         'dtype': 'f32', 'data': 'synthetic',
         'config': {'workload': 'phantom 256^3 nt=8 H2 beta=1e-3, %s' % form,
                    'init': (('U-Net (64^3, 16/32/64/128, bf16) prediction, modes |k|<%s, '
-                             'x%.2f' % (info['kc'], info['alpha'])) if learned else 'v = 0'),
+                             'x%.2f, %d stage(s)' % (info['kc'], info['alpha'], info['stages']))
+                            if learned else 'v = 0'),
                    'storage': ('bf16 images, fp32 fields'
                                if args.precision == 'mixed_bf16' else 'fp32'),
                    'grid': list(SHAPE), 'nt': NT, 'beta': BETA, 'regularisation': KIND,

@@ -197,39 +197,65 @@ def train(net, X, V, scale, epochs, lr, seed=0, val=None, budget_s=None, log=pri
     return hist
 
 
-def predict(net, scale, rho_T, rho_R, n, kc=None, alpha=1.0):
+def predict(net, scale, rho_T, rho_R, n, kc=None, alpha=1.0, stages=1, ctx=None):
     """Initial velocity at n^3: the network at its grid, times alpha * scale,
     keeping the Fourier modes |k_j| < kc (the H2-regularised solutions carry
     almost all their energy there; the network's error outside them would
-    cost beta |k|^4 in the objective), resampled to n^3."""
+    cost beta |k|^4 in the objective), resampled to n^3.  stages > 1 (ctx: a
+    reg.Registration at n^3): the template is transported by the guess so
+    far and the network's prediction for (transported template, rho_R) is
+    added, a first-order correction of the remaining deformation."""
     y = net.forward(net_input(rho_T, rho_R, net.R))
     y.mul_(alpha * scale)
-    return band_limit(y, kc, n).contiguous()
+    v = band_limit(y, kc, n).contiguous()
+    for _ in range(stages - 1):
+        d_fwd, _ = ctx.departure(v)
+        rho1 = ctx.state_transport(rho_T, d_fwd)[-1].contiguous()
+        y = net.forward(net_input(rho1, rho_R, net.R))
+        y.mul_(alpha * scale)
+        v = (v + band_limit(y, kc, n)).contiguous()
+    return v
 
 
 def select_cutoff(net, scale, seeds, n, cutoffs=(4, 6, 8, 12, 16, 32), alphas=(0.6, 0.8, 1.0),
-                  nt=8, beta=1e-3, log=print):
+                  stage_options=(1, 2, 3), nt=8, beta=1e-3, log=print):
     """The (kc, alpha) with the smallest mean J(v0) / J(0) over the pairs
-    `seeds` at n^3 (pairs used for nothing else)."""
+    `seeds` at n^3 (pairs used for nothing else), then the number of stages
+    at that (kc, alpha).  Returns ((kc, alpha, stages), table)."""
     shape = (n, n, n)
     ctx = reg.Registration(shape, nt, beta, 'H2')
-    table = {}
+    table, stab = {}, {}
+    pairs = []
     for seed in seeds:
         rho_T, rho_R, _ = phantom(n, seed)
-        rho_T, rho_R = rho_T.contiguous(), rho_R.contiguous()
+        pairs.append((rho_T.contiguous(), rho_R.contiguous()))
+    j0s = []
+    for rho_T, rho_R in pairs:
         ctx.set_images(rho_T, rho_R, presmooth=True)
         j0 = ctx.objective(torch.zeros((3,) + shape, device='cuda'))
+        j0s.append(j0)
         for kc in cutoffs:
             base = predict(net, scale, rho_T, rho_R, n, kc, 1.0)
             for a in alphas:
                 table.setdefault((kc, a), []).append(ctx.objective((a * base).contiguous()) / j0)
-    ctx.close()
     mean = {k: float(np.mean(v)) for k, v in table.items()}
-    best = min(mean, key=mean.get)
+    kc, alpha = min(mean, key=mean.get)
+    for (rho_T, rho_R), j0 in zip(pairs, j0s):
+        ctx.set_images(rho_T, rho_R, presmooth=True)
+        for st in stage_options:
+            v = predict(net, scale, rho_T, rho_R, n, kc, alpha, st, ctx)
+            stab.setdefault(st, []).append(ctx.objective(v) / j0)
+    smean = {k: float(np.mean(v)) for k, v in stab.items()}
+    stages = min(smean, key=smean.get)
+    ctx.close()
     if log:
         log('J(v0)/J(0) by (kc, alpha): ' +
             ', '.join('%s: %.3f' % (k, v) for k, v in sorted(mean.items())))
-    return best, {'%d,%.2f' % k: v for k, v in mean.items()}
+        log('J(v0)/J(0) by stages at (%s, %.2f): ' % (kc, alpha) +
+            ', '.join('%d: %.3f' % (k, v) for k, v in sorted(smean.items())))
+    out = {'%d,%.2f' % k: v for k, v in mean.items()}
+    out.update({'stages %d' % k: v for k, v in smean.items()})
+    return (kc, alpha, stages), out
 
 
 ARMS = (('plain', 'zero', 'fp32'), ('learned_fp32', 'learned', 'fp32'),
@@ -237,7 +263,7 @@ ARMS = (('plain', 'zero', 'fp32'), ('learned_fp32', 'learned', 'fp32'),
 
 
 def evaluate(net, scale, seeds, n, kc=None, alpha=1.0, nt=8, beta=1e-3, gtol=1e-2,
-             arms=ARMS, log=print):
+             arms=ARMS, stages=1, log=print):
     """Each arm (name, initial guess 'zero' | 'learned', precision) solves the
     held-out pairs at n^3 to ||g|| <= gtol ||g(0)||, g(0) the FP32 gradient at
     v = 0.  Per arm and pair: the solver's statistics, the wall time from the
@@ -266,7 +292,7 @@ def evaluate(net, scale, seeds, n, kc=None, alpha=1.0, nt=8, beta=1e-3, gtol=1e-
             if init == 'zero':
                 v = torch.zeros((3,) + shape, device='cuda')
             else:
-                v = predict(net, scale, rho_T, rho_R, n, kc, alpha)
+                v = predict(net, scale, rho_T, rho_R, n, kc, alpha, stages, ctx)
             s, st = ctx.solve(v, gtol=gtol, gnorm_ref=gref)
             torch.cuda.synchronize()
             st['seconds'] = time.perf_counter() - t0
@@ -307,11 +333,11 @@ def he_normal(net, seed):
     return np.concatenate(parts).astype(np.float32)
 
 
-def save_params(path, net, scale, meta, kc=None, alpha=1.0):
+def save_params(path, net, scale, meta, kc=None, alpha=1.0, stages=1):
     np.savez(path, params=net.get_params().astype(np.float16), scale=np.float64(scale),
              channels=np.array(net.channels), res=np.int64(net.R),
              kc=np.int64(0 if kc is None else kc), alpha=np.float64(alpha),
-             meta=np.array(json.dumps(meta)))
+             stages=np.int64(stages), meta=np.array(json.dumps(meta)))
 
 
 def load(path):
@@ -322,7 +348,8 @@ def load(path):
     net.set_params(d['params'].astype(np.float32))
     kc = int(d['kc']) if 'kc' in d and int(d['kc']) > 0 else None
     alpha = float(d['alpha']) if 'alpha' in d else 1.0
-    return net, {'scale': float(d['scale']), 'kc': kc, 'alpha': alpha,
+    stages = int(d['stages']) if 'stages' in d else 1
+    return net, {'scale': float(d['scale']), 'kc': kc, 'alpha': alpha, 'stages': stages,
                  'meta': json.loads(str(d['meta']))}
 
 
@@ -344,6 +371,8 @@ def main(argv=None):
     ap.add_argument('--select', type=int, default=8,
                     help='pairs (at the evaluation grid) that choose the cutoff and scale')
     ap.add_argument('--select-seed', type=int, default=7300)
+    ap.add_argument('--stages', type=int, default=0,
+                    help='prediction stages (0: the stored or selected number)')
     ap.add_argument('--eval-large', type=int, default=0, help='grid of one more held-out pair')
     ap.add_argument('--eval-large-seed', type=int, default=7100)
     ap.add_argument('--train-seed', type=int, default=5000)
@@ -394,20 +423,24 @@ def main(argv=None):
         del X, V, Xt, Vt, Xv, Vv
         torch.cuda.empty_cache()
     report['scale'] = scale
-    kc, alpha = (info['kc'], info['alpha']) if a.load else (None, 1.0)
+    kc, alpha, stages = (info['kc'], info['alpha'], info['stages']) if a.load else (None, 1.0, 1)
     if a.select > 0:
-        (kc, alpha), table = select_cutoff(net, scale, range(a.select_seed, a.select_seed + a.select),
-                                           a.eval_n, log=log)
-        report['select'] = {'kc': kc, 'alpha': alpha, 'J_ratio': table}
-        save_params(os.path.join(a.out, 'unet_r%d.npz' % net.R), net, scale, meta, kc, alpha)
+        (kc, alpha, stages), table = select_cutoff(
+            net, scale, range(a.select_seed, a.select_seed + a.select), a.eval_n, log=log)
+        report['select'] = {'kc': kc, 'alpha': alpha, 'stages': stages, 'J_ratio': table}
+        save_params(os.path.join(a.out, 'unet_r%d.npz' % net.R), net, scale, meta, kc, alpha,
+                    stages)
+    if a.stages:
+        stages = a.stages
     if a.eval > 0:
         ev = evaluate(net, scale, range(a.eval_seed, a.eval_seed + a.eval), a.eval_n, kc, alpha,
-                      log=log)
+                      stages=stages, log=log)
         report['eval'] = ev
         report['eval_summary'] = summarise(ev)
         log('summary ' + json.dumps(report['eval_summary']))
     if a.eval_large > 0:
-        ev = evaluate(net, scale, [a.eval_large_seed], a.eval_large, kc, alpha, log=log)
+        ev = evaluate(net, scale, [a.eval_large_seed], a.eval_large, kc, alpha, stages=stages,
+                      log=log)
         report['eval_large'] = ev
     with open(os.path.join(a.out, 'report.json'), 'w') as f:
         json.dump(report, f, indent=1)

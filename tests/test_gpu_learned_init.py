@@ -42,7 +42,7 @@ def test_pipeline_runs_at_small_size(li):
     scale = float(torch.sqrt(torch.mean(V * V)))
     hist = li.train(net, X[:4], V[:4], scale, epochs=3, lr=1e-3, val=(X[4:], V[4:]), log=None)
     assert len(hist) == 3 and all(np.isfinite(h['train_loss']) for h in hist)
-    ev = li.evaluate(net, scale, [200], 32, log=None)
+    ev = li.evaluate(net, scale, [200], 32, stages=2, log=None)
     for name, _, prec in li.ARMS:
         e = ev[0][name]
         assert e['status'] == 0
@@ -59,7 +59,7 @@ def test_learned_guess_saves_matvecs_on_held_out_pairs(li):
     net, info = li.load(WEIGHTS)
     arms = (('plain', 'zero', 'fp32'), ('learned', 'learned', 'fp32'))
     ev = li.evaluate(net, info['scale'], [7000, 7001, 7002], 256, info['kc'], info['alpha'],
-                     arms=arms, log=None)
+                     arms=arms, stages=info['stages'], log=None)
     zero = sum(e['plain']['matvecs'] for e in ev)
     learned = sum(e['learned']['matvecs'] for e in ev)
     for e in ev:
