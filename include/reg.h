@@ -61,7 +61,7 @@ typedef enum {
  *            divergence penalty vanishes, so it acts as REG_H1). */
 enum { REG_H1 = 1, REG_H2 = 2, REG_H1DIV = 3 };
 
-/* Storage precision of the images and the cached state gradients.
+/* Storage precision of the images.
  *  REG_FP32        everything FP32 (reductions FP64);
  *  REG_MIXED_BF16  rho_T and rho_R stored in bfloat16 (rounded once in
  *                  reg_set_images, widened where a step reads them);
