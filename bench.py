@@ -322,7 +322,7 @@ def gpu_bench(args):
             torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
 
-        # the other forms of the method, one timed solve each after a warm-up,
+        # the other forms of the method, the faster of two timed solves each after a warm-up,
         # to the same stopping test (the plain FP32 solver is the target's
         # comparison)
         arms = {}
@@ -337,12 +337,17 @@ def gpu_bench(args):
                 ctxs[prec] = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=prec,
                                               stream=stream)
             solve_from_images(ctxs[prec], init)
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            _, st = solve_from_images(ctxs[prec], init)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            arms[name] = {'time_to_solution_s': e0.elapsed_time(e1) / 1e3,
+            best = None
+            for _ in range(2):   # the faster of two timed solves
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                _, st = solve_from_images(ctxs[prec], init)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / 1e3
+                best = t if best is None else min(best, t)
+            arms[name] = {'time_to_solution_s': best,
                           'gn_iters': st['gn_iters'], 'matvecs': st['matvecs'],
                           'gnorm_rel': st['gnorm_rel'], 'mismatch_rel': st['mismatch_rel']}
         for c in ctxs.values():
