@@ -153,7 +153,9 @@ constexpr int kMaxBoxFloats16 = 28224;
 cudaError_t launch_absmax(const float* d, long long count, unsigned int* out, cudaStream_t st);
 
 // transport.cu
-cudaError_t launch_departure(const Dims& g, const float* v, float dt, float* d_fwd,
+// t.halo (>= ceil of the predictor's largest displacement, grid units) and
+// the tile select the shared-memory staged kernel when it applies.
+cudaError_t launch_departure(const Dims& g, Tile t, const float* v, float dt, float* d_fwd,
                              float* d_adj, cudaStream_t st);
 // out = I[f](x + d) for one scalar field.
 cudaError_t launch_interp(const Dims& g, Tile t, const float* f, const float* d, float* out,

@@ -105,8 +105,14 @@ void release_graph_timing(reg_ctx* c) {
 // ------------------------------------------------------------- operations
 
 int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj) {
+    // the predictor's displacement dt v_j n_j / (2 pi) (grid units) is below
+    // max |v| dt max_j n_j / (2 pi): its ceiling is the staged kernel's halo
+    const int nmax = std::max(c->g.n1, std::max(c->g.n2, c->g.n3));
+    int halo = 0;
+    REG_TRY(op_halo(c, v, &halo, (float)(nmax / (c->nt * 6.283185307179586))));
     Phase p(c, REG_PH_DEPARTURE, (double)c->g.n * (d_adj ? 36.0 : 24.0));
-    REG_CK(c, launch_departure(c->g, v, (float)(1.0 / c->nt), d_fwd, d_adj, c->stream));
+    REG_CK(c, launch_departure(c->g, tile_with(c, halo), v, (float)(1.0 / c->nt), d_fwd, d_adj,
+                               c->stream));
     return REG_OK;
 }
 
@@ -198,13 +204,14 @@ int read_scalars(reg_ctx* c, int first, int count) {
     return REG_OK;
 }
 
-int op_halo(reg_ctx* c, const float* d, int* halo) {
+int op_halo(reg_ctx* c, const float* d, int* halo, float scale) {
     REG_CK(c, launch_absmax(d, 3LL * c->g.n, c->dabs, c->stream));
     unsigned int bits = 0;
     REG_CK(c, cudaMemcpyAsync(&bits, c->dabs, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
     REG_CK(c, cudaStreamSynchronize(c->stream));
     float m;
     memcpy(&m, &bits, sizeof m);
+    m *= scale;
     if (!std::isfinite(m)) return fail(c, REG_ENONFINITE, "non-finite displacement");
     *halo = m < 1e6f ? (int)std::ceil(m) : 1000000;
     return REG_OK;

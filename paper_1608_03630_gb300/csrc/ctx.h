@@ -135,8 +135,8 @@ int op_precond(reg_ctx* c, const float* r, float* z);
 int op_leray(reg_ctx* c, const float* v, float* out);
 int read_scalars(reg_ctx* c, int first, int count);   // dsc -> hsc, synchronises
 int bind_stream(reg_ctx* c, cudaStream_t s);         // launch stream + cuFFT plans
-// ceil(max |d|) over a displacement field [3n] (synchronises the stream).
-int op_halo(reg_ctx* c, const float* d, int* halo);
+// ceil(scale max |d|) over a field [3n] (synchronises the stream).
+int op_halo(reg_ctx* c, const float* d, int* halo, float scale = 1.f);
 reg::Tile tile_with(const reg_ctx* c, int halo);
 int ensure_solver(reg_ctx* c);
 

@@ -612,6 +612,128 @@ cudaError_t run_tile_fixed(const Dims& g, Tile t, const float* f, const float* d
     return cudaGetLastError();
 }
 
+// Tricubic value at displacement (e1, e2, e3) (grid units) of the point of
+// local x1 plane kloc, from a staged box laid out as in k_tile_fixed
+// (H, WY fixed; clamped indices keep every read inside the box).
+template <int H, int WY>
+__device__ __forceinline__ float box_interp(const float* box, int E1, int kloc, int r2, int r3,
+                                            float e1, float e2, float e3) {
+    constexpr int E2 = WY + 3 + 2 * H;
+    constexpr int E3 = 35 + 2 * H;
+    constexpr int P3 = (E3 + 31) & ~31;
+    constexpr int E23 = E2 * P3;
+    const float fl1 = floorf(e1), fl2 = floorf(e2), fl3 = floorf(e3);
+    float w1[4], w2[4], w3[4];
+    lagrange4(e1 - fl1, w1);
+    lagrange4(e2 - fl2, w2);
+    lagrange4(e3 - fl3, w3);
+    const int l1 = min(max(kloc + H + (int)fl1, 0), E1 - 4);
+    const int l2 = min(max(r2 + (int)fl2, 0), E2 - 4);
+    const int l3 = min(max(r3 + (int)fl3, 0), E3 - 4);
+    const float* base = box + (l1 * E2 + l2) * P3 + l3;
+    const f32x2 w2a = pk(w2[0], w2[1]), w2b = pk(w2[2], w2[3]);
+    f32x2 ww3[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ww3[c] = pk(w3[c], w3[c]);
+    float r[4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const float* pl = base + a * E23;
+        f32x2 s01 = mul2(ww3[0], pk(pl[0], pl[P3]));
+        f32x2 s23 = mul2(ww3[0], pk(pl[2 * P3], pl[3 * P3]));
+#pragma unroll
+        for (int c = 1; c < 4; ++c) {
+            s01 = fma2(ww3[c], pk(pl[c], pl[P3 + c]), s01);
+            s23 = fma2(ww3[c], pk(pl[2 * P3 + c], pl[3 * P3 + c]), s23);
+        }
+        const float2 t2 = upk(fma2(w2b, s23, mul2(w2a, s01)));
+        r[a] = t2.x + t2.y;
+    }
+    float val = w1[0] * r[0];
+    val = fmaf(w1[1], r[1], val);
+    val = fmaf(w1[2], r[2], val);
+    return fmaf(w1[3], r[3], val);
+}
+
+// RK2 points of v and -v (Eq. sml-trajectory) from shared memory: the boxes
+// of the three velocity components are staged one after the other, and each
+// serves both feet of every point of the tile (x - u and x + u, u = dt v(x)
+// in grid units, |u| <= H).
+template <int H>
+__global__ void __launch_bounds__(256)
+k_departure_tile(Dims g, int K, const float* __restrict__ v, float dth1, float dth2,
+                 float dth3, float* __restrict__ d_fwd, float* __restrict__ d_adj) {
+    constexpr int WY = 8;
+    constexpr int E2 = WY + 3 + 2 * H;
+    constexpr int E3 = 35 + 2 * H;
+    constexpr int P3 = (E3 + 31) & ~31;
+    extern __shared__ float box[];   // [E1][E2][P3], E3 columns used
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int E1 = K + 3 + 2 * H;
+    const int i3 = blockIdx.x * 32 + lane;
+    const int i2 = blockIdx.y * WY + ty;
+    const int i1b = blockIdx.z * K;
+    const int o1 = i1b - 1 - H, o2 = blockIdx.y * WY - 1 - H;
+    const int o3 = blockIdx.x * 32 - 1 - H;
+    const bool active = i3 < g.n3 && i2 < g.n2;
+    const int kend = min(K, g.n1 - i1b);
+    const long long n = g.n;
+    const int r2 = i2 - 1 - o2, r3 = i3 - 1 - o3;
+    int col[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) col[c] = wrap_near(o3 + lane + 32 * c, g.n3);
+    for (int comp = 0; comp < 3; ++comp) {
+        const float* f = v + comp * n;
+        const float dthc = comp == 0 ? dth1 : (comp == 1 ? dth2 : dth3);
+        if (comp > 0) __syncthreads();   // every thread is done with the last box
+        for (int a = 0; a < E1; ++a) {
+            const float* plane = f + (long long)wrap_near(o1 + a, g.n1) * g.n23;
+            for (int b = ty; b < E2; b += WY) {
+                const float* src = plane + wrap_near(o2 + b, g.n2) * g.n3;
+                float* dst = box + (a * E2 + b) * P3;
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    if (lane + 32 * c < E3) cp_async4(dst + lane + 32 * c, src + col[c]);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        if (!active) continue;
+        for (int k = 0; k < kend; ++k) {
+            const int idx = ((i1b + k) * g.n2 + i2) * g.n3 + i3;
+            const float u1 = __ldg(v + idx) * dth1;
+            const float u2 = __ldg(v + n + idx) * dth2;
+            const float u3 = __ldg(v + 2 * n + idx) * dth3;
+            const float uc = comp == 0 ? u1 : (comp == 1 ? u2 : u3);
+            // forward: X* = x - u, X = x - (u + dt v(X*)) / 2
+            const float af = box_interp<H, WY>(box, E1, k, r2, r3, -u1, -u2, -u3) * dthc;
+            d_fwd[comp * n + idx] = -0.5f * (uc + af);
+            if (d_adj) {
+                // adjoint (velocity -v): X* = x + u, X = x + (u + dt v(X*)) / 2
+                const float aa = box_interp<H, WY>(box, E1, k, r2, r3, u1, u2, u3) * dthc;
+                d_adj[comp * n + idx] = 0.5f * (uc + aa);
+            }
+        }
+    }
+}
+
+template <int H>
+cudaError_t run_departure_tile(const Dims& g, Tile t, const float* v, float dth1, float dth2,
+                               float dth3, float* d_fwd, float* d_adj, cudaStream_t st) {
+    constexpr int E2 = 8 + 3 + 2 * H;
+    constexpr int P3 = ((35 + 2 * H) + 31) & ~31;
+    const size_t smem = sizeof(float) * (size_t)(t.k + 3 + 2 * H) * E2 * P3;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k_departure_tile<H>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)(sizeof(float) * kMaxBoxFloats));
+        if (e != cudaSuccess) return e;
+    }
+    k_departure_tile<H><<<march_grid(g, t), dim3(32, 8), smem, st>>>(g, t.k, v, dth1, dth2, dth3,
+                                                                    d_fwd, d_adj);
+    return cudaGetLastError();
+}
+
 dim3 march_grid(const Dims& g, Tile t) {
     return dim3((g.n3 + 31) / 32, (g.n2 + t.wy - 1) / t.wy, (g.n1 + t.k - 1) / t.k);
 }
@@ -720,11 +842,16 @@ int march_blocks(const Dims& g, Tile t) {
     return (int)(gr.x * gr.y * gr.z);
 }
 
-cudaError_t launch_departure(const Dims& g, const float* v, float dt, float* d_fwd,
+cudaError_t launch_departure(const Dims& g, Tile t, const float* v, float dt, float* d_fwd,
                              float* d_adj, cudaStream_t st) {
     const float two_pi = 6.283185307179586f;
-    k_departure<<<nblocks(g.n), kThreads, 0, st>>>(
-        g, v, dt * g.n1 / two_pi, dt * g.n2 / two_pi, dt * g.n3 / two_pi, d_fwd, d_adj);
+    const float dth1 = dt * g.n1 / two_pi, dth2 = dt * g.n2 / two_pi, dth3 = dt * g.n3 / two_pi;
+    if (t.halo >= 0 && t.halo <= 3 && t.wy == 8 && tile_staged(t)) {
+        if (t.halo <= 1) return run_departure_tile<1>(g, t, v, dth1, dth2, dth3, d_fwd, d_adj, st);
+        if (t.halo == 2) return run_departure_tile<2>(g, t, v, dth1, dth2, dth3, d_fwd, d_adj, st);
+        return run_departure_tile<3>(g, t, v, dth1, dth2, dth3, d_fwd, d_adj, st);
+    }
+    k_departure<<<nblocks(g.n), kThreads, 0, st>>>(g, v, dth1, dth2, dth3, d_fwd, d_adj);
     return cudaGetLastError();
 }
 
