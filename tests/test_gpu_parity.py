@@ -56,9 +56,12 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize('shape', SHAPES)
-def test_departure_points(reg, shape):
+@pytest.mark.parametrize('amp', [2.5, 0.3])
+def test_departure_points(reg, shape, amp):
+    """amp 2.5: several cells per step (the unstaged kernel); amp 0.3: at
+    most a few cells (the shared-memory staged kernel)."""
     nt = 4
-    v = f32(2.5 * synth.bandlimited(shape, 3, 7))      # several cells per step
+    v = f32(amp * synth.bandlimited(shape, 3, 7))
     R = reg.Registration(shape, nt, 1e-2)
     df, da = R.departure(dev(v))
     ef = otr.departure(v, 1.0 / nt)
