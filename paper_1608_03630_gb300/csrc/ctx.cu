@@ -339,23 +339,35 @@ static int adjoint_solve(reg_ctx* c, int phase, float* out, const float* dotp, i
     return REG_OK;
 }
 
-int op_linearize(reg_ctx* c, const float* v) {
+// The points of v and -v, their halos and the state history of v (with
+// lam(1) and the mismatch) in the linearisation buffers.
+static int state_of(reg_ctx* c, const float* v) {
+    REG_TRY(op_departure(c, v, c->d_fwd, c->d_adj));
+    REG_TRY(op_halo(c, c->d_fwd, &c->halo_fwd));
+    REG_TRY(op_halo(c, c->d_adj, &c->halo_adj));
+    return state_solve(c, c->d_fwd, c->halo_fwd, c->rho_hist, true,
+                       c->lam_hist + (long long)c->nt * c->g.n);
+}
+
+int op_trial_state(reg_ctx* c, const float* v) {
+    c->have_lin = false;
+    return state_of(c, v);
+}
+
+int op_linearize(reg_ctx* c, const float* v, bool state_ready) {
     const Dims& g = c->g;
     const long long n = g.n;
     const int nt = c->nt;
     const bool comp = !c->incompressible;
     c->have_lin = false;
-    REG_TRY(op_departure(c, v, c->d_fwd, c->d_adj));
-    REG_TRY(op_halo(c, c->d_fwd, &c->halo_fwd));
-    REG_TRY(op_halo(c, c->d_adj, &c->halo_adj));
+    // points, halos, state history, lam(1) = rho_R - rho(1) and the mismatch
+    if (!state_ready) REG_TRY(state_of(c, v));
     if (comp) {
         REG_TRY(op_div(c, v, c->divv));
         Phase p(c, REG_PH_ADJOINT, 20.0 * n);
         REG_CK(c, launch_adjoint_coef(g, tile_with(c, c->halo_adj), c->divv, c->d_adj,
                                       (float)(1.0 / nt), c->coef, c->stream));
     }
-    // state history; lam(1) = rho_R - rho(1) into lam_hist[nt]
-    REG_TRY(state_solve(c, c->d_fwd, c->halo_fwd, c->rho_hist, true, c->lam_hist + nt * n));
     // spectral gradients of every level (cached for the matvecs)
     for (int j = 0; j <= nt; ++j) {
         float* gj = c->grad_hist + (long long)j * 3 * n;

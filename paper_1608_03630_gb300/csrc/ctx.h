@@ -121,7 +121,13 @@ int op_div(reg_ctx* c, const float* v3, float* out);
 int op_inner(reg_ctx* c, const float* a, const float* b, long long count, int slot);
 // Linearisation at v: points, div v and c(x), state history, grad rho
 // levels, adjoint, and b = int lam grad rho dt into bacc.
-int op_linearize(reg_ctx* c, const float* v);
+// state_ready: op_trial_state(c, v) ran last for this v (its points, state
+// history and mismatch are reused).
+int op_linearize(reg_ctx* c, const float* v, bool state_ready = false);
+// J's mismatch at v with the points and state history kept in the
+// linearisation buffers (the solver's line search: an accepted trial point
+// is linearised next without redoing them).  Invalidates the linearisation.
+int op_trial_state(reg_ctx* c, const float* v);
 int op_gradient(reg_ctx* c, const float* v, float* g, int slot_J);
 int op_objective(reg_ctx* c, const float* v, int slot_J);
 // dsc[SC_JMIS] = 1/2 ||rho(1) - rho_R||^2_h for v (scratch buffers only).

@@ -307,12 +307,14 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
 }
 
 // g_hat = beta A v_hat + P b_hat at the spectral iterate; J and ||g||.
-static int evaluate_gradient(reg_ctx* c, double* J, double* gnorm) {
+// after_trial: the accepted line-search trial point is v; its physical copy,
+// points and state history are still in place.
+static int evaluate_gradient(reg_ctx* c, double* J, double* gnorm, bool after_trial = false) {
     const int nb = blas_blocks();
     float2** S = c->ss;
     float* v = c->sv[R_V];
-    REG_TRY(to_physical(c, S[S_V], v));
-    REG_TRY(op_linearize(c, v));
+    if (!after_trial) REG_TRY(to_physical(c, S[S_V], v));
+    REG_TRY(op_linearize(c, v, after_trial));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
     {
         Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
@@ -329,7 +331,9 @@ static int evaluate_gradient(reg_ctx* c, double* J, double* gnorm) {
     return REG_OK;
 }
 
-// J at v_hat + alpha s_hat (into S_VT): forward state solve only.
+// J at v_hat + alpha s_hat (into S_VT): points and forward state solve of the
+// trial, kept in the linearisation buffers for the gradient that follows an
+// accepted step.
 static int evaluate_trial(reg_ctx* c, double alpha, double* J) {
     const int nb = blas_blocks();
     float2** S = c->ss;
@@ -341,7 +345,7 @@ static int evaluate_trial(reg_ctx* c, double alpha, double* J) {
     REG_TRY(finalize_to(c, 0, nb, 0.5 * c->beta * kTwoPi3, SC_JREG));
     float* v = c->sv[R_V];
     REG_TRY(op_fft_c2r(c, c->spec[0], v, 3));
-    REG_TRY(op_mismatch(c, v));
+    REG_TRY(op_trial_state(c, v));
     REG_TRY(read_scalars(c, SC_JMIS, 2));
     *J = c->hsc[SC_JMIS] + c->hsc[SC_JREG];
     return REG_OK;
@@ -408,7 +412,7 @@ static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solv
             break;
         }
         std::swap(S[S_V], S[S_VT]);
-        REG_TRY(evaluate_gradient(c, &J, &gn));
+        REG_TRY(evaluate_gradient(c, &J, &gn, true));
         jmis = c->hsc[SC_JMIS];
         st->gradient_evals++;
         st->gn_iters = k + 1;
