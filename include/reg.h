@@ -150,8 +150,10 @@ typedef struct {
     int verbose;          /* print one line per Newton iteration to stderr (0) */
     double gnorm_ref;     /* > 0: use it as ||g_0|| in the stop test and the
                              forcing term, e.g. the gradient norm at v = 0
-                             when v_inout holds a prediction; 0: ||g|| at the
-                             initial guess                               (0) */
+                             when v_inout holds a prediction; < 0: use the
+                             gradient norm at v = 0, from its closed form
+                             P[(rho_R - rho_T) grad rho_T] (one spectral
+                             gradient); 0: ||g|| at the initial guess    (0) */
     double precond_shift; /* >= 0: PCG preconditioner M = 1/(beta A + shift);
                              0 is the paper's inverse regularisation
                              operator (Sec. III-A)                       (0) */

@@ -100,6 +100,18 @@ __global__ void k_jacobian_det(const float* __restrict__ gu, float* __restrict__
     }
 }
 
+// out[c n + i] = s[i] v[c n + i], c = 0, 1, 2
+__global__ void k_mul_fields(const float* __restrict__ s, const float* __restrict__ v,
+                             float* __restrict__ out, long long n) {
+    const long long stride = (long long)gridDim.x * kThreads;
+    for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < n; i += stride) {
+        const float a = s[i];
+        out[i] = a * v[i];
+        out[n + i] = a * v[n + i];
+        out[2 * n + i] = a * v[2 * n + i];
+    }
+}
+
 __global__ void k_scale(float* __restrict__ y, float alpha, long long count) {
     const long long stride = (long long)gridDim.x * kThreads;
     for (long long i = (long long)blockIdx.x * kThreads + threadIdx.x; i < count; i += stride)
@@ -161,6 +173,12 @@ cudaError_t launch_axpby_out(float* out, const float* x, const float* y, float a
 
 cudaError_t launch_jacobian_det(const float* gu, float* det, long long n, cudaStream_t st) {
     k_jacobian_det<<<grid_for(n), kThreads, 0, st>>>(gu, det, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mul_fields(const float* s, const float* v, float* out, long long n,
+                              cudaStream_t st) {
+    k_mul_fields<<<grid_for(n), kThreads, 0, st>>>(s, v, out, n);
     return cudaGetLastError();
 }
 

@@ -272,5 +272,8 @@ cudaError_t launch_axpby_out(float* out, const float* x, const float* y, float a
 cudaError_t launch_finalize_multi(const double* partials, int nblk, int stride, int count,
                                   double scale, double* result, cudaStream_t st);
 cudaError_t launch_scale(float* y, float alpha, long long count, cudaStream_t st);
+// out[3][n] = s[n] * v[3][n] (pointwise, per component)
+cudaError_t launch_mul_fields(const float* s, const float* v, float* out, long long n,
+                              cudaStream_t st);
 
 }  // namespace reg

@@ -351,6 +351,48 @@ static int evaluate_trial(reg_ctx* c, double alpha, double* J) {
     return REG_OK;
 }
 
+// ||g(0)||: at v = 0 the transport is the identity, so rho(t) = rho(t_0),
+// lam(t) = rho_R - rho(t_0) and b = (rho_R - rho(t_0)) grad rho(t_0)
+// (trapezoid weights sum to 1); g(0) = P b (Eq. gradient).  One spectral
+// gradient instead of a linearisation; equal to the gradient at v = 0 up to
+// FP32 rounding.  Clobbers the linearisation buffers and S_G.
+static int gradient_norm_at_zero(reg_ctx* c, double* g0) {
+    const long long n = c->g.n;
+    const int nb = blas_blocks();
+    float2** S = c->ss;
+    c->have_lin = false;
+    float* r0 = c->rho_hist;   // rho(t_0) as the state solve starts from it
+    if (c->precision == REG_MIXED_BF16 && c->img_bf) {
+        Phase p(c, REG_PH_OTHER, 6.0 * n);
+        REG_CK(c, launch_from_bf16(c->img_bf, r0, n, c->stream));
+    } else {
+        REG_CK(c, cudaMemcpyAsync(r0, c->rho_T, sizeof(float) * n, cudaMemcpyDeviceToDevice,
+                                  c->stream));
+    }
+    {
+        Phase p(c, REG_PH_OTHER, 12.0 * n);
+        REG_CK(c, launch_axpby_out(c->tmp3, c->rho_R, r0, 1.f, -1.f, n, c->stream));
+    }
+    REG_TRY(op_grad(c, r0, c->grad_hist));
+    {
+        Phase p(c, REG_PH_OTHER, 28.0 * n);
+        REG_CK(c, launch_mul_fields(c->tmp3, c->grad_hist, c->bacc, n, c->stream));
+    }
+    REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_normalise(c->g, c->spec[1], S[S_G], c->incompressible, c->stream));
+    }
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_dot(c->g, S[S_G], S[S_G], c->partials, nb, c->stream));
+    }
+    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_GG));
+    REG_TRY(read_scalars(c, SC_GG, 1));
+    *g0 = std::sqrt(c->hsc[SC_GG]);
+    return REG_OK;
+}
+
 static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solve_stats* st) {
     const auto t0 = std::chrono::steady_clock::now();
     const long long n = c->g.n;
@@ -368,13 +410,15 @@ static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solv
     REG_TRY(read_scalars(c, SC_TMP, 1));
     const double m0 = std::sqrt(c->hsc[SC_TMP]);
 
+    double gz = 0.0;
+    if (o->gnorm_ref < 0.0) REG_TRY(gradient_norm_at_zero(c, &gz));
     double J, gn;
     REG_TRY(evaluate_gradient(c, &J, &gn));
     st->gradient_evals++;
     // the stop test and the forcing term are relative to ||g_0||: the
-    // gradient at the initial guess, or the caller's reference norm (the
-    // gradient at v = 0 when the guess is a prediction)
-    const double g0 = o->gnorm_ref > 0.0 ? o->gnorm_ref : gn;
+    // gradient at the initial guess, or a reference norm (the caller's, or
+    // the gradient at v = 0 when the guess is a prediction)
+    const double g0 = o->gnorm_ref > 0.0 ? o->gnorm_ref : (o->gnorm_ref < 0.0 ? gz : gn);
     st->J0 = J;
     st->gnorm0 = g0;
     double jmis = c->hsc[SC_JMIS];
@@ -463,7 +507,8 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
     reg_solve_opts o;
     reg_solve_opts_default(&o);
     if (opts) o = *opts;
-    if (!(o.gtol >= 0.0) || !(o.gnorm_ref >= 0.0) || !(o.precond_shift >= 0.0) || o.max_gn < 0 || o.max_pcg < 1 || o.armijo_max < 1 ||
+    if (!(o.gtol >= 0.0) || !std::isfinite(o.gnorm_ref) || !(o.precond_shift >= 0.0) ||
+        o.max_gn < 0 || o.max_pcg < 1 || o.armijo_max < 1 ||
         !(o.armijo_shrink > 0.0 && o.armijo_shrink < 1.0))
         return fail(c, REG_EINVAL, "bad solver options");
     REG_TRY(ensure_solver(c));

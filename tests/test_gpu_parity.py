@@ -327,3 +327,23 @@ def test_divergence_free_velocity_keeps_the_jacobian_at_one(reg):
     det = host(R.jacobian_det(u))
     R.close()
     assert np.abs(det - 1.0).max() <= 1e-2
+
+
+def test_closed_form_reference_norm_at_zero(reg):
+    """gnorm_ref < 0: the stop test uses ||g(0)|| from its closed form
+    P[(rho_R - rho_T) grad rho_T]; from v = 0 that is the solver's own
+    ||g_0|| (same iterates)."""
+    shape = (24, 24, 24)
+    rho_T, rho_R, _ = synth.sinusoid_problem(shape, 0.5)
+    res = []
+    for ref in (0.0, -1.0):
+        R = reg.Registration(shape, 4, 1e-3)
+        R.set_images(dev(rho_T), dev(rho_R), presmooth=True)
+        v = torch.zeros((3,) + shape, device='cuda')
+        s, st = R.solve(v, gtol=1e-2, gnorm_ref=ref)
+        R.close()
+        assert s == 0
+        res.append((st, host(v)))
+    assert abs(res[1][0]['gnorm0'] - res[0][0]['gnorm0']) < 1e-5 * res[0][0]['gnorm0']
+    assert res[1][0]['pcg_iters'] == res[0][0]['pcg_iters']
+    assert rel(res[1][1], res[0][1]) < 1e-6
