@@ -32,7 +32,7 @@ def lib():
     return reg.lib()
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_calls_of_the_path():
     names = declared_functions()
     for n in ('reg_create', 'reg_set_images', 'reg_gradient', 'reg_hessian_matvec',
               'reg_precond_apply', 'reg_solve', 'reg_destroy'):
