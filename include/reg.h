@@ -272,6 +272,16 @@ int reg_jacobian_det(reg_ctx* ctx, const float* u, float* det);
 int reg_set_tile(reg_ctx* ctx, int k, int wy);
 int reg_get_tile(const reg_ctx* ctx, int* k, int* wy);
 
+/* How the staged interpolation kernels fill their shared-memory box.
+ * tma = 1 (default): one TMA tensor copy per block (cp.async.bulk.tensor,
+ * completion on an mbarrier) wherever x3 is a multiple of 4 and the grid is
+ * at least one box large (n3 >= 64, n2 >= wy + 3 + 2h, n1 >= k + 3 + 2h for
+ * halo h); blocks at a face of the periodic domain reload the elements outside
+ * the grid from their periodic images.  Elsewhere, and with tma = 0, every
+ * thread issues 4-byte cp.async copies.  The box content, and so every result,
+ * is the same either way.  REG_EINVAL unless tma is 0 or 1. */
+int reg_set_staging(reg_ctx* ctx, int tma);
+
 /* Autotuner: time the interpolation kernels of the current linearisation
  * point (reg_gradient first, else REG_ENOTREADY) for a few tile shapes and
  * keep the fastest in ctx; the choice is cached per (grid, halo) for the

@@ -141,6 +141,8 @@ struct Tile {
     int halo = -1;  // bound on |floor(displacement)| (cells) of the launch's
                     // points; >= 0 selects the shared-memory staged kernel,
                     // -1 (unknown) the register-window kernel
+    int tma = 1;    // staged box by one TMA copy where the grid allows (1) or
+                    // by per-thread cp.async copies (0)
 };
 
 // Largest shared-memory box (floats) of the staged interpolation kernel.

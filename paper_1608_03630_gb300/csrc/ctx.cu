@@ -883,6 +883,13 @@ int reg_set_tile(reg_ctx* c, int k, int wy) {
     return REG_OK;
 }
 
+int reg_set_staging(reg_ctx* c, int tma) {
+    CHECK_CTX(c);
+    if (tma != 0 && tma != 1) return fail(c, REG_EINVAL, "staging: tma must be 0 or 1");
+    c->tile.tma = tma;
+    return REG_OK;
+}
+
 int reg_get_tile(const reg_ctx* c, int* k, int* wy) {
     if (!c || !k || !wy) return REG_EINVAL;
     *k = c->tile.k;

@@ -17,6 +17,12 @@
 // plane slots rotate with a period of four unrolled steps, so every register
 // index is static.
 #include <climits>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+
+#include <cuda.h>            // CUtensorMap and its enums (no driver library link:
+#include <cudaTypedefs.h>    // the encoder is fetched through the runtime)
 
 #include "common.cuh"
 
@@ -387,6 +393,62 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// Tensor-memory-accelerator staging: one cp.async.bulk.tensor copy brings a
+// whole 3-D box from global to shared memory, and an mbarrier counts its
+// bytes in (complete_tx).
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+    unsigned done;
+    asm volatile(
+        "{\n"
+        "  .reg .pred p;\n"
+        "  mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "  selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Wait for phase `parity` of the barrier for at most ~1 s of SM clock; false
+// when it gave up (the copy never completed).
+constexpr long long kStageWaitCycles = 2000000000LL;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kStageWaitCycles) return false;
+    return true;
+}
+
+// Box of the 3-D tensor map at element coordinates (x3, x2, x1) = (x, y, z);
+// x * 4 bytes must be a multiple of 16.  Coordinates outside the grid read
+// zeros.
+__device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map, uint64_t* bar,
+                                             int x, int y, int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ------------------------------------------- shared-memory staged kernel
 // The block's output tile is 32 (x3) x wy (x2) x k (x1) points.  With every
 // |floor(d)| <= H, the stencils of the tile lie in the box of
@@ -495,47 +557,108 @@ k_tile(Dims g, int K, int H, int E1, int E2, int E3, int P3, const float* __rest
     epi.done(acc);
 }
 
+// Box elements [a0, a1) x [b0, b1) x [c0, c1) (plane, row, column of a box
+// with E2 rows of pitch P3 whose element (0, 0, 0) is grid point (o1, o2, o3))
+// loaded from their periodic images, one element per thread at a time.
+template <int E2, int P3>
+__device__ void load_wrapped(float* box, const float* __restrict__ f, const Dims& g, int o1, int o2,
+                             int o3, int a0, int a1, int b0, int b1, int c0, int c1, int tid,
+                             int nthr) {
+    const int na = a1 - a0, nb = b1 - b0, nc = c1 - c0;
+    if (na <= 0 || nb <= 0 || nc <= 0) return;
+    for (int e = tid; e < na * nb * nc; e += nthr) {
+        const int c = c0 + e % nc, r = e / nc;
+        const int b = b0 + r % nb, a = a0 + r / nb;
+        box[(a * E2 + b) * P3 + c] =
+            __ldg(f + (long long)wrap_near(o1 + a, g.n1) * g.n23 +
+                  wrap_near(o2 + b, g.n2) * g.n3 + wrap_near(o3 + c, g.n3));
+    }
+}
+
 // The same kernel with the halo H and the block height WY fixed at compile
 // time: every one of the 64 shared-memory offsets of a point is then an
-// immediate, and only the base address is computed per point.
+// immediate, and only the base address is computed per point.  The box row
+// starts at the 16-byte aligned column o3 = 32 bx - 4, its pitch is 64 words,
+// and columns [3 - H, 38 + H) hold every stencil of the tile.  With a tensor
+// map (use_tma) one thread stages the whole box with a single TMA copy that
+// the block waits for on an mbarrier; the copy reads zeros outside the grid,
+// so a block at a face of the periodic domain then reloads those elements
+// from their periodic images.  Without one, every thread issues 4-byte
+// cp.async copies with the wrap resolved per row.  A block whose wait for the
+// copy gives up (bounded, about a second) writes NaN for its points.
 template <class Epi, int H, int WY>
-__global__ void __launch_bounds__(32 * WY)
-k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict__ d, Epi epi) {
+__global__ void __launch_bounds__(32 * WY, 1024 / (32 * WY))
+k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict__ d, Epi epi,
+             const __grid_constant__ CUtensorMap box_map, int use_tma) {
     constexpr int E2 = WY + 3 + 2 * H;
-    constexpr int E3 = 35 + 2 * H;
-    constexpr int P3 = (E3 + 31) & ~31;
+    constexpr int P3 = 64;
+    constexpr int C0 = 3 - H, C1 = 38 + H;   // columns read by the tile's stencils
+    static_assert(C0 >= 0 && C1 <= P3, "box row");
     constexpr int E23 = E2 * P3;
-    extern __shared__ float box[];   // [E1][E2][P3], E3 columns used
+    extern __shared__ __align__(128) float box[];   // [E1][E2][P3], then the mbarrier
     const int lane = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + lane;
     const int E1 = K + 3 + 2 * H;
     const int i3 = blockIdx.x * 32 + lane;
     const int i2 = blockIdx.y * WY + ty;
     const int i1b = blockIdx.z * K;
     const int o1 = i1b - 1 - H, o2 = blockIdx.y * WY - 1 - H;
-    const int o3 = blockIdx.x * 32 - 1 - H;
+    const int o3 = blockIdx.x * 32 - 4;
     const bool active = i3 < g.n3 && i2 < g.n2;
     const int kend = min(K, g.n1 - i1b);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(box + E1 * E23);
+    const bool tma = use_tma && (smem_u32(box) & 127u) == 0;
+    if (tma) {
+        if (tid == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (tid == 0) {
+            mbar_expect_tx(bar, (unsigned)(sizeof(float) * E1 * E23));
+            tma_load_box(box, &box_map, bar, o3, o2, o1);
+        }
+    }
     Ahead<Epi> ah[2];
     if (active) {
         if (0 < kend) fetch(ah[0], d, g, epi, i1b, i2, i3);
         if (1 < kend) fetch(ah[1], d, g, epi, i1b + 1, i2, i3);
     }
-    {
-        int col[3];
+    bool staged = true;
+    if (tma) {
+        staged = mbar_wait_bounded(bar, 0);
+        if (!staged) mbar_wait_bounded(bar, 0);   // let a late copy land before exit
+        // in-grid index ranges of the box along each axis
+        const int a_lo = min(max(-o1, 0), E1), a_hi = max(min(g.n1 - o1, E1), a_lo);
+        const int b_lo = min(max(-o2, 0), E2), b_hi = max(min(g.n2 - o2, E2), b_lo);
+        const int c_lo = min(max(-o3, C0), C1), c_hi = max(min(g.n3 - o3, C1), c_lo);
+        if (a_lo > 0 || a_hi < E1 || b_lo > 0 || b_hi < E2 || c_lo > C0 || c_hi < C1) {
+            // elements with a coordinate outside the grid, in disjoint parts:
+            // planes outside; rows outside of inside planes; columns outside
+            // of inside rows
+            const int nthr = 32 * WY;
+            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, 0, a_lo, 0, E2, C0, C1, tid, nthr);
+            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_hi, E1, 0, E2, C0, C1, tid, nthr);
+            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_lo, a_hi, 0, b_lo, C0, C1, tid, nthr);
+            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_lo, a_hi, b_hi, E2, C0, C1, tid, nthr);
+            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_lo, a_hi, b_lo, b_hi, C0, c_lo, tid,
+                                 nthr);
+            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_lo, a_hi, b_lo, b_hi, c_hi, C1, tid,
+                                 nthr);
+        }
+    } else {
+        int col[2];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) col[c] = wrap_near(o3 + lane + 32 * c, g.n3);
+        for (int c = 0; c < 2; ++c) col[c] = wrap_near(o3 + C0 + lane + 32 * c, g.n3);
         for (int a = 0; a < E1; ++a) {
             const float* plane = f + (long long)wrap_near(o1 + a, g.n1) * g.n23;
             for (int b = ty; b < E2; b += WY) {
                 const float* src = plane + wrap_near(o2 + b, g.n2) * g.n3;
-                float* dst = box + (a * E2 + b) * P3;
+                float* dst = box + (a * E2 + b) * P3 + C0;
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    if (lane + 32 * c < E3) cp_async4(dst + lane + 32 * c, src + col[c]);
+                for (int c = 0; c < 2; ++c)
+                    if (lane + 32 * c < C1 - C0) cp_async4(dst + lane + 32 * c, src + col[c]);
             }
         }
+        cp_async_wait_all();
     }
-    cp_async_wait_all();
     __syncthreads();
     double acc = 0.0;
     if (active) {
@@ -552,7 +675,7 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
             lagrange4(cur.d3 - fl3, w3);
             const int l1 = min(max(k + H + (int)fl1, 0), E1 - 4);   // i1 + fl1 - 1 - o1
             const int l2 = min(max(r2 + (int)fl2, 0), E2 - 4);
-            const int l3 = min(max(r3 + (int)fl3, 0), E3 - 4);
+            const int l3 = min(max(r3 + (int)fl3, 0), P3 - 4);
             const float* base = box + (l1 * E2 + l2) * P3 + l3;
             const f32x2 w2a = pk(w2[0], w2[1]), w2b = pk(w2[2], w2[3]);
             f32x2 ww3[4];
@@ -577,6 +700,7 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
             val = fmaf(w1[1], r[1], val);
             val = fmaf(w1[2], r[2], val);
             val = fmaf(w1[3], r[3], val);
+            if (!staged) val = __int_as_float(0x7fffffff);
             epi.post(idx0 + k * g.n23, val, cur.pre, acc);
         };
         for (int k = 0; k < kend; k += 2) {
@@ -595,25 +719,69 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
     epi.done(acc);
 }
 
+// The runtime's handle on the driver's tensor-map encoder (null when the
+// driver does not offer it; the staged kernel then copies with cp.async).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor map of the field f (n1 x n2 x n3, x3 fastest) with a box of 64 x E2
+// x E1 elements; false (map unused) unless the grid rows are whole 16-byte
+// units, f is 16-byte aligned and the grid is at least one box large.
+bool box_tensor_map(CUtensorMap* map, const Dims& g, const float* f, int E1, int E2) {
+    std::memset(map, 0, sizeof(*map));
+    if (g.n3 % 4 || g.n3 < 64 || g.n2 < E2 || g.n1 < E1 || E1 > 256 || E2 > 256 ||
+        (reinterpret_cast<uintptr_t>(f) & 15))
+        return false;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dim[3] = {(cuuint64_t)g.n3, (cuuint64_t)g.n2, (cuuint64_t)g.n1};
+    const cuuint64_t stride[2] = {sizeof(float) * (cuuint64_t)g.n3,
+                                  sizeof(float) * (cuuint64_t)g.n23};
+    const cuuint32_t boxd[3] = {64, (cuuint32_t)E2, (cuuint32_t)E1};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(f), dim, stride, boxd,
+               estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
 template <class Epi, int H, int WY>
 cudaError_t run_tile_fixed(const Dims& g, Tile t, const float* f, const float* d,
                            const Epi& epi, cudaStream_t st) {
     constexpr int E2 = WY + 3 + 2 * H;
-    constexpr int P3 = ((35 + 2 * H) + 31) & ~31;
-    const size_t smem = sizeof(float) * (size_t)(t.k + 3 + 2 * H) * E2 * P3;
+    constexpr int P3 = 64;
+    const int E1 = t.k + 3 + 2 * H;
+    // the box, then the 8-byte mbarrier
+    const size_t smem = sizeof(float) * (size_t)E1 * E2 * P3 + 16;
     if (smem > 48 * 1024) {
         const int cap = WY >= 16 ? kMaxBoxFloats16 : kMaxBoxFloats;
         const cudaError_t e = cudaFuncSetAttribute(k_tile_fixed<Epi, H, WY>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   (int)(sizeof(float) * cap));
+                                                   (int)(sizeof(float) * cap + 16));
         if (e != cudaSuccess) return e;
     }
-    k_tile_fixed<Epi, H, WY><<<march_grid(g, t), dim3(32, WY), smem, st>>>(g, t.k, f, d, epi);
+    CUtensorMap map;
+    const int use_tma = t.tma && box_tensor_map(&map, g, f, E1, E2) ? 1 : 0;
+    k_tile_fixed<Epi, H, WY><<<march_grid(g, t), dim3(32, WY), smem, st>>>(g, t.k, f, d, epi, map,
+                                                                            use_tma);
     return cudaGetLastError();
 }
 
 // Tricubic value at displacement (e1, e2, e3) (grid units) of the point of
-// local x1 plane kloc, from a staged box laid out as in k_tile_fixed
+// local x1 plane kloc, from a staged box laid out as in k_departure_tile
 // (H, WY fixed; clamped indices keep every read inside the box).
 template <int H, int WY>
 __device__ __forceinline__ float box_interp(const float* box, int E1, int kloc, int r2, int r3,

@@ -95,6 +95,7 @@ _SIGS = {
     'reg_set_timing': [_P, _I],
     'reg_set_tile': [_P, _I, _I],
     'reg_get_tile': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    'reg_set_staging': [_P, _I],
     'reg_get_timing': [_P, ctypes.POINTER(Timing)],
     'reg_autotune': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_batch_create': [_I, _P, _I, _D, _I, _I, _I, ctypes.POINTER(_P)],
@@ -351,6 +352,11 @@ class Registration:
 
     def set_tile(self, k, wy):
         self._call('reg_set_tile', int(k), int(wy))
+
+    def set_staging(self, tma):
+        """True: stage interpolation boxes with one TMA copy per block where
+        the grid allows; False: per-thread cp.async copies (same results)."""
+        self._call('reg_set_staging', 1 if tma else 0)
 
     def get_tile(self):
         k, wy = ctypes.c_int(), ctypes.c_int()

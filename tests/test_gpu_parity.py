@@ -86,6 +86,26 @@ def test_interpolation_with_large_displacements(reg, shape, nf):
     R.close()
 
 
+@pytest.mark.parametrize('shape,wy', [((20, 24, 68), 8), ((18, 17, 100), 8), ((24, 20, 64), 8),
+                                      ((20, 28, 64), 16)])
+@pytest.mark.parametrize('H', [1, 2, 3])
+def test_interpolation_staged_by_tensor_copy(reg, shape, wy, H):
+    """Displacements below H cells run the staged kernel; with x3 a multiple
+    of 4 and at least 64 and the box no larger than the grid, its box is
+    staged by one TMA copy, and the blocks at the faces of the domain reload
+    the parts outside the grid from their periodic images (x3 ragged against
+    the 32-wide tile in two of the shapes)."""
+    rng = np.random.default_rng(17 + H)
+    f = f32(synth.bandlimited(shape, 5, 19, ncomp=None))
+    d = f32(np.stack([rng.uniform(-(H - 0.05), H - 0.05, shape) for _ in range(3)]))
+    R = reg.Registration(shape, 4, 1e-2)
+    R.set_tile(8, wy)
+    out = host(R.interp(dev(f[None]), dev(d)))[0]
+    exp = oip.interp_at_displacement(f, d)
+    assert np.abs(out - exp).max() < 1e-5 * np.abs(f).max() * 8
+    R.close()
+
+
 def test_interpolation_exact_at_integer_displacements(reg):
     shape = (24, 20, 36)
     rng = np.random.default_rng(3)
@@ -190,6 +210,49 @@ def test_gradient_and_matvec(reg, shape, kind, incompressible, beta, nt, at_vsta
         h = R.hessian_matvec(dev(w))
         assert rel(host(h), P.hessian_matvec(w)) < 1e-4, s
     R.close()
+
+
+def test_gradient_and_matvec_with_tensor_copy_staging(reg):
+    """A grid whose boxes are staged by TMA copies (x3 = 68: a multiple of 4,
+    at least 64, ragged against the 32-wide tile).  beta = 1e-4 and
+    directions of band 3 keep the transported (data) part at about 95 % of
+    H w, so the incremental transports, not the regularisation, decide the
+    comparison."""
+    shape, beta, nt = (20, 24, 68), 1e-4, 4
+    rho_T, rho_R, v = _problem_case(shape, 'H2', False, beta, nt, True)
+    P = opr.Problem(rho_T, rho_R, nt, beta, 'H2', False)
+    g_ref, J_ref = P.gradient(v)
+    R = reg.Registration(shape, nt, beta, 'H2', False)
+    R.set_images(dev(rho_T), dev(rho_R))
+    g, J = R.gradient(dev(v))
+    assert rel(host(g), g_ref) < _gradient_tol(shape, beta, 'H2', v, g_ref)
+    assert abs(J - J_ref) < 1e-5 * abs(J_ref)
+    for s in range(3):
+        w = f32(synth.bandlimited(shape, 3, 1101 + s))
+        h = R.hessian_matvec(dev(w))
+        assert rel(host(h), P.hessian_matvec(w)) < 1e-4, s
+    R.close()
+
+
+@pytest.mark.parametrize('shape,wy', [((18, 16, 100), 8), ((20, 28, 64), 16), ((24, 24, 96), 8)])
+def test_tensor_copy_and_per_thread_staging_agree_bit_for_bit(reg, shape, wy):
+    """The two ways of filling the box put the same values in it, so the
+    gradient, the objective and the Hessian matvec agree exactly."""
+    rho_T, rho_R, v = _problem_case(shape, 'H2', False, 1e-3, 4, True)
+    w = dev(synth.bandlimited(shape, 3, 1201))
+    res = []
+    for tma in (True, False):
+        R = reg.Registration(shape, 4, 1e-3, 'H2', False)
+        R.set_tile(8, wy)
+        R.set_staging(tma)
+        R.set_images(dev(rho_T), dev(rho_R))
+        g, J = R.gradient(dev(v))
+        h = R.hessian_matvec(w)
+        res.append((host(g), J, host(h)))
+        R.close()
+    assert np.array_equal(res[0][0], res[1][0])
+    assert res[0][1] == res[1][1]
+    assert np.array_equal(res[0][2], res[1][2])
 
 
 def test_matvec_before_gradient_is_refused(reg):
