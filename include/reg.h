@@ -355,6 +355,13 @@ int reg_unet_create(int R, int levels, const int* ch, int cin, int cout, reg_une
 int reg_unet_destroy(reg_unet* net);
 const char* reg_unet_last_error(const reg_unet* net);
 int reg_unet_set_stream(reg_unet* net, void* stream);
+/* Tensor-core path of the forward 3x3x3 convolutions.  tcgen05 = 1 (default):
+ * where Co is 16, 32, 64 or 128 and Ci a multiple of 8, a 128-voxel x Co tile
+ * per CTA on tcgen05.mma (BF16 operands in shared memory, FP32 accumulator in
+ * tensor memory); tcgen05 = 0, and every other layer and every gradient: the
+ * warp-level wmma path.  Same inputs and rounding of the operands; the FP32
+ * sums may differ in order.  REG_EINVAL unless tcgen05 is 0 or 1. */
+int reg_unet_set_mma(reg_unet* net, int tcgen05);
 int reg_unet_param_count(const reg_unet* net, size_t* count);
 /* Host arrays of reg_unet_param_count floats.  set_params also zeroes the
  * Adam moments and step count.  Both wait for the stream. */

@@ -35,6 +35,8 @@ struct reg_unet {
     size_t np;
     float *p, *grad, *m, *v;     // FP32 parameters, gradients, Adam moments
     bf16 *wbf, *wtbf;            // bf16 weights [k][ci][co] and transposed [k][co][ci]
+    int tc;                      // forward 3x3x3 convolutions on tcgen05 where they fit (1)
+                                 // or on the wmma path (0)
     long long step;
     // activations (bf16, channels last)
     bf16* xin;
@@ -297,7 +299,11 @@ int conv_fwd(reg_unet* u, const UConv& L, int R, const bf16* x, bf16* out_bf, fl
     a.out_off = out_off;
     a.bias = u->p + L.boff;
     a.relu = relu;
-    U_CK(u, reg::unet::launch_igemm(reg::unet::MODE_FWD, a, u->stream));
+    a.Bt_src = u->wtbf + L.woff;
+    if (u->tc && reg::unet::conv_fwd_tc_ok(a))
+        U_CK(u, reg::unet::launch_conv_fwd_tc(a, u->stream));
+    else
+        U_CK(u, reg::unet::launch_igemm(reg::unet::MODE_FWD, a, u->stream));
     return REG_OK;
 }
 
@@ -477,6 +483,7 @@ int reg_unet_create(int res, int levels, const int* ch, int cin, int cout, reg_u
     if (!u) return REG_ENOMEM;
     u->R = res;
     u->L = levels;
+    u->tc = 1;
     u->cin = cin;
     u->cout = cout;
     for (int l = 0; l < levels; ++l) u->ch[l] = ch[l];
@@ -566,6 +573,12 @@ const char* reg_unet_last_error(const reg_unet* u) { return u ? u->err.c_str() :
 int reg_unet_set_stream(reg_unet* u, void* stream) {
     if (!u) return REG_EINVAL;
     u->stream = (cudaStream_t)stream;
+    return REG_OK;
+}
+
+int reg_unet_set_mma(reg_unet* u, int tcgen05) {
+    if (!u || (tcgen05 != 0 && tcgen05 != 1)) return REG_EINVAL;
+    u->tc = tcgen05;
     return REG_OK;
 }
 

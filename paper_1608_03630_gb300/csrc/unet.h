@@ -27,9 +27,16 @@ struct IgemmArgs {
     float* dX;                    // BWD_DATA output [V][out_stride]
     float* dW;                    // BWD_WEIGHT output [ks^3 Ci][Co] (accumulated)
     int kchunk;                   // BWD_WEIGHT: voxels per block
+    const __nv_bfloat16* Bt_src;  // FWD on tcgen05: wt [ks^3][Co][Ci] (K-major B)
 };
 
 cudaError_t launch_igemm(int mode, const IgemmArgs& a, cudaStream_t st);
+
+// Forward 3x3x3 convolution on the tcgen05 tensor cores (unet_tc.cu): usable
+// when Co is 16, 32, 64 or 128, Ci a multiple of 8, the output BF16 with row
+// stride and channel offset multiples of 8, and every pointer 16-byte aligned.
+bool conv_fwd_tc_ok(const IgemmArgs& a);
+cudaError_t launch_conv_fwd_tc(const IgemmArgs& a, cudaStream_t st);
 
 }  // namespace unet
 }  // namespace reg

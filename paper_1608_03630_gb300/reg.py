@@ -107,6 +107,7 @@ _SIGS = {
     'reg_unet_create': [_I, _I, _P, _I, _I, ctypes.POINTER(_P)],
     'reg_unet_destroy': [_P],
     'reg_unet_set_stream': [_P, _P],
+    'reg_unet_set_mma': [_P, _I],
     'reg_unet_param_count': [_P, ctypes.POINTER(ctypes.c_size_t)],
     'reg_unet_set_params': [_P, _P],
     'reg_unet_get_params': [_P, _P],
@@ -468,6 +469,11 @@ class UNet:
         s = getattr(lib(), name)(self._u, *args)
         if s != 0:
             raise RegError(s, lib().reg_unet_last_error(self._u).decode())
+
+    def set_mma(self, tcgen05):
+        """True: forward 3x3x3 convolutions on tcgen05 where they fit; False:
+        the wmma path for every layer."""
+        self._call('reg_unet_set_mma', 1 if tcgen05 else 0)
 
     def layer_shapes(self):
         """(name, weight shape, bias shape) per layer, in parameter order."""

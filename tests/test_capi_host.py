@@ -75,6 +75,7 @@ def test_null_context_is_rejected(lib):
     assert lib.reg_hessian_matvec(None, None, None) == 1
     assert lib.reg_solve(None, None, None, None) == 1
     assert lib.reg_set_staging(None, 1) == 1
+    assert lib.reg_unet_set_mma(None, 1) == 1
 
 
 def test_unet_and_resample_reject_bad_arguments_before_touching_the_gpu(lib):

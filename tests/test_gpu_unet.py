@@ -119,17 +119,40 @@ def test_unet_forward_matches_oracle(reg, R, ch):
     assert rel(y, want.transpose(3, 0, 1, 2)) < 2e-2
 
 
-def test_unet_forward_full_channels(reg):
+@pytest.mark.parametrize('tcgen05', [True, False])
+def test_unet_forward_full_channels(reg, tcgen05):
     """The four-level 16/32/64/128 network at 32^3 (every GEMM shape of the
-    production network: K from 54 to 5184, N from 3 to 128)."""
+    production network: K from 54 to 5184, N from 3 to 128), with the
+    forward 3x3x3 convolutions on tcgen05 and on the wmma path."""
     ch = (16, 32, 64, 128)
     net = reg.UNet(32, ch)
+    net.set_mma(tcgen05)
     flat, used = make_params(net, seed=5)
     net.set_params(flat)
     x = make_input(32, 2, seed=6)
     y = host(net.forward(dev(x)))
     want, _ = oracle_forward(used, x, ch)
     assert rel(y, want.transpose(3, 0, 1, 2)) < 2e-2
+
+
+@pytest.mark.parametrize('R', [16, 32])
+def test_tcgen05_and_wmma_forward_agree(reg, R):
+    """The forward 3x3x3 convolutions with 16..128 output channels run on
+    tcgen05 (TMEM accumulator) by default and on the wmma path when told;
+    same BF16 operands, FP32 sums in another order: the outputs agree to the
+    BF16 rounding of the activations (the 2-channel first layer and the 1x1
+    head are on the wmma path either way)."""
+    ch = (16, 32, 64, 128) if R == 32 else (16, 32)
+    net = reg.UNet(R, ch)
+    flat, _ = make_params(net, seed=9)
+    net.set_params(flat)
+    x = dev(make_input(R, 2, seed=10))
+    y_tc = host(net.forward(x))
+    net.set_mma(False)
+    y_w = host(net.forward(x))
+    net.set_mma(True)
+    assert np.isfinite(y_tc).all()
+    assert rel(y_tc, y_w) < 1e-2
 
 
 @pytest.mark.parametrize('R,ch', CONFIGS)
