@@ -12,7 +12,7 @@
 // offset) 512 B; one MMA (K = 16) reads K groups 2s and 2s + 1 from the chunk
 // base + 256 s.
 //
-// Pipeline: four stages.  Every thread copies its part of chunk q + 3 with
+// Pipeline: three stages.  Every thread copies its part of chunk q + 2 with
 // 16-byte cp.async copies (8 consecutive channels of one neighbour, zero
 // filled outside the volume) while the tensor core works on chunk q; when a
 // chunk has landed, the threads fence it for the tensor core (async proxy)
@@ -35,7 +35,7 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int TBM = 128;    // voxels per CTA (MMA M)
 constexpr int TBK = 32;     // K elements per chunk (two MMAs of K = 16)
-constexpr int kStages = 4;  // chunks in flight
+constexpr int kStages = 3;  // chunks in flight
 constexpr long long kWaitCycles = 2000000000LL;
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -180,6 +180,20 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(IgemmArgs a) {
     const bf16* Wt = a.Bt_src;   // [27][Co][Ci]
     constexpr uint32_t idesc = instr_desc(BN);
 
+    // Chunks are issued in order 0, 1, 2, ..., so the gathered index
+    // j = k Ci + c of every 16-byte piece advances without divisions: the A
+    // pieces of a row are consecutive (8 channels each; Ci is a multiple of
+    // 8), and each B piece of the thread moves by one chunk (TBK) per issue.
+    int a_k = 0, a_c = 0;
+    int a_nb = row_ok ? nbr(g, pz, py, px, 0) : -1;
+    constexpr int NPB = (BN * KG + 127) / 128;
+    int b_k[NPB], b_c[NPB];
+#pragma unroll
+    for (int i = 0; i < NPB; ++i) {
+        const int j = ((tid + 128 * i) / BN) * 8;
+        b_k[i] = j / Ci;
+        b_c[i] = j - b_k[i] * Ci;
+    }
     // chunk q into stage q % kStages: A row tid (KG groups of 8 channels of
     // one neighbour), B rows n (consecutive threads, consecutive n)
     auto issue = [&](int q) {
@@ -187,31 +201,38 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(IgemmArgs a) {
         uint8_t* Bs = As + A_BYTES;
 #pragma unroll
         for (int kg = 0; kg < KG; ++kg) {
-            const int j0 = q * TBK + kg * 8;
             const bf16* src = X;
             uint32_t bytes = 0;
-            if (row_ok && j0 < K) {
-                const int k = j0 / Ci, c = j0 - k * Ci;
-                const int nb = nbr(g, pz, py, px, k);
-                if (nb >= 0) {
-                    src = X + (long long)nb * Ci + c;
-                    bytes = 16;
-                }
-            }
-            cp16(As + core_off(tid, kg), src, bytes);
-        }
-#pragma unroll
-        for (int e = tid; e < BN * KG; e += 128) {
-            const int n = e % BN, kg = e / BN;
-            const int j0 = q * TBK + kg * 8;
-            const bf16* src = Wt;
-            uint32_t bytes = 0;
-            if (j0 < K) {
-                const int k = j0 / Ci, c = j0 - k * Ci;
-                src = Wt + ((long long)k * BN + n) * Ci + c;
+            if (a_k < 27 && a_nb >= 0) {
+                src = X + (long long)a_nb * Ci + a_c;
                 bytes = 16;
             }
-            cp16(Bs + core_off(n, kg), src, bytes);
+            cp16(As + core_off(tid, kg), src, bytes);
+            a_c += 8;
+            if (a_c == Ci) {
+                a_c = 0;
+                ++a_k;
+                a_nb = (row_ok && a_k < 27) ? nbr(g, pz, py, px, a_k) : -1;
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NPB; ++i) {
+            const int e = tid + 128 * i;
+            if (e < BN * KG) {
+                const int n = e % BN, kg = e / BN;
+                const bf16* src = Wt;
+                uint32_t bytes = 0;
+                if (b_k[i] < 27) {
+                    src = Wt + ((long long)b_k[i] * BN + n) * Ci + b_c[i];
+                    bytes = 16;
+                }
+                cp16(Bs + core_off(n, kg), src, bytes);
+                b_c[i] += TBK;
+                while (b_c[i] >= Ci) {
+                    b_c[i] -= Ci;
+                    ++b_k[i];
+                }
+            }
         }
     };
 
