@@ -316,13 +316,10 @@ cudaError_t launch_bn(const IgemmArgs& a, cudaStream_t st) {
     constexpr int STAGE = TBM * TBK * 2 + BN * TBK * 2;
     // stages, barriers + TMEM slot, alignment slack
     const int smem = kStages * STAGE + 8 * kStages + 16 + 1024;
-    static bool attr = false;
-    if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(
-            k_conv_fwd_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // set once per process (thread-safe static initialisation)
+    static const cudaError_t attr = cudaFuncSetAttribute(
+        k_conv_fwd_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (attr != cudaSuccess) return attr;
     const int grid = (a.g.V + TBM - 1) / TBM;
     k_conv_fwd_tc<BN><<<grid, 128, smem, st>>>(a);
     return cudaGetLastError();
