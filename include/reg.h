@@ -272,6 +272,23 @@ int reg_jacobian_det(reg_ctx* ctx, const float* u, float* det);
 int reg_set_tile(reg_ctx* ctx, int k, int wy);
 int reg_get_tile(const reg_ctx* ctx, int* k, int* wy);
 
+/* Host-side fault injection, for tests of the error paths (no GPU fault is
+ * involved).  Arms one process-wide injection that fires once, at the
+ * (after + 1)-th matching event, and then disarms:
+ *  REG_INJECT_ALLOC       a device allocation of reg_create fails as if
+ *                         cudaMalloc had: reg_create frees what it holds and
+ *                         returns REG_ENOMEM with *out = NULL;
+ *  REG_INJECT_CUFFT_PLAN  a cuFFT plan of reg_create fails: REG_ECUFFT;
+ *  REG_INJECT_NAN_IMAGE   the next reg_set_images writes a NaN into rho_T
+ *                         (in every stored copy) after its copies, so the
+ *                         next objective or gradient returns REG_ENONFINITE
+ *                         and the context stays usable;
+ *  REG_INJECT_NONE        disarm.
+ * REG_EINVAL on an unknown kind or after < 0. */
+enum { REG_INJECT_NONE = 0, REG_INJECT_ALLOC = 1, REG_INJECT_CUFFT_PLAN = 2,
+       REG_INJECT_NAN_IMAGE = 3 };
+int reg_debug_inject(int what, int after);
+
 /* How the staged interpolation kernels fill their shared-memory box.
  * tma = 1 (default): one TMA tensor copy per block (cp.async.bulk.tensor,
  * completion on an mbarrier) wherever x3 is a multiple of 4 and the grid is

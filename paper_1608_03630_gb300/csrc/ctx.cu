@@ -1,5 +1,6 @@
 // Context management, timing, the internal operations of the hot path and
 // their C-ABI entry points.
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -496,6 +497,18 @@ static void free_ctx(reg_ctx* c) {
     delete c;
 }
 
+// Host-side fault injection (reg_debug_inject): the armed kind fires at its
+// (after + 1)-th event and disarms.
+static std::atomic<int> g_inject_what{REG_INJECT_NONE};
+static std::atomic<int> g_inject_left{0};
+
+static bool inject_fires(int what) {
+    if (g_inject_what.load() != what) return false;
+    if (g_inject_left.fetch_sub(1) > 0) return false;
+    g_inject_what.store(REG_INJECT_NONE);
+    return true;
+}
+
 static int alloc_grad_hist(reg_ctx* c) {
     const size_t cnt = (size_t)(c->nt + 1) * 3 * c->g.n;
     if (c->grad_hist) { cudaFree(c->grad_hist); c->grad_hist = nullptr; }
@@ -559,7 +572,7 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
         {(void**)&c->dabs, sizeof(unsigned int) * 4},
     };
     for (auto& a : allocs) {
-        if (cudaMalloc(a.p, a.bytes) != cudaSuccess) {
+        if (inject_fires(REG_INJECT_ALLOC) || cudaMalloc(a.p, a.bytes) != cudaSuccess) {
             cudaGetLastError();
             free_ctx(c);
             return fail(nullptr, REG_ENOMEM, "device allocation failed in reg_create");
@@ -577,18 +590,26 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
     cudaMemset(c->dsc, 0, sizeof(double) * 32);
     int dims[3] = {n1, n2, n3};
     cufftResult r;
-    r = cufftPlanMany(&c->r2c1, 3, dims, nullptr, 1, (int)n, nullptr, 1, (int)nc, CUFFT_R2C, 1);
+    r = inject_fires(REG_INJECT_CUFFT_PLAN)
+                ? CUFFT_ALLOC_FAILED
+                : cufftPlanMany(&c->r2c1, 3, dims, nullptr, 1, (int)n, nullptr, 1, (int)nc, CUFFT_R2C, 1);
     c->plans[0] = (r == CUFFT_SUCCESS);
     if (r == CUFFT_SUCCESS) {
-        r = cufftPlanMany(&c->c2r1, 3, dims, nullptr, 1, (int)nc, nullptr, 1, (int)n, CUFFT_C2R, 1);
+        r = inject_fires(REG_INJECT_CUFFT_PLAN)
+                ? CUFFT_ALLOC_FAILED
+                : cufftPlanMany(&c->c2r1, 3, dims, nullptr, 1, (int)nc, nullptr, 1, (int)n, CUFFT_C2R, 1);
         c->plans[1] = (r == CUFFT_SUCCESS);
     }
     if (r == CUFFT_SUCCESS) {
-        r = cufftPlanMany(&c->r2c3, 3, dims, nullptr, 1, (int)n, nullptr, 1, (int)nc, CUFFT_R2C, 3);
+        r = inject_fires(REG_INJECT_CUFFT_PLAN)
+                ? CUFFT_ALLOC_FAILED
+                : cufftPlanMany(&c->r2c3, 3, dims, nullptr, 1, (int)n, nullptr, 1, (int)nc, CUFFT_R2C, 3);
         c->plans[2] = (r == CUFFT_SUCCESS);
     }
     if (r == CUFFT_SUCCESS) {
-        r = cufftPlanMany(&c->c2r3, 3, dims, nullptr, 1, (int)nc, nullptr, 1, (int)n, CUFFT_C2R, 3);
+        r = inject_fires(REG_INJECT_CUFFT_PLAN)
+                ? CUFFT_ALLOC_FAILED
+                : cufftPlanMany(&c->c2r3, 3, dims, nullptr, 1, (int)nc, nullptr, 1, (int)n, CUFFT_C2R, 3);
         c->plans[3] = (r == CUFFT_SUCCESS);
     }
     if (r != CUFFT_SUCCESS) {
@@ -684,6 +705,11 @@ int reg_set_images(reg_ctx* c, const float* rho_T, const float* rho_R, int presm
         REG_CK(c, launch_to_bf16(c->rho_T, c->img_bf, n, c->stream));
         REG_CK(c, launch_to_bf16(c->rho_R, c->img_bf + n, n, c->stream));
         REG_CK(c, launch_from_bf16(c->img_bf + n, c->rho_R, n, c->stream));
+    }
+    if (inject_fires(REG_INJECT_NAN_IMAGE)) {
+        // all-ones bits: a NaN in FP32 and in bfloat16
+        REG_CK(c, cudaMemsetAsync(c->rho_T, 0xFF, sizeof(float), c->stream));
+        if (c->img_bf) REG_CK(c, cudaMemsetAsync(c->img_bf, 0xFF, sizeof(__nv_bfloat16), c->stream));
     }
     c->have_images = true;
     return REG_OK;
@@ -880,6 +906,14 @@ int reg_set_tile(reg_ctx* c, int k, int wy) {
                     "tile: k must be a multiple of 4 in [4, 64], wy in {1,2,4,8,16}");
     c->tile.k = k;
     c->tile.wy = wy;
+    return REG_OK;
+}
+
+int reg_debug_inject(int what, int after) {
+    if (what < REG_INJECT_NONE || what > REG_INJECT_NAN_IMAGE || after < 0) return REG_EINVAL;
+    g_inject_what.store(REG_INJECT_NONE);
+    g_inject_left.store(after);
+    g_inject_what.store(what);
     return REG_OK;
 }
 

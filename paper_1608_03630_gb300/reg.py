@@ -96,6 +96,7 @@ _SIGS = {
     'reg_set_tile': [_P, _I, _I],
     'reg_get_tile': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_set_staging': [_P, _I],
+    'reg_debug_inject': [_I, _I],
     'reg_get_timing': [_P, ctypes.POINTER(Timing)],
     'reg_autotune': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_batch_create': [_I, _P, _I, _D, _I, _I, _I, ctypes.POINTER(_P)],
@@ -146,6 +147,19 @@ def status_name(s):
         return lib().reg_status_string(s).decode()
     except Exception:
         return 'status %d' % s
+
+
+INJECT = {'none': 0, 'alloc': 1, 'cufft_plan': 2, 'nan_image': 3}
+
+
+def debug_inject(what, after=0):
+    """Arm one host-side fault injection (reg_debug_inject): 'alloc' or
+    'cufft_plan' fails the (after + 1)-th device allocation or cuFFT plan of
+    reg_create; 'nan_image' puts a NaN into the next reg_set_images; 'none'
+    disarms."""
+    s = lib().reg_debug_inject(INJECT[what], int(after))
+    if s != 0:
+        raise RegError(s, 'reg_debug_inject(%r, %r)' % (what, after))
 
 
 def _ptr(t, shape=None, what='tensor'):

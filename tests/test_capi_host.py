@@ -78,6 +78,16 @@ def test_null_context_is_rejected(lib):
     assert lib.reg_unet_set_mma(None, 1) == 1
 
 
+def test_fault_injection_arguments(lib):
+    """Arming and disarming the host-side injection touches no GPU."""
+    assert lib.reg_debug_inject(4, 0) == 1
+    assert lib.reg_debug_inject(-1, 0) == 1
+    assert lib.reg_debug_inject(1, -1) == 1
+    for what in (1, 2, 3):
+        assert lib.reg_debug_inject(what, 2) == 0
+    assert lib.reg_debug_inject(0, 0) == 0
+
+
 def test_unet_and_resample_reject_bad_arguments_before_touching_the_gpu(lib):
     out = ctypes.c_void_p()
     ch = (ctypes.c_int * 4)(16, 32, 64, 128)
