@@ -124,6 +124,24 @@ int reg_gradient(reg_ctx* ctx, const float* v, float* g, double* J);
  * vt, Hvt [3n], may not overlap.  REG_ENOTREADY before any reg_gradient. */
 int reg_hessian_matvec(reg_ctx* ctx, const float* vt, float* Hvt);
 
+/* The gradient and the Hessian matvec in the solver's own representation
+ * (Sec. III-B1: every field is a trigonometric polynomial): normalised
+ * half-spectrum Fourier coefficients, f_hat = F f / n with f(x) =
+ * sum_k f_hat(k) exp(i k.x), stored as interleaved complex pairs
+ * [3][n1][n2][n3/2 + 1][2] floats (k1, k2 in FFT order, k3 = 0 .. n3/2).
+ * beta A and P act on the coefficients exactly (diagonal products), so the
+ * FP32 rounding of the FFTs is not amplified by beta |k|^4 in the result as
+ * it is through the physical-space calls above.  The transports run on the
+ * physical field C2R(v_hat).
+ * reg_gradient_spectral: g_hat = beta A v_hat + P F(b) / n (Eq. gradient),
+ * *J (host, may be NULL) = J[v]; makes v the linearisation point like
+ * reg_gradient.  reg_hessian_matvec_spectral: Hvt_hat = beta A vt_hat +
+ * P F(b~) / n at that point (Eq. hessian; REG_ENOTREADY before a gradient).
+ * Inputs and outputs may not overlap; REG_ENOMEM if the solver's vectors
+ * cannot be allocated. */
+int reg_gradient_spectral(reg_ctx* ctx, const float* v_hat, float* g_hat, double* J);
+int reg_hessian_matvec_spectral(reg_ctx* ctx, const float* vt_hat, float* Hvt_hat);
+
 /* Spectral preconditioner z = F^-1[ M(k) P(k) F r ], M = 1/(beta A(k)) for
  * k != 0 and M(0) = 1/beta (Sec. III-A: the inverse regularisation
  * operator).  r, z [3n]; r == z (in place) is allowed. */
@@ -204,9 +222,10 @@ int reg_state_transport(reg_ctx* ctx, const float* rho0, const float* d_fwd,
                         float* rho_hist);
 
 /* The forward state transport of reg_state_transport, for callers that
- * cannot allocate device memory (code running during CUDA graph capture,
- * inside another library's callback, on a fixed memory pool, or in a loop
- * where a possibly synchronising cudaMalloc is not acceptable).  The paper
+ * cannot allocate device memory (code inside another library's callback
+ * that must not touch the allocator, on a fixed memory pool that must not
+ * grow, or in a loop where a possibly synchronising cudaMalloc is not
+ * acceptable).  The paper
  * has no counterpart: it is a property of this library's interface only.
  * No context: grid n1 x n2 x n3 (n <= 2^22 points, else REG_EINVAL), nt
  * steps (1..64) with the points d_fwd [3n]; rho0 [n] -> rho1 [n] = rho(t_nt)
@@ -216,7 +235,9 @@ int reg_state_transport(reg_ctx* ctx, const float* rho0, const float* d_fwd,
  * intermediate level lives in a fixed 16 MiB static device array that every
  * GPU loading the library keeps until exit.  The first call on a device
  * looks up that array's address (cudaGetSymbolAddress) with the device
- * current, so make the first call on each device before any stream capture.
+ * current, so make the first call on each device before any stream capture;
+ * a failed lookup returns REG_ECUDA, is not cached, and is retried by the
+ * next call.  The tensors must be on the current device.
  * All calls share the array: calls whose GPU work overlaps (other streams,
  * other threads) race on it; serialise them.  Every element of the array is
  * written before it is read within a call.  REG_ECUDA on a launch or

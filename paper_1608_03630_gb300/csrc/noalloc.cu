@@ -1,11 +1,11 @@
 // Forward state transport for callers that cannot allocate device memory.
 //
-// Some callers of this library may not call cudaMalloc: code that runs while a
-// CUDA graph is being captured (allocation is forbidden there), code inside
-// another library's callback, programs whose device memory is owned by a
-// fixed pool or arena that must not grow, and latency-critical loops where an
-// allocation (which may synchronise the device) is not acceptable.  This file
-// gives them reg_state_transport_noalloc: the same state transport as
+// Some callers of this library may not call cudaMalloc: code inside another
+// library's callback that must not touch the allocator, programs whose device
+// memory is owned by a fixed pool or arena that must not grow, and
+// latency-critical loops where an allocation (which may synchronise the
+// device) is not acceptable.  This file gives them
+// reg_state_transport_noalloc: the same state transport as
 // reg_state_transport, with no context and no allocation.  Its one
 // intermediate time level lives in the file-scope array g_level below, a fixed
 // 16 MiB that every GPU loading the library keeps until the process exits.
@@ -24,18 +24,22 @@ __device__ __align__(256) float g_level[kMaxPoints];
 
 // Device address of g_level per device.  In host code the name g_level is a
 // host-side stand-in, not a device address: the address must come from
-// cudaGetSymbolAddress, once per device, with that device current.
+// cudaGetSymbolAddress, once per device, with that device current.  Only a
+// successful lookup is kept, so a failed one (for instance while the device
+// was not yet usable) is retried by the next call.
 float* g_level_addr[kMaxDevices];
-std::once_flag g_once[kMaxDevices];
-cudaError_t g_setup_err[kMaxDevices];
+std::mutex g_level_mutex;
 
-float* level_address(int dev, cudaError_t* err) {
-    std::call_once(g_once[dev], [dev]() {
+float* level_address(int dev) {
+    std::lock_guard<std::mutex> lk(g_level_mutex);
+    if (!g_level_addr[dev]) {
         void* p = nullptr;
-        g_setup_err[dev] = cudaGetSymbolAddress(&p, g_level);
-        g_level_addr[dev] = (g_setup_err[dev] == cudaSuccess) ? static_cast<float*>(p) : nullptr;
-    });
-    *err = g_setup_err[dev];
+        if (cudaGetSymbolAddress(&p, g_level) == cudaSuccess) {
+            g_level_addr[dev] = static_cast<float*>(p);
+        } else {
+            cudaGetLastError();   // leave no error behind for the caller
+        }
+    }
     return g_level_addr[dev];
 }
 
@@ -51,8 +55,7 @@ extern "C" int reg_state_transport_noalloc(int n1, int n2, int n3, int nt, const
         cudaGetLastError();
         return REG_ECUDA;
     }
-    cudaError_t err;
-    float* level = level_address(dev, &err);
+    float* level = level_address(dev);
     if (!level) return REG_ECUDA;
     const reg::Dims g = reg::make_dims(n1, n2, n3);
     const reg::Tile t{8, 4};
@@ -64,8 +67,8 @@ extern "C" int reg_state_transport_noalloc(int n1, int n2, int n3, int nt, const
     const float* in = rho0;
     for (int j = 1; j <= nt; ++j) {
         float* out = ((nt - j) % 2 == 0) ? rho1 : level;
-        err = reg::launch_state_step(g, t, in, d_fwd, out, nullptr, nullptr, nullptr, 0, nullptr,
-                                     st);
+        const cudaError_t err = reg::launch_state_step(g, t, in, d_fwd, out, nullptr, nullptr,
+                                                       nullptr, 0, nullptr, st);
         if (err != cudaSuccess) return REG_ECUDA;
         in = out;
     }

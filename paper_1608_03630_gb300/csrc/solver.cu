@@ -520,6 +520,56 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
     return s;
 }
 
+int reg_gradient_spectral(reg_ctx* c, const float* v_hat, float* g_hat, double* J) {
+    if (!c) return REG_EINVAL;
+    if (c->dead) return fail(c, REG_ECUDA, "context unusable after a CUDA error");
+    if (!v_hat || !g_hat || ((uintptr_t)v_hat & 15u) || ((uintptr_t)g_hat & 15u))
+        return fail(c, REG_EINVAL, "v_hat / g_hat: null or not 16-byte aligned");
+    if (v_hat == g_hat) return fail(c, REG_EINVAL, "v_hat and g_hat overlap");
+    if (!c->have_images) return fail(c, REG_ENOTREADY, "reg_set_images first");
+    REG_TRY(ensure_solver(c));
+    const int nb = blas_blocks();
+    const float2* vh = reinterpret_cast<const float2*>(v_hat);
+    float* v = c->sv[R_V];
+    REG_TRY(to_physical(c, vh, v));
+    REG_TRY(op_linearize(c, v));
+    REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_gradient(c->g, vh, c->spec[1], reinterpret_cast<float2*>(g_hat),
+                                     c->beta, c->kind, c->incompressible, c->partials, nb,
+                                     c->stream));
+    }
+    REG_TRY(finalize_to(c, 1, nb, 0.5 * c->beta * kTwoPi3, SC_JREG));
+    if (J) {
+        REG_TRY(read_scalars(c, SC_JMIS, 2));
+        *J = c->hsc[SC_JMIS] + c->hsc[SC_JREG];
+        if (!std::isfinite(*J)) return fail(c, REG_ENONFINITE, "objective is not finite");
+    }
+    return REG_OK;
+}
+
+int reg_hessian_matvec_spectral(reg_ctx* c, const float* vt_hat, float* Hvt_hat) {
+    if (!c) return REG_EINVAL;
+    if (c->dead) return fail(c, REG_ECUDA, "context unusable after a CUDA error");
+    if (!vt_hat || !Hvt_hat || ((uintptr_t)vt_hat & 15u) || ((uintptr_t)Hvt_hat & 15u))
+        return fail(c, REG_EINVAL, "vt_hat / Hvt_hat: null or not 16-byte aligned");
+    if (vt_hat == Hvt_hat) return fail(c, REG_EINVAL, "vt_hat and Hvt_hat overlap");
+    if (!c->have_lin) return fail(c, REG_ENOTREADY, "reg_gradient must come first");
+    REG_TRY(ensure_solver(c));
+    const int nb = blas_blocks();
+    const float2* ph = reinterpret_cast<const float2*>(vt_hat);
+    float* p = c->sv[R_P];
+    REG_TRY(to_physical(c, ph, p));
+    REG_TRY(op_matvec_transport(c, p, nullptr, 0));
+    REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
+    Phase pq(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
+    REG_CK(c, launch_sp_gradient(c->g, ph, c->spec[1], reinterpret_cast<float2*>(Hvt_hat),
+                                 c->beta, c->kind, c->incompressible, c->partials, nb,
+                                 c->stream));
+    return REG_OK;
+}
+
 int reg_solve_host(reg_ctx* c, const float* rho_T_host, const float* rho_R_host, int presmooth,
                    float* v_host_inout, const reg_solve_opts* opts, reg_solve_stats* stats) {
     if (!c) return REG_EINVAL;

@@ -79,6 +79,8 @@ _SIGS = {
     'reg_gradient': [_P, _P, _P, ctypes.POINTER(_D)],
     'reg_hessian_matvec': [_P, _P, _P],
     'reg_precond_apply': [_P, _P, _P],
+    'reg_gradient_spectral': [_P, _P, _P, ctypes.POINTER(_D)],
+    'reg_hessian_matvec_spectral': [_P, _P, _P],
     'reg_solve_opts_default': [ctypes.POINTER(SolveOpts)],
     'reg_solve': [_P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)],
     'reg_solve_host': [_P, _P, _P, _I, _P, ctypes.POINTER(SolveOpts),
@@ -174,15 +176,22 @@ def _ptr(t, shape=None, what='tensor'):
 
 def state_transport_noalloc(rho0, d_fwd, rho1, nt, stream=None):
     """reg_state_transport_noalloc: rho1 = rho(t_nt) from rho0 with the
-    points d_fwd, with no allocation and no context (see include/reg.h)."""
+    points d_fwd, with no allocation and no context (see include/reg.h).
+    The three tensors must be on one device; the call runs with that device
+    current, on `stream` (default: that device's current stream)."""
     shape = tuple(rho0.shape)
-    if stream is None:
-        stream = torch.cuda.current_stream()
-    s = lib().reg_state_transport_noalloc(shape[0], shape[1], shape[2], int(nt),
-                                          _ptr(rho0, shape, 'rho0'),
-                                          _ptr(d_fwd, (3,) + shape, 'd_fwd'),
-                                          _ptr(rho1, shape, 'rho1'),
-                                          ctypes.c_void_p(stream.cuda_stream))
+    devs = {t.device for t in (rho0, d_fwd, rho1)}
+    if len(devs) != 1:
+        raise ValueError('rho0, d_fwd and rho1 must be on one device, got %s' % sorted(map(str, devs)))
+    device = rho0.device
+    with torch.cuda.device(device):
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        s = lib().reg_state_transport_noalloc(shape[0], shape[1], shape[2], int(nt),
+                                              _ptr(rho0, shape, 'rho0'),
+                                              _ptr(d_fwd, (3,) + shape, 'd_fwd'),
+                                              _ptr(rho1, shape, 'rho1'),
+                                              ctypes.c_void_p(stream.cuda_stream))
     if s != 0:
         raise RegError(s, 'reg_state_transport_noalloc failed')
 
@@ -262,6 +271,36 @@ class Registration:
     def hessian_matvec(self, vt, out=None):
         o = self._new(self.vshape) if out is None else out
         self._call('reg_hessian_matvec', _ptr(vt, self.vshape, 'vt'), _ptr(o, self.vshape, 'Hvt'))
+        return o
+
+    @property
+    def sshape(self):
+        """Shape of a vector field's normalised half spectrum as a complex64
+        tensor: (3, n1, n2, n3 // 2 + 1)."""
+        return (3, self.shape[0], self.shape[1], self.shape[2] // 2 + 1)
+
+    def _cptr(self, t, what):
+        if not isinstance(t, torch.Tensor) or t.device.type != 'cuda' or \
+                t.dtype != torch.complex64 or not t.is_contiguous() or \
+                tuple(t.shape) != self.sshape:
+            raise ValueError('%s must be a contiguous CUDA complex64 tensor of shape %s'
+                             % (what, self.sshape))
+        return ctypes.c_void_p(t.data_ptr())
+
+    def gradient_spectral(self, v_hat, out=None):
+        """(g_hat, J) from normalised half-spectrum coefficients v_hat
+        (complex64 (3, n1, n2, n3 // 2 + 1)); reg_gradient_spectral."""
+        g = torch.empty(self.sshape, device='cuda', dtype=torch.complex64) if out is None else out
+        J = ctypes.c_double()
+        self._call('reg_gradient_spectral', self._cptr(v_hat, 'v_hat'), self._cptr(g, 'g_hat'),
+                   ctypes.byref(J))
+        return g, J.value
+
+    def hessian_matvec_spectral(self, vt_hat, out=None):
+        """Hvt_hat from the coefficients vt_hat; reg_hessian_matvec_spectral."""
+        o = torch.empty(self.sshape, device='cuda', dtype=torch.complex64) if out is None else out
+        self._call('reg_hessian_matvec_spectral', self._cptr(vt_hat, 'vt_hat'),
+                   self._cptr(o, 'Hvt_hat'))
         return o
 
     def precond(self, r, out=None):

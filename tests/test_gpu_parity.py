@@ -312,6 +312,31 @@ def test_three_gauss_newton_steps_match_the_oracle(reg):
     R.close()
 
 
+def test_incompressible_solve_matches_the_oracle(reg):
+    """The incompressible variant (Leray projection, H1-div, beta = 1e-3) of
+    the 32^3 sinusoid problem solved to ||g|| <= 1e-2 ||g_0|| on both sides:
+    the same number of Newton steps (+-1), PCG iterations within 10 %, the
+    same objective and velocity, and a divergence-free result."""
+    shape, nt, beta = (32, 32, 32), 4, 1e-3
+    rho_T, rho_R, _ = [f32(a) for a in synth.sinusoid_problem(shape, 0.5)]
+    P = opr.Problem(rho_T, rho_R, nt, beta, 'H1DIV', True)
+    v_ref, st_ref = oso.gauss_newton(P, np.zeros((3,) + shape), gtol=1e-2, max_gn=50)
+    R = reg.Registration(shape, nt, beta, 'H1DIV', True)
+    R.set_images(dev(rho_T), dev(rho_R))
+    v = torch.zeros((3,) + shape, device='cuda')
+    status, st = R.solve(v, gtol=1e-2, max_gn=50)
+    R.close()
+    assert status == 0 and st['gnorm_rel'] <= 1e-2
+    assert abs(st['gn_iters'] - st_ref['gn_iters']) <= 1, (st['gn_iters'], st_ref['gn_iters'])
+    assert abs(st['pcg_iters'] - st_ref['pcg_iters']) <= max(1, 0.1 * st_ref['pcg_iters'])
+    assert abs(st['J'] - st_ref['J']) < 1e-3 * st_ref['J']
+    vg = host(v)
+    assert rel(vg, v_ref) < 1e-2
+    div = osp.divergence(vg)
+    gv = np.stack([osp.gradient(vg[c]) for c in range(3)])
+    assert np.linalg.norm(div) < 1e-5 * np.linalg.norm(gv)
+
+
 def test_graph_and_eager_pcg_agree(reg):
     """Plain launches, one graph per PCG iteration, and the device-controlled
     while-loop graph run the same kernels in the same order: same counts,

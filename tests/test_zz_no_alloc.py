@@ -1,12 +1,15 @@
 """The allocation-free state transport (reg_state_transport_noalloc).
 
-For callers that cannot allocate device memory (graph capture, callbacks,
-fixed memory pools), the library offers a context-free forward state
-transport whose intermediate level lives in a static device array.  Its
-output must equal the final level of the ordinary, context-based
-reg_state_transport on the same inputs, on two calls in a row (the second
-call reuses the static array left over from the first).  This file is named
-so that pytest collects it last.
+Some callers cannot allocate device memory: code inside another library's
+callback that must not touch the allocator, programs on a fixed memory pool
+that must not grow, and latency-critical loops where a cudaMalloc (which may
+synchronise the device) is not acceptable.  For them the library offers a
+context-free forward state transport whose intermediate level lives in a
+static device array.  Its output must equal the final level of the
+ordinary, context-based reg_state_transport on the same inputs, on two calls
+in a row (the second call reuses the static array left over from the
+first), and a call after the first must leave the device's free memory
+unchanged.  This file is named so that pytest collects it last.
 """
 
 import numpy as np
@@ -44,8 +47,14 @@ def test_noalloc_transport_matches_the_context_path_twice(reg, shape, nt):
         d_fwd, _ = R.departure(v)
         expected = R.state_transport(rho0, d_fwd)[nt]
         out = torch.full(shape, float('nan'), device='cuda')
-        reg.state_transport_noalloc(rho0, d_fwd, out, nt)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
         torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        reg.state_transport_noalloc(rho0, d_fwd, out, nt, stream=side)
+        torch.cuda.synchronize()
+        if call > 0:   # the first call may load the library's device code
+            assert torch.cuda.mem_get_info()[0] == free_before, call
         err = float((out - expected).norm() / expected.norm())
         assert err < 1e-5, (call, err)
     R.close()
