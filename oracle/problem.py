@@ -5,6 +5,8 @@ Test infrastructure.  Follows Sec. II-B ("Formulation"):
   J[v] = 1/2 ||rho(1) - rho_R||^2 + beta/2 <v, A v>          Eq. (varopt)
   g(v) = beta A v + P b,  b = int_0^1 lam grad rho dt         Eq. (gradient)
   H v~ = beta A v~ + P b~,  b~ = int_0^1 lam~ grad rho dt     Eq. (hessian), GN
+  full Newton: lam~ from Eq. (inc-adj) with div(lam v~) kept and
+  b~ = int_0^1 (lam~ grad rho + lam grad rho~) dt              Eq. (hessian)
 
 For the compressible problem P -> I (Sec. II-B, after Eq. (gradient)) and the
 adjoint carries the source lam div v; for the incompressible problem v is kept
@@ -30,16 +32,19 @@ class Problem:
 
     rho_T, rho_R: (N1, N2, N3) arrays.  kind: 'H2', 'H1' or 'H1DIV'.
     presmooth: apply the one-cell Gaussian to both images first (Sec. III-B1).
+    newton: hessian_matvec applies the full Newton Hessian (Eq. (hessian) with
+    the terms in lam) instead of the Gauss-Newton one.
     """
 
     def __init__(self, rho_T, rho_R, nt, beta, kind='H2', incompressible=False,
-                 presmooth=False):
+                 presmooth=False, newton=False):
         self.shape = rho_T.shape
         self.nt = int(nt)
         self.dt = 1.0 / self.nt
         self.beta = float(beta)
         self.kind = kind
         self.incompressible = bool(incompressible)
+        self.newton = bool(newton)   # full Newton Hessian instead of Gauss-Newton
         rt = np.array(rho_T, dtype=np.float64)
         rr = np.array(rho_R, dtype=np.float64)
         if presmooth:
@@ -97,19 +102,30 @@ class Problem:
         lin = self.lin
         return _tr.incremental_state_solve(vt, lin['grad_rho'], lin['d_fwd'], self.nt)
 
-    def hessian_matvec(self, vt):
-        """GN Hessian matvec at the last gradient's v.
+    def hessian_matvec(self, vt, full=None):
+        """Hessian matvec at the last gradient's v.
 
         rho~ from Eq. (inc-state) (Algorithm 2), lam~(1) = -rho~(1)
-        (Eq. (inc-adj-fc)), lam~ from Eq. (inc-adj) without the div(lam v~)
-        term (Gauss-Newton), b~ = int lam~ grad rho dt, H v~ = beta A v~ + P b~.
+        (Eq. (inc-adj-fc)), H v~ = beta A v~ + P b~.  Gauss-Newton (the
+        default, full=False): lam~ from Eq. (inc-adj) without the div(lam v~)
+        term and b~ = int lam~ grad rho dt (Sec. II-B drops both terms that
+        involve lam).  Full Newton (full=True, or the problem's `newton`):
+        lam~ with the source div(lam v~), where lam is the adjoint of the
+        linearisation point at the time levels, and b~ = int (lam~ grad rho +
+        lam grad rho~) dt, grad rho~ spectral on every level.
         """
         if self.lin is None:
             raise RuntimeError('hessian_matvec before gradient')
+        full = self.newton if full is None else full
         lin = self.lin
         rt = self.incremental_state(vt)
-        lt = _tr.adjoint_solve(-rt[-1], lin['d_adj'], lin['divv'], self.nt)
+        src = None
+        if full:
+            src = [_sp.divergence(lin['lam'][j] * vt) for j in range(self.nt + 1)]
+        lt = _tr.adjoint_solve(-rt[-1], lin['d_adj'], lin['divv'], self.nt, src)
         bt = _tr.time_integral(lt, lin['grad_rho'])
+        if full:
+            bt = bt + _tr.time_integral(lin['lam'], [_sp.gradient(r) for r in rt])
         return self.beta * self.regularisation(vt) + self.project(bt)
 
     def precond(self, r):

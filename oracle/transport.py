@@ -54,7 +54,7 @@ def state_solve(rho0, d_fwd, nt):
     return rho
 
 
-def adjoint_step(nu, d_adj, divv, dt):
+def adjoint_step(nu, d_adj, divv, dt, src_old=None, src_new=None):
     """One tau-step of -d_t lam - div(v lam) = 0 (Eq. (adjoint)).
 
     In tau = 1 - t this is d_tau lam + (-v) . grad lam = lam div v: transport
@@ -67,29 +67,43 @@ def adjoint_step(nu, d_adj, divv, dt):
     div v interpolated at X (an interpolation "for the f terms that depend on
     the semi-Lagrangian point").  Then nu_* = nu_0 + dt f_0,
     f_* = nu_* div v(x), lam_new = nu_0 + dt/2 (f_0 + f_*).
+
+    src_old, src_new: an additional known source s(x, tau) at the level the
+    step starts from and at the level it reaches (the full-Newton incremental
+    adjoint of Eq. (inc-adj) carries s = div(lam v~)); f gains s, with
+    s_old interpolated at X like every term that belongs to the
+    semi-Lagrangian point and s_new taken at the grid point.
     """
     nu0 = _interp.interp_at_displacement(nu, d_adj)
-    if divv is None:
-        return nu0
-    f0 = nu0 * _interp.interp_at_displacement(divv, d_adj)
+    f0 = np.zeros_like(nu0) if divv is None else nu0 * _interp.interp_at_displacement(divv, d_adj)
+    if src_old is not None:
+        f0 = f0 + _interp.interp_at_displacement(src_old, d_adj)
     nu_star = nu0 + dt * f0
-    f_star = nu_star * divv
+    f_star = np.zeros_like(nu0) if divv is None else nu_star * divv
+    if src_new is not None:
+        f_star = f_star + src_new
     return nu0 + (dt / 2.0) * (f0 + f_star)
 
 
-def adjoint_solve(lam_final, d_adj, divv, nt):
-    """Adjoint (or Gauss-Newton incremental adjoint) backward in time.
+def adjoint_solve(lam_final, d_adj, divv, nt, src=None):
+    """Adjoint (or incremental adjoint) backward in time.
 
     lam_final is the value at t = 1.  Returns [lam(t_0), ..., lam(t_nt)].
     Used for Eq. (adjoint) with lam(1) = rho_R - rho(1), and for Eq. (inc-adj)
     with lam~(1) = -rho~(1): the Gauss-Newton Hessian drops div(lam v~), so
-    the incremental adjoint is the same equation (Sec. II-B).
+    the incremental adjoint is the same equation (Sec. II-B).  For the full
+    Newton Hessian, src = [s(t_0), ..., s(t_nt)] is the known source
+    s = div(lam v~) of Eq. (inc-adj) on the time levels: in tau the equation
+    reads d_tau lam~ + (-v) . grad lam~ = lam~ div v + div(lam v~).
     """
     dt = 1.0 / nt
     lam = [None] * (nt + 1)
     lam[nt] = np.array(lam_final, dtype=np.float64)
     for j in range(nt - 1, -1, -1):
-        lam[j] = adjoint_step(lam[j + 1], d_adj, divv, dt)
+        if src is None:
+            lam[j] = adjoint_step(lam[j + 1], d_adj, divv, dt)
+        else:
+            lam[j] = adjoint_step(lam[j + 1], d_adj, divv, dt, src[j + 1], src[j])
     return lam
 
 
