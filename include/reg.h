@@ -119,8 +119,9 @@ int reg_objective(reg_ctx* ctx, const float* v, double* J);
  * history rho(t_j) and its spectral gradients.  v and g may not overlap. */
 int reg_gradient(reg_ctx* ctx, const float* v, float* g, double* J);
 
-/* Gauss-Newton Hessian matvec Hvt = beta A vt + P b~ (Eq. hessian, without
- * the lambda terms), b~ = int lam~ grad rho dt, at the last reg_gradient's v.
+/* Hessian matvec Hvt = beta A vt + P b~ at the last reg_gradient's v
+ * (Eq. hessian): Gauss-Newton by default (without the lambda terms,
+ * b~ = int lam~ grad rho dt), full Newton after reg_set_hessian.
  * vt, Hvt [3n], may not overlap.  REG_ENOTREADY before any reg_gradient. */
 int reg_hessian_matvec(reg_ctx* ctx, const float* vt, float* Hvt);
 
@@ -141,6 +142,22 @@ int reg_hessian_matvec(reg_ctx* ctx, const float* vt, float* Hvt);
  * cannot be allocated. */
 int reg_gradient_spectral(reg_ctx* ctx, const float* v_hat, float* g_hat, double* J);
 int reg_hessian_matvec_spectral(reg_ctx* ctx, const float* vt_hat, float* Hvt_hat);
+
+/* Which Hessian reg_hessian_matvec(_spectral) and reg_solve apply (Eq. hessian):
+ *  REG_HESS_GAUSS_NEWTON (default) drops the two terms in lam, the paper's
+ *      choice for its runs (Sec. IV-A3);
+ *  REG_HESS_FULL_NEWTON keeps them: the incremental adjoint carries the
+ *      source div(lam v~) (Eq. inc-adj), advanced like every source term by
+ *      Eq. sml-advection, and b~ = int (lam~ grad rho + lam grad rho~) dt
+ *      with spectral grad rho~ on every time level.  Allocates (nt + 1) n +
+ *      nt n floats for the adjoint levels of the linearisation point and
+ *      the incremental-state levels (REG_ENOMEM if that fails).  Far from a
+ *      minimiser this Hessian can be indefinite; PCG then stops at the
+ *      negative curvature (reg_solve_stats.negative_curvature).
+ * Invalidates the linearisation point (the next reg_gradient keeps the
+ * adjoint levels).  REG_EINVAL on another value. */
+enum { REG_HESS_GAUSS_NEWTON = 0, REG_HESS_FULL_NEWTON = 1 };
+int reg_set_hessian(reg_ctx* ctx, int hessian);
 
 /* Spectral preconditioner z = F^-1[ M(k) P(k) F r ], M = 1/(beta A(k)) for
  * k != 0 and M(0) = 1/beta (Sec. III-A: the inverse regularisation

@@ -176,11 +176,25 @@ cudaError_t launch_state_step(const Dims& g, Tile t, const float* rho_in, const 
 // step): b starts from w_first lam_first grad_first instead of its stored
 // value.  dotp != nullptr (last step): per-block FP64 partials of <dotp, b>
 // into partials[0 .. *nblk_out).
+// add != nullptr: lam_out = c(x) I[lam_in](x + d) + add(x) (the known-source
+// part of a full-Newton incremental adjoint step, from launch_source_step).
 cudaError_t launch_adjoint_acc(const Dims& g, Tile t, const float* lam_in, const float* d,
                                const float* c, float* lam_out, const float* grad, float w,
                                float* b, const float* lam_first, const float* grad_first,
                                float w_first, const float* dotp, double* partials,
-                               int max_partials, int* nblk_out, cudaStream_t st);
+                               int max_partials, int* nblk_out, cudaStream_t st,
+                               const float* add = nullptr);
+// Known-source part of an adjoint tau-step: out = dt/2 (1 + dt dv(x))
+// I[s_old](x + d) + dt/2 s_new(x), dv = divv (null: divergence free, dv = 0).
+cudaError_t launch_source_step(const Dims& g, Tile t, const float* s_old, const float* d,
+                               const float* divv, const float* s_new, float dt, float* out,
+                               cudaStream_t st);
+// rho~_j = u_j + dt/2 v~ . grad rho_j from the carried incremental state u_j.
+cudaError_t launch_inc_state_level(const Dims& g, const float* u, const float* vt,
+                                   const float* grad_j, float dt, float* out, cudaStream_t st);
+// b[3][n] += w lam[n] grad_f[3][n].
+cudaError_t launch_acc_scaled_grad(const Dims& g, const float* lam, const float* grad_f, float w,
+                                   float* b, cudaStream_t st);
 // c(x) = 1 + dt/2 (dX + dv + dt dX dv), dv = div v(x), dX = I[div v](x + d_adj).
 cudaError_t launch_adjoint_coef(const Dims& g, Tile t, const float* divv, const float* d_adj,
                                 float dt, float* c, cudaStream_t st);

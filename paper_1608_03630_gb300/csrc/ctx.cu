@@ -303,34 +303,58 @@ int op_objective(reg_ctx* c, const float* v, int slot_J) {
     return reg_energy(c, c->spec[0]);
 }
 
-// Adjoint (or incremental adjoint) from lam_hist[nt] down to lam_hist[0].
-// Adjoint (or incremental adjoint) solve from lam_hist[nt] = lam(1), fused
+// Adjoint (or incremental adjoint) solve from levels[nt] = lam(1), fused
 // with the trapezoid time integral of Eq. gradient / Eq. inc-control: every
-// tau-step stores lam_j (except the last) and accumulates
+// tau-step stores lam_j (except the last, unless keep_all) and accumulates
 // b = sum_j w_j lam_j grad rho_j into out at its output points; with dotp,
-// dsc[slot] = <dotp, b>_h.
-static int adjoint_solve(reg_ctx* c, int phase, float* out, const float* dotp, int slot) {
+// dsc[slot] = <dotp, b>_h.  src_vt (full Newton incremental adjoint,
+// Eq. inc-adj): the equation carries the known source s_j = div(lam_j v~)
+// with lam_j the adjoint levels of the linearisation point (lam_lin); each
+// step then adds dt/2 (1 + dt dv) I[s_{j+1}](X) + dt/2 s_j(x).
+static int adjoint_solve(reg_ctx* c, int phase, float* levels, bool keep_all,
+                         const float* src_vt, float* out, const float* dotp, int slot) {
     const long long n = c->g.n;
     const int nt = c->nt;
     const bool comp = !c->incompressible;
     const float dt = 1.f / (float)nt;
+    float* sbuf[2] = {reinterpret_cast<float*>(c->buf[0]),
+                      reinterpret_cast<float*>(c->buf[0]) + n};
+    float* add = reinterpret_cast<float*>(c->buf[1]);
+    // s_j = div(lam_j v~) into sbuf[j & 1]
+    auto source_level = [&](int j) -> int {
+        {
+            Phase p(c, phase, 28.0 * n);
+            REG_CK(c, launch_mul_fields(c->lam_lin + j * n, src_vt, c->tmp3, n, c->stream));
+        }
+        return op_div(c, c->tmp3, sbuf[j & 1]);
+    };
+    if (src_vt) REG_TRY(source_level(nt));
     int nb = 0;
     for (int j = nt - 1; j >= 0; --j) {
         const bool first = (j == nt - 1), last = (j == 0);
         const float w = last ? 0.5f * dt : dt;
+        if (src_vt) {
+            REG_TRY(source_level(j));
+            Phase p(c, phase, (comp ? 24.0 : 20.0) * n);
+            REG_CK(c, launch_source_step(c->g, tile_with(c, c->halo_adj), sbuf[(j + 1) & 1],
+                                         c->d_adj, comp ? c->divv : nullptr, sbuf[j & 1], dt, add,
+                                         c->stream));
+        }
         // X 12, lam 4, c 4, lam_j 4 (not after the last step); grad_j 12; b
         // written 12 and read 12 (first step: lam(1) 4 and grad rho(1) 12
-        // instead); dotp 12
-        double bytes = (comp ? 24.0 : 20.0) - (last ? 4.0 : 0.0) + 24.0 +
-                       (first ? 16.0 : 12.0) + (last && dotp ? 12.0 : 0.0);
+        // instead); dotp 12; the source part 4
+        const bool store = !last || keep_all;
+        double bytes = (comp ? 20.0 : 16.0) + (store ? 4.0 : 0.0) + 24.0 +
+                       (first ? 16.0 : 12.0) + (last && dotp ? 12.0 : 0.0) +
+                       (src_vt ? 4.0 : 0.0);
         Phase p(c, phase, bytes * n);
-        REG_CK(c, launch_adjoint_acc(c->g, tile_with(c, c->halo_adj), c->lam_hist + (j + 1) * n,
+        REG_CK(c, launch_adjoint_acc(c->g, tile_with(c, c->halo_adj), levels + (j + 1) * n,
                                      c->d_adj, comp ? c->coef : nullptr,
-                                     last ? nullptr : c->lam_hist + j * n, grad_level(c, j), w,
-                                     out, first ? c->lam_hist + nt * n : nullptr,
+                                     store ? levels + j * n : nullptr, grad_level(c, j), w,
+                                     out, first ? levels + nt * n : nullptr,
                                      first ? grad_level(c, nt) : nullptr, 0.5f * dt,
                                      last ? dotp : nullptr, c->partials, c->npartials, &nb,
-                                     c->stream));
+                                     c->stream, src_vt ? add : nullptr));
     }
     if (dotp) {
         Phase p(c, REG_PH_BLAS, 0.0);
@@ -374,7 +398,15 @@ int op_linearize(reg_ctx* c, const float* v, bool state_ready) {
         float* gj = c->grad_hist + (long long)j * 3 * n;
         REG_TRY(op_grad(c, c->rho_hist + j * n, gj));
     }
-    REG_TRY(adjoint_solve(c, REG_PH_ADJOINT, c->bacc, nullptr, 0));
+    if (c->hessian == REG_HESS_FULL_NEWTON) {
+        // the full Newton matvec needs every adjoint level of this point
+        REG_CK(c, cudaMemcpyAsync(c->lam_lin + nt * n, c->lam_hist + nt * n, sizeof(float) * n,
+                                  cudaMemcpyDeviceToDevice, c->stream));
+        REG_TRY(adjoint_solve(c, REG_PH_ADJOINT, c->lam_lin, true, nullptr, c->bacc, nullptr, 0));
+    } else {
+        REG_TRY(adjoint_solve(c, REG_PH_ADJOINT, c->lam_hist, false, nullptr, c->bacc, nullptr,
+                              0));
+    }
     c->have_lin = true;
     return REG_OK;
 }
@@ -403,19 +435,45 @@ int op_matvec_transport(reg_ctx* c, const float* vt, const float* dotp, int slot
     const int nt = c->nt;
     const float dt = (float)(1.0 / nt);
     const double gb = 12.0;
+    const bool full = c->hessian == REG_HESS_FULL_NEWTON;
+    // Gauss-Newton: the carried incremental state u_j in two ping-pong
+    // levels; full Newton: every level u_0 .. u_{nt-1} (for grad rho~_j)
     float* u[2] = {reinterpret_cast<float*>(c->buf[0]), reinterpret_cast<float*>(c->buf[1])};
+    auto level = [&](int j) { return full ? c->rt_hist + j * n : u[j & 1]; };
     {
         Phase p(c, REG_PH_INCSTATE, (16.0 + gb) * n);
-        REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), dt, u[0], c->stream));
+        REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), dt, level(0), c->stream));
     }
     for (int j = 0; j < nt; ++j) {
         const bool fin = (j == nt - 1);
         Phase p(c, REG_PH_INCSTATE, (32.0 + gb) * n);
-        REG_CK(c, launch_incstate_step(g, tile_with(c, c->halo_fwd), u[j & 1], c->d_fwd, vt,
+        REG_CK(c, launch_incstate_step(g, tile_with(c, c->halo_fwd), level(j), c->d_fwd, vt,
                                        grad_level(c, j + 1), dt, fin ? 1 : 0,
-                                       fin ? c->lam_hist + nt * n : u[(j + 1) & 1], c->stream));
+                                       fin ? c->lam_hist + nt * n : level(j + 1), c->stream));
     }
-    return adjoint_solve(c, REG_PH_INCADJ, c->bacc, dotp, slot);
+    if (!full) return adjoint_solve(c, REG_PH_INCADJ, c->lam_hist, false, nullptr, c->bacc, dotp,
+                                    slot);
+    // full Newton (Eq. inc-adj with div(lam v~); b~ += int lam grad rho~ dt)
+    REG_TRY(adjoint_solve(c, REG_PH_INCADJ, c->lam_hist, false, vt, c->bacc, nullptr, 0));
+    float* rt = reinterpret_cast<float*>(c->buf[0]);
+    for (int j = 1; j <= nt; ++j) {
+        const float w = (j == nt) ? 0.5f * dt : dt;
+        const float* f = rt;
+        float wj = w;
+        if (j < nt) {
+            Phase p(c, REG_PH_INCADJ, 20.0 * n);
+            REG_CK(c, launch_inc_state_level(g, level(j), vt, grad_level(c, j), dt, rt,
+                                             c->stream));
+        } else {
+            f = c->lam_hist + nt * n;   // rho~(1) = -lam~(1)
+            wj = -w;
+        }
+        REG_TRY(op_grad(c, f, c->tmp3));
+        Phase p(c, REG_PH_INCADJ, 28.0 * n);
+        REG_CK(c, launch_acc_scaled_grad(g, c->lam_lin + j * n, c->tmp3, wj, c->bacc, c->stream));
+    }
+    if (dotp) REG_TRY(op_inner(c, dotp, c->bacc, 3 * n, slot));
+    return REG_OK;
 }
 
 int op_matvec(reg_ctx* c, const float* vt, float* out) {
@@ -481,7 +539,8 @@ static void free_ctx(reg_ctx* c) {
         if (c->plans[i]) cufftDestroy(i == 0 ? c->r2c1 : i == 1 ? c->c2r1 : i == 2 ? c->r2c3 : c->c2r3);
     void* ptrs[] = {c->rho_T, c->rho_R, c->img_bf, c->d_fwd, c->d_adj, c->divv, c->rho_hist,
                     c->grad_hist, c->lam_hist, c->coef, c->buf[0], c->buf[1],
-                    c->bacc, c->tmp3, c->spec[0], c->spec[1], c->partials, c->dsc, c->dabs};
+                    c->bacc, c->tmp3, c->spec[0], c->spec[1], c->partials, c->dsc, c->dabs,
+                    c->lam_lin, c->rt_hist};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i)
@@ -672,6 +731,28 @@ int reg_set_precision(reg_ctx* c, int precision) {
             return fail(c, REG_ENOMEM, "cannot allocate bf16 images");
         }
     }
+    return REG_OK;
+}
+
+int reg_set_hessian(reg_ctx* c, int hessian) {
+    CHECK_CTX(c);
+    if (hessian != REG_HESS_GAUSS_NEWTON && hessian != REG_HESS_FULL_NEWTON)
+        return fail(c, REG_EINVAL, "hessian must be REG_HESS_GAUSS_NEWTON or REG_HESS_FULL_NEWTON");
+    if (hessian == c->hessian) return REG_OK;
+    REG_CK(c, cudaStreamSynchronize(c->stream));
+    if (hessian == REG_HESS_FULL_NEWTON && !c->lam_lin) {
+        const size_t n = (size_t)c->g.n;
+        if (cudaMalloc(&c->lam_lin, sizeof(float) * (c->nt + 1) * n) != cudaSuccess ||
+            cudaMalloc(&c->rt_hist, sizeof(float) * c->nt * n) != cudaSuccess) {
+            cudaGetLastError();
+            if (c->lam_lin) cudaFree(c->lam_lin);
+            if (c->rt_hist) cudaFree(c->rt_hist);
+            c->lam_lin = c->rt_hist = nullptr;
+            return fail(c, REG_ENOMEM, "cannot allocate the full Newton levels");
+        }
+    }
+    c->hessian = hessian;
+    c->have_lin = false;   // the adjoint levels are kept only by the next gradient
     return REG_OK;
 }
 

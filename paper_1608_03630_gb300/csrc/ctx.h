@@ -51,13 +51,21 @@ struct reg_ctx {
     double* hsc;         // pinned host mirror [32]
     double pshift;       // shift of the solver's spectral preconditioner (reg_solve)
     // the device-controlled PCG graph, reused while the kernels it captured
-    // stay the same: key = (halo_fwd, halo_adj, tile k, tile wy), pshift
+    // stay the same: key = (halo_fwd, halo_adj, tile k, tile wy, hessian),
+    // the preconditioner shift and beta
     cudaGraphExec_t pcg_exec;
-    int pcg_key[4];
-    double pcg_key_shift;
+    int pcg_key[5];
+    double pcg_key_shift, pcg_key_beta;
     reg::Tile tile;      // tile of the interpolation kernels (k, wy)
     int halo_fwd, halo_adj;   // ceil(max |X - x|) of d_fwd / d_adj (-1: unknown)
     unsigned int* dabs;  // [2] device scratch for max |d| (float bits)
+
+    // Hessian: REG_HESS_GAUSS_NEWTON (default) or REG_HESS_FULL_NEWTON; the
+    // full Newton matvec keeps the adjoint levels of the linearisation point
+    // and every level of the incremental state (allocated when selected)
+    int hessian;
+    float* lam_lin;      // [(nt+1) n] lam(t_j) at the linearisation point
+    float* rt_hist;      // [nt n] carried incremental state u_j, j < nt
 
     // solver vectors: real [3n] each, spectral [3 nc] each
     float* sv[4];

@@ -192,9 +192,9 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
     if (use_graph >= 2 && !c->timing && verbose <= 1) {
         // reuse the captured loop while its kernels and launch shapes are
         // unchanged (they depend on the halos and the tile only)
-        const int key[4] = {c->halo_fwd, c->halo_adj, c->tile.k, c->tile.wy};
+        const int key[5] = {c->halo_fwd, c->halo_adj, c->tile.k, c->tile.wy, c->hessian};
         if (c->pcg_exec && (memcmp(key, c->pcg_key, sizeof key) != 0 ||
-                            c->pcg_key_shift != c->pshift)) {
+                            c->pcg_key_shift != c->pshift || c->pcg_key_beta != c->beta)) {
             cudaGraphExecDestroy(c->pcg_exec);
             c->pcg_exec = nullptr;
         }
@@ -202,6 +202,7 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
             c->pcg_exec = build_pcg_loop(c);
             memcpy(c->pcg_key, key, sizeof key);
             c->pcg_key_shift = c->pshift;
+            c->pcg_key_beta = c->beta;
         }
         cudaGraphExec_t loop = c->pcg_exec;
         if (loop) {

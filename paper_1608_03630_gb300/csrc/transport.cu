@@ -233,8 +233,12 @@ struct EpiStateFinal {       // out = val; lam = rho_R - val; sum (val - rho_R)^
 // null after the last one) and b at the output point gains w lam_j grad_j.
 // init (first step): b starts from w_first lam_first grad_first at the point
 // (the level the solve starts from) instead of its stored value.  dotp (last
-// step): per-block FP64 partial sums of <dotp, b>.
-struct EpiAdjAcc {
+// step): per-block FP64 partial sums of <dotp, b>.  kAdd: lam_j = c(x) val +
+// add(x), the known-source part of the step (full Newton incremental
+// adjoint); a separate instantiation, so the Gauss-Newton path loads nothing
+// more.
+template <bool kAdd>
+struct EpiAdjAccT {
     float* out;
     const float* c;          // may be null (c = 1)
     const float* grad;       // grad rho_j [3n]
@@ -246,7 +250,8 @@ struct EpiAdjAcc {
     float w_first;
     const float* dotp;       // last step only (else null)
     double* partials;
-    struct Pre { float c, g0, g1, g2, b0, b1, b2; };
+    const float* add;        // kAdd only: [n] added to lam_j
+    struct Pre { float c, g0, g1, g2, b0, b1, b2, a; };
     __device__ Pre pre(int idx) const {
         Pre p;
         p.c = c ? __ldg(c + idx) : 1.f;
@@ -263,10 +268,11 @@ struct EpiAdjAcc {
             p.b1 = b[n + idx];
             p.b2 = b[2 * n + idx];
         }
+        p.a = kAdd ? __ldg(add + idx) : 0.f;
         return p;
     }
     __device__ void post(int idx, float val, const Pre& p, double& acc) const {
-        const float lam = p.c * val;
+        const float lam = kAdd ? fmaf(p.c, val, p.a) : p.c * val;
         if (out) out[idx] = lam;
         const float l = w * lam;
         const float b0 = fmaf(l, p.g0, p.b0), b1 = fmaf(l, p.g1, p.b1), b2 = fmaf(l, p.g2, p.b2);
@@ -282,6 +288,28 @@ struct EpiAdjAcc {
         if (threadIdx.x == 0 && threadIdx.y == 0)
             partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
     }
+};
+using EpiAdjAcc = EpiAdjAccT<false>;
+
+// Known-source part of an adjoint tau-step (Eq. sml-advection with a source
+// s(x, t) that does not depend on the transported field): the step reaches
+// lam_new = c(x) I[lam_old](X) + dt/2 (1 + dt dv(x)) I[s_old](X) + dt/2 s_new(x)
+// (dv = div v; 0 when divergence free).  This epilogue writes the last two
+// terms, val = I[s_old](X).
+struct EpiSrcAdd {
+    float* out;
+    const float* divv;       // may be null
+    const float* s_new;
+    float dt;
+    struct Pre { float dv, s; };
+    __device__ Pre pre(int idx) const {
+        return {divv ? __ldg(divv + idx) : 0.f, __ldg(s_new + idx)};
+    }
+    __device__ void post(int idx, float val, const Pre& p, double&) const {
+        const float h = 0.5f * dt;
+        out[idx] = fmaf(h * fmaf(dt, p.dv, 1.f), val, h * p.s);
+    }
+    __device__ void done(double) const {}
 };
 
 struct EpiCoef {             // c = 1 + dt/2 (dX + dv + dt dX dv), val = dX
@@ -968,6 +996,31 @@ k_incstate_init(Dims g, const float* __restrict__ vt, const float* __restrict__ 
 }
 
 
+// rho~_j = u_j - dt/2 f_j = u_j + dt/2 v~ . grad rho_j (the incremental state
+// from the carried u_j = rho~_j + dt/2 f_j).
+__global__ void __launch_bounds__(kThreads)
+k_inc_state_level(Dims g, const float* __restrict__ u, const float* __restrict__ vt,
+                  const float* __restrict__ gj, float dt, float* __restrict__ out) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;
+    if (idx >= g.n) return;
+    const long long n = g.n;
+    const float vg = vt[idx] * ld(gj, idx) + vt[n + idx] * ld(gj, n + idx) +
+                     vt[2 * n + idx] * ld(gj, 2 * n + idx);
+    out[idx] = fmaf(0.5f * dt, vg, u[idx]);
+}
+
+// b += w lam grad_f (3 components): one term of int lam grad rho~ dt.
+__global__ void __launch_bounds__(kThreads)
+k_acc_scaled_grad(Dims g, const float* __restrict__ lam, const float* __restrict__ gf, float w,
+                  float* __restrict__ b) {
+    const int idx = blockIdx.x * kThreads + threadIdx.x;
+    if (idx >= g.n) return;
+    const long long n = g.n;
+    const float l = w * lam[idx];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) b[c * n + idx] = fmaf(l, gf[c * n + idx], b[c * n + idx]);
+}
+
 __global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
                           long long count) {
     long long i = (long long)blockIdx.x * kThreads + threadIdx.x;
@@ -1046,14 +1099,38 @@ cudaError_t launch_adjoint_acc(const Dims& g, Tile t, const float* lam_in, const
                                const float* c, float* lam_out, const float* grad, float w,
                                float* b, const float* lam_first, const float* grad_first,
                                float w_first, const float* dotp, double* partials,
-                               int max_partials, int* nblk_out, cudaStream_t st) {
+                               int max_partials, int* nblk_out, cudaStream_t st,
+                               const float* add) {
     const int nb = march_blocks(g, t);
     if (dotp && nb > max_partials) return cudaErrorInvalidValue;
     if (nblk_out) *nblk_out = nb;
+    if (add)
+        return run_march(g, t, lam_in, d,
+                         EpiAdjAccT<true>{lam_out, c, grad, b, g.n, w, lam_first, grad_first,
+                                          w_first, dotp, partials, add},
+                         st);
     return run_march(g, t, lam_in, d,
                      EpiAdjAcc{lam_out, c, grad, b, g.n, w, lam_first, grad_first, w_first, dotp,
-                               partials},
+                               partials, nullptr},
                      st);
+}
+
+cudaError_t launch_source_step(const Dims& g, Tile t, const float* s_old, const float* d,
+                               const float* divv, const float* s_new, float dt, float* out,
+                               cudaStream_t st) {
+    return run_march(g, t, s_old, d, EpiSrcAdd{out, divv, s_new, dt}, st);
+}
+
+cudaError_t launch_inc_state_level(const Dims& g, const float* u, const float* vt,
+                                   const float* grad_j, float dt, float* out, cudaStream_t st) {
+    k_inc_state_level<<<nblocks(g.n), kThreads, 0, st>>>(g, u, vt, grad_j, dt, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_acc_scaled_grad(const Dims& g, const float* lam, const float* grad_f, float w,
+                                   float* b, cudaStream_t st) {
+    k_acc_scaled_grad<<<nblocks(g.n), kThreads, 0, st>>>(g, lam, grad_f, w, b);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint_coef(const Dims& g, Tile t, const float* divv, const float* d_adj,

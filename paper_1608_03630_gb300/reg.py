@@ -74,6 +74,7 @@ _SIGS = {
     'reg_destroy': [_P],
     'reg_set_stream': [_P, _P],
     'reg_set_precision': [_P, _I],
+    'reg_set_hessian': [_P, _I],
     'reg_set_images': [_P, _P, _P, _I],
     'reg_objective': [_P, _P, ctypes.POINTER(_D)],
     'reg_gradient': [_P, _P, _P, ctypes.POINTER(_D)],
@@ -252,6 +253,11 @@ class Registration:
         return torch.empty(shape, device='cuda', dtype=torch.float32)
 
     # -- API --------------------------------------------------------------
+    def set_hessian(self, full_newton):
+        """True: full Newton Hessian (Eq. hessian with the lam terms);
+        False: Gauss-Newton (the default)."""
+        self._call('reg_set_hessian', 1 if full_newton else 0)
+
     def set_images(self, rho_T, rho_R, presmooth=False):
         self._call('reg_set_images', _ptr(rho_T, self.shape, 'rho_T'),
                    _ptr(rho_R, self.shape, 'rho_R'), 1 if presmooth else 0)
