@@ -493,6 +493,62 @@ def batched_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def beta_sweep(args):
+    """Sensitivity of the solver's work to beta, the shape of the paper's
+    Table 5 (Hessian matvecs of four Newton iterations growing as beta
+    falls, Sec. IV-C), on the 256^3 phantom (nt = 8, H2, FP32) instead of the
+    brain images: per beta, (a) four Newton iterations from v = 0 (the
+    table's protocol), (b) the solve to ||g|| <= 1e-2 ||g_0||, and (c) the
+    same solve with parameter continuation from beta = 1e-1 (factor 10).
+    Time to solution by CUDA events on the library stream."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1608_03630_gb300 import reg
+    n = args.sweep_n
+    shape = (n, n, n)
+    rho_T, rho_R = make_inputs(shape)
+    stream = torch.cuda.Stream()
+    rows = []
+    with torch.cuda.stream(stream):
+        dT = torch.from_numpy(rho_T).cuda()
+        dR = torch.from_numpy(rho_R).cuda()
+        v = torch.zeros((3,) + shape, device='cuda')
+        R = reg.Registration(shape, NT, 1e-1, KIND, False, stream=stream)
+        R.set_images(dT, dR, presmooth=True)
+
+        def timed(**opts):
+            v.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s, st = R.solve(v, **opts)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            return {'status': s, 'time_s': e0.elapsed_time(e1) / 1e3, 'gn_iters': st['gn_iters'],
+                    'matvecs': st['matvecs'], 'gnorm_rel': st['gnorm_rel'],
+                    'mismatch_rel': st['mismatch_rel'], 'stages': st['stages'],
+                    'negative_curvature': st['negative_curvature']}
+
+        timed(gtol=1e-2)   # warm-up: plans, graphs
+        for beta in args.betas:
+            R.set_beta(beta)
+            row = {'beta': beta,
+                   'newton4': timed(gtol=0.0, max_gn=4),
+                   'gtol': timed(gtol=1e-2)}
+            if beta < 1e-1:
+                row['continuation'] = timed(gtol=1e-2, beta_start=1e-1, beta_factor=10.0)
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr, flush=True)
+        R.close()
+    base = rows[0]['newton4']['matvecs']
+    line = {'metric': 'Hessian matvecs vs beta (four Newton iterations; solve to gtol)',
+            'workload': 'phantom %d^3 nt=%d H2 fp32, betas %s' % (n, NT, list(args.betas)),
+            'rows': rows,
+            'newton4_matvecs_relative': [r['newton4']['matvecs'] / max(1, base) for r in rows]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -503,7 +559,10 @@ def main():
     ap.add_argument('--init', default='learned', choices=['learned', 'zero'],
                     help='initial velocity: the trained U-Net prediction or v = 0')
     ap.add_argument('--no-cpu-baseline', action='store_true')
-    ap.add_argument('--workload', default='phantom256', choices=['phantom256', 'batched'])
+    ap.add_argument('--workload', default='phantom256',
+                    choices=['phantom256', 'batched', 'beta_sweep'])
+    ap.add_argument('--sweep-n', type=int, default=256)
+    ap.add_argument('--betas', type=float, nargs='+', default=[1e-1, 1e-2, 1e-3, 1e-4, 1e-5])
     ap.add_argument('--pairs', type=int, default=48)
     ap.add_argument('--profile-matvec', type=int, default=0, metavar='N',
                     help='run one gradient and two matvecs at N^3 (nt = 4) for ncu, then exit')
@@ -512,6 +571,8 @@ def main():
         profile_matvec(args.profile_matvec, 4, 2, args.precision)
     elif args.workload == 'batched' and args.impl != 'reference':
         batched_bench(args)
+    elif args.workload == 'beta_sweep' and args.impl != 'reference':
+        beta_sweep(args)
     elif args.impl == 'reference':
         cpu_reference(args)
     else:

@@ -192,6 +192,15 @@ typedef struct {
     double precond_shift; /* >= 0: PCG preconditioner M = 1/(beta A + shift);
                              0 is the paper's inverse regularisation
                              operator (Sec. III-A)                       (0) */
+    double beta_start;    /* > the context's beta: parameter continuation on
+                             beta (Sec. III-A): Gauss-Newton solves at
+                             beta_start, beta_start / beta_factor, ...
+                             down to the context's beta, each from the
+                             last one's velocity, every stage stopped at
+                             ||g|| <= gtol ||g_0|| with ||g_0|| of the first
+                             stage (at v = 0 independent of beta); 0 or
+                             <= beta: one solve at the context's beta     (0) */
+    double beta_factor;   /* continuation divisor per stage, > 1          (10) */
 } reg_solve_opts;
 
 typedef struct {
@@ -200,7 +209,14 @@ typedef struct {
     int negative_curvature;   /* PCG steps stopped by p.Hp <= 0 */
     double J0, J, gnorm0, gnorm, gnorm_rel, mismatch_rel;
     double ms_total;          /* wall time of the solve (host clock) */
+    int stages;               /* continuation stages run (1 without) */
 } reg_solve_stats;
+
+/* Set the regularisation weight beta > 0 (e.g. between the stages of a
+ * hand-made continuation).  The linearisation point stays valid (the
+ * transports do not depend on beta).  REG_EINVAL unless beta is finite and
+ * positive. */
+int reg_set_beta(reg_ctx* ctx, double beta);
 
 /* Fill *opts with the defaults listed above. */
 int reg_solve_opts_default(reg_solve_opts* opts);
@@ -209,7 +225,10 @@ int reg_solve_opts_default(reg_solve_opts* opts);
  * v_inout [3n] is the initial guess on entry (zero, or a learned prediction)
  * and the solution on exit.  opts NULL = defaults; stats may be NULL.
  * Returns REG_OK when ||g|| <= gtol ||g_0||, REG_EMAXITER when max_gn was
- * reached first (v_inout then holds the last accepted iterate). */
+ * reached first (v_inout then holds the last accepted iterate).  With
+ * continuation (opts->beta_start) the counts of stats add up over the stages,
+ * J0 is the first stage's and J, gnorm, gnorm_rel, mismatch_rel the last
+ * one's; the context's beta is the target throughout and afterwards. */
 int reg_solve(reg_ctx* ctx, float* v_inout, const reg_solve_opts* opts,
               reg_solve_stats* stats);
 

@@ -52,14 +52,21 @@ def pcg(matvec, precond, rhs, tol_abs, max_iter):
 
 
 def gauss_newton(problem, v0, gtol=1e-2, max_gn=50, max_pcg=500,
-                 armijo_c=1e-4, armijo_max=10, log=None):
-    """Inexact GN-Krylov with Armijo line search.  Returns (v, stats)."""
+                 armijo_c=1e-4, armijo_max=10, log=None, gnorm_ref=None):
+    """Inexact GN-Krylov with Armijo line search.  Returns (v, stats).
+
+    gnorm_ref: the reference ||g_0|| of the stop test ||g|| <= gtol ||g_0||
+    and of the forcing term eta = min(0.5, ||g|| / ||g_0||); None takes the
+    gradient norm at v0 (the paper's solves start from v = 0).  A solve
+    resumed from one of its own iterates with the original ||g_0|| takes the
+    same steps as the uninterrupted solve.
+    """
     v = problem.project(np.array(v0, dtype=np.float64))
     g, J = problem.gradient(v)
-    g0 = np.sqrt(inner(g, g))
-    gn = g0
+    gn = np.sqrt(inner(g, g))
+    g0 = gn if gnorm_ref is None else float(gnorm_ref)
     stats = dict(gn_iters=0, pcg_iters=0, matvecs=0, J0=J, J=J, gnorm0=g0,
-                 gnorm=g0, history=[(J, g0)])
+                 gnorm=gn, history=[(J, gn)], pcg_per_step=[])
     r0 = problem.rho_T - problem.rho_R
     m0 = np.sqrt(inner(r0, r0))
     for k in range(max_gn):
@@ -70,6 +77,7 @@ def gauss_newton(problem, v0, gtol=1e-2, max_gn=50, max_pcg=500,
                            eta * gn, max_pcg)
         stats['pcg_iters'] += its
         stats['matvecs'] += its
+        stats['pcg_per_step'].append(its)
         slope = inner(g, s)
         alpha = 1.0
         accepted = False
@@ -97,3 +105,46 @@ def gauss_newton(problem, v0, gtol=1e-2, max_gn=50, max_pcg=500,
     r1 = rho1 - problem.rho_R
     stats['mismatch_rel'] = np.sqrt(inner(r1, r1)) / m0 if m0 > 0 else 0.0
     return v, stats
+
+
+def beta_schedule(beta_start, beta, factor):
+    """Continuation values of the regularisation weight: beta_start,
+    beta_start / factor, ... while above beta, then beta itself."""
+    out = []
+    b = float(beta_start)
+    while b > beta * (1.0 + 1e-12):
+        out.append(b)
+        b /= factor
+    out.append(float(beta))
+    return out
+
+
+def continuation(problem, v0, beta_start, factor=10.0, gtol=1e-2, **kw):
+    """Parameter continuation on beta (Sec. III-A: the problem is highly
+    nonlinear, so the solver starts from a larger regularisation weight and
+    lowers it to the target).  Reading (the paper gives no schedule): beta is
+    divided by `factor` from beta_start down to the problem's beta, each
+    stage a Gauss-Newton solve warm-started from the last one, every stage
+    stopped at ||g|| <= gtol ||g(v0)|| with ||g(v0)|| from the first stage
+    (at v0 = 0 the gradient -- P[(rho_R - rho_T) grad rho_T] -- does not
+    depend on beta, so every stage stops at the same absolute norm).
+    Returns (v, stats) with per-stage statistics in stats['stages'].
+    """
+    target = problem.beta
+    v = np.array(v0, dtype=np.float64)
+    stages, ref = [], kw.pop('gnorm_ref', None)
+    try:
+        for b in beta_schedule(beta_start, target, factor):
+            problem.beta = b
+            v, st = gauss_newton(problem, v, gtol=gtol, gnorm_ref=ref, **kw)
+            if ref is None:
+                ref = st['gnorm0']
+            st['beta'] = b
+            stages.append(st)
+    finally:
+        problem.beta = target
+    total = dict(stages[-1])
+    total['stages'] = stages
+    for key in ('gn_iters', 'pcg_iters', 'matvecs'):
+        total[key] = sum(st[key] for st in stages)
+    return v, total

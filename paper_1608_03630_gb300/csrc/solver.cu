@@ -497,6 +497,15 @@ int reg_solve_opts_default(reg_solve_opts* o) {
     o->verbose = 0;
     o->gnorm_ref = 0.0;
     o->precond_shift = 0.0;
+    o->beta_start = 0.0;
+    o->beta_factor = 10.0;
+    return REG_OK;
+}
+
+int reg_set_beta(reg_ctx* c, double beta) {
+    if (!c) return REG_EINVAL;
+    if (!(beta > 0.0) || !std::isfinite(beta)) return fail(c, REG_EINVAL, "beta must be > 0");
+    c->beta = beta;
     return REG_OK;
 }
 
@@ -512,11 +521,55 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
         o.max_gn < 0 || o.max_pcg < 1 || o.armijo_max < 1 ||
         !(o.armijo_shrink > 0.0 && o.armijo_shrink < 1.0))
         return fail(c, REG_EINVAL, "bad solver options");
+    if (!(o.beta_start >= 0.0) || !std::isfinite(o.beta_start) || !(o.beta_factor > 1.0) ||
+        !std::isfinite(o.beta_factor))
+        return fail(c, REG_EINVAL, "bad continuation options");
     REG_TRY(ensure_solver(c));
     c->pshift = o.precond_shift;
     reg_solve_stats local;
     memset(&local, 0, sizeof local);
-    const int s = solve_impl(c, v_inout, &o, &local);
+    if (!(o.beta_start > c->beta * (1.0 + 1e-12))) {
+        const int s = solve_impl(c, v_inout, &o, &local);
+        local.stages = 1;
+        if (stats) *stats = local;
+        return s;
+    }
+    // continuation: beta_start, beta_start / factor, ... down to the target
+    const auto t0 = std::chrono::steady_clock::now();
+    const double target = c->beta;
+    double b = o.beta_start;
+    int s = REG_OK;
+    bool last = false;
+    for (int stage = 0; !last; ++stage) {
+        last = !(b > target * (1.0 + 1e-12));
+        c->beta = last ? target : b;
+        reg_solve_stats st;
+        memset(&st, 0, sizeof st);
+        s = solve_impl(c, v_inout, &o, &st);
+        if (stage == 0) {
+            local.J0 = st.J0;
+            // later stages stop at the first stage's ||g_0||
+            if (o.gnorm_ref == 0.0 || o.gnorm_ref < 0.0) o.gnorm_ref = st.gnorm0;
+        }
+        local.gn_iters += st.gn_iters;
+        local.pcg_iters += st.pcg_iters;
+        local.matvecs += st.matvecs;
+        local.objective_evals += st.objective_evals;
+        local.gradient_evals += st.gradient_evals;
+        local.line_search_failed |= st.line_search_failed;
+        local.negative_curvature += st.negative_curvature;
+        local.gnorm0 = st.gnorm0;
+        local.J = st.J;
+        local.gnorm = st.gnorm;
+        local.gnorm_rel = st.gnorm_rel;
+        local.mismatch_rel = st.mismatch_rel;
+        local.stages = stage + 1;
+        if (s != REG_OK && s != REG_EMAXITER) break;
+        b /= o.beta_factor;
+    }
+    c->beta = target;
+    local.ms_total =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = local;
     return s;
 }

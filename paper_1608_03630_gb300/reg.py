@@ -34,7 +34,8 @@ class SolveOpts(ctypes.Structure):
                 ('armijo_c', ctypes.c_double), ('armijo_shrink', ctypes.c_double),
                 ('armijo_max', ctypes.c_int), ('use_graph', ctypes.c_int),
                 ('verbose', ctypes.c_int), ('gnorm_ref', ctypes.c_double),
-                ('precond_shift', ctypes.c_double)]
+                ('precond_shift', ctypes.c_double), ('beta_start', ctypes.c_double),
+                ('beta_factor', ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -45,7 +46,7 @@ class SolveStats(ctypes.Structure):
                 ('J0', ctypes.c_double), ('J', ctypes.c_double),
                 ('gnorm0', ctypes.c_double), ('gnorm', ctypes.c_double),
                 ('gnorm_rel', ctypes.c_double), ('mismatch_rel', ctypes.c_double),
-                ('ms_total', ctypes.c_double)]
+                ('ms_total', ctypes.c_double), ('stages', ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -83,6 +84,7 @@ _SIGS = {
     'reg_gradient_spectral': [_P, _P, _P, ctypes.POINTER(_D)],
     'reg_hessian_matvec_spectral': [_P, _P, _P],
     'reg_solve_opts_default': [ctypes.POINTER(SolveOpts)],
+    'reg_set_beta': [_P, _D],
     'reg_solve': [_P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)],
     'reg_solve_host': [_P, _P, _P, _I, _P, ctypes.POINTER(SolveOpts),
                        ctypes.POINTER(SolveStats)],
@@ -253,6 +255,10 @@ class Registration:
         return torch.empty(shape, device='cuda', dtype=torch.float32)
 
     # -- API --------------------------------------------------------------
+    def set_beta(self, beta):
+        """Regularisation weight beta > 0 (reg_set_beta)."""
+        self._call('reg_set_beta', float(beta))
+
     def set_hessian(self, full_newton):
         """True: full Newton Hessian (Eq. hessian with the lam terms);
         False: Gauss-Newton (the default)."""

@@ -40,6 +40,25 @@ def rounded_hat(f):
     return h32, from_hat(h32.astype(np.complex128), f.shape[-3:])
 
 
+def herm_weights(shape):
+    """Parseval weights of the half spectrum: 1 on the k3 = 0 (and Nyquist)
+    planes, 2 elsewhere."""
+    m3 = shape[2] // 2 + 1
+    w = np.full(m3, 2.0)
+    w[0] = 1.0
+    if shape[2] % 2 == 0:
+        w[-1] = 1.0
+    return w
+
+
+def rel_hat(got, ref, shape):
+    """Relative L2 error of normalised half-spectrum coefficients (the
+    physical-space relative L2, by Parseval)."""
+    w = herm_weights(shape)
+    d = np.abs(np.asarray(got).astype(np.complex128) - ref) ** 2
+    return float(np.sqrt(np.sum(d * w) / np.sum(np.abs(ref) ** 2 * w)))
+
+
 def sinusoid_case(shape, scale, kind, incompressible, beta, nt, vscale, dir_seeds, dir_kmax=8):
     """Gradient and Hessian matvecs of the sinusoid problem (v* x scale) at
     v = vscale v*, on band-limited directions (|k| <= dir_kmax, Leray-projected

@@ -49,23 +49,7 @@ def dev(a):
     return torch.tensor(np.ascontiguousarray(a), device='cuda')
 
 
-def herm_weights(shape):
-    """Parseval weights of the half spectrum: 1 on the k3 = 0 (and Nyquist)
-    planes, 2 elsewhere."""
-    m3 = shape[2] // 2 + 1
-    w = np.full(m3, 2.0)
-    w[0] = 1.0
-    if shape[2] % 2 == 0:
-        w[-1] = 1.0
-    return w
-
-
-def rel_hat(got, ref, shape):
-    """Relative L2 error of normalised half-spectrum coefficients (the
-    physical-space relative L2 by Parseval)."""
-    w = herm_weights(shape)
-    d = np.abs(got.astype(np.complex128) - ref) ** 2
-    return float(np.sqrt(np.sum(d * w) / np.sum(np.abs(ref) ** 2 * w)))
+rel_hat = oracle_jobs.rel_hat
 
 
 def host(t):

@@ -134,3 +134,62 @@ def test_pins_catch_a_wrong_step_sign(monkeypatch):
         _, st = so.gauss_newton(P, v0, gtol=1e-6, max_gn=20)
         assert st.get('line_search_failed', False)
         assert st['gnorm_rel'] > 1e-6
+
+
+class RegularisedQuadratic(Quadratic):
+    """J_beta(v) = 1/2 <v, (A + beta B) v> - <b, v>: a data term plus a
+    regularisation weighted by beta, minimiser (A + beta B)^-1 b."""
+
+    def __init__(self, seed, beta):
+        super().__init__(seed)
+        rng = np.random.default_rng(seed + 100)
+        n = self.A.shape[0]
+        self.A = self.A - np.eye(n) + 1e-3 * np.eye(n)   # nearly singular data term
+        self.B = np.diag(1.0 + rng.uniform(0.0, 10.0, n))
+        self.beta = beta
+
+    def apply(self, v):
+        return ((self.A + self.beta * self.B) @ v.ravel()).reshape(SHAPE)
+
+    def precond(self, r):
+        return r / (self.beta * np.diag(self.B)).reshape(SHAPE)
+
+    def minimiser(self):
+        return np.linalg.solve(self.A + self.beta * self.B, self.b.ravel()).reshape(SHAPE)
+
+
+def test_resumed_solve_with_the_reference_norm_repeats_the_uninterrupted_one():
+    """gnorm_ref: a solve stopped after two Newton steps and resumed from its
+    iterate with the original ||g_0|| takes exactly the remaining steps."""
+    P = RegularisedQuadratic(7, 1e-2)
+    v_all, st_all = so.gauss_newton(P, np.zeros(SHAPE), gtol=1e-9, max_gn=20)
+    v2, st2 = so.gauss_newton(P, np.zeros(SHAPE), gtol=1e-9, max_gn=2)
+    v_rest, st_rest = so.gauss_newton(P, v2, gtol=1e-9, max_gn=20, gnorm_ref=st2['gnorm0'])
+    assert st2['gn_iters'] + st_rest['gn_iters'] == st_all['gn_iters']
+    assert st2['pcg_per_step'] + st_rest['pcg_per_step'] == st_all['pcg_per_step']
+    assert np.abs(v_rest - v_all).max() <= 1e-12 * np.abs(v_all).max()
+
+
+def test_beta_schedule():
+    assert np.allclose(so.beta_schedule(1e-1, 1e-4, 10.0), [1e-1, 1e-2, 1e-3, 1e-4])
+    assert so.beta_schedule(1.0, 0.3, 10.0) == [1.0, 0.3]
+    assert so.beta_schedule(1e-3, 1e-3, 10.0) == [1e-3]
+
+
+def test_continuation_ends_at_the_target_minimiser():
+    """Continuation from beta = 1 to 1e-4 reaches the minimiser of the target
+    objective (to the stopping tolerance), the single-stage schedule is the
+    plain solve, and the weight is restored afterwards."""
+    P = RegularisedQuadratic(9, 1e-4)
+    x = P.minimiser()
+    v, st = so.continuation(P, np.zeros(SHAPE), 1.0, 10.0, gtol=1e-10, max_gn=30)
+    assert [s['beta'] for s in st['stages']] == so.beta_schedule(1.0, 1e-4, 10.0)
+    assert P.beta == 1e-4
+    assert np.abs(v - x).max() < 1e-7 * np.abs(x).max()
+    assert st['gn_iters'] == sum(s['gn_iters'] for s in st['stages'])
+    v1, st1 = so.continuation(P, np.zeros(SHAPE), 1e-4, 10.0, gtol=1e-10, max_gn=30)
+    v0, st0 = so.gauss_newton(P, np.zeros(SHAPE), gtol=1e-10, max_gn=30)
+    assert np.array_equal(v1, v0) and st1['pcg_iters'] == st0['pcg_iters']
+    # every stage stops at the first stage's reference norm: the final
+    # gradient is below gtol times the gradient at v = 0
+    assert st['gnorm'] <= 1e-10 * st['stages'][0]['gnorm0'] * (1 + 1e-9)
