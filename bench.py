@@ -499,7 +499,9 @@ def beta_sweep(args):
     falls, Sec. IV-C), on the 256^3 phantom (nt = 8, H2, FP32) instead of the
     brain images: per beta, (a) four Newton iterations from v = 0 (the
     table's protocol), (b) the solve to ||g|| <= 1e-2 ||g_0||, and (c) the
-    same solve with parameter continuation from beta = 1e-1 (factor 10).
+    same solve with parameter continuation from beta = 1e-1 (factor 10), and
+    (d) the solve with the two-level preconditioner (coarse grids n/2, n/4;
+    inner PCG to 0.1, at most 20 iterations; flexible PCG outside).
     Time to solution by CUDA events on the library stream."""
     import torch
 
@@ -526,7 +528,8 @@ def beta_sweep(args):
             e1.record(stream)
             torch.cuda.synchronize()
             return {'status': s, 'time_s': e0.elapsed_time(e1) / 1e3, 'gn_iters': st['gn_iters'],
-                    'matvecs': st['matvecs'], 'gnorm_rel': st['gnorm_rel'],
+                    'matvecs': st['matvecs'], 'coarse_matvecs': st['coarse_matvecs'],
+                    'gnorm_rel': st['gnorm_rel'],
                     'mismatch_rel': st['mismatch_rel'], 'stages': st['stages'],
                     'negative_curvature': st['negative_curvature']}
 
@@ -538,6 +541,9 @@ def beta_sweep(args):
                    'gtol': timed(gtol=1e-2)}
             if beta < 1e-1:
                 row['continuation'] = timed(gtol=1e-2, beta_start=1e-1, beta_factor=10.0)
+            for cf in args.coarse_factors:
+                row['twolevel_%d' % cf] = timed(gtol=1e-2, coarse_factor=cf, coarse_tol=0.1,
+                                                coarse_max=20)
             rows.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
         R.close()
@@ -563,6 +569,7 @@ def main():
                     choices=['phantom256', 'batched', 'beta_sweep'])
     ap.add_argument('--sweep-n', type=int, default=256)
     ap.add_argument('--betas', type=float, nargs='+', default=[1e-1, 1e-2, 1e-3, 1e-4, 1e-5])
+    ap.add_argument('--coarse-factors', type=int, nargs='*', default=[2, 4])
     ap.add_argument('--pairs', type=int, default=48)
     ap.add_argument('--profile-matvec', type=int, default=0, metavar='N',
                     help='run one gradient and two matvecs at N^3 (nt = 4) for ncu, then exit')

@@ -201,6 +201,21 @@ typedef struct {
                              stage (at v = 0 independent of beta); 0 or
                              <= beta: one solve at the context's beta     (0) */
     double beta_factor;   /* continuation divisor per stage, > 1          (10) */
+    int coarse_factor;    /* >= 2: the two-level preconditioner
+                             M^-1 r = Pi_L H_c^-1 Pi_L r
+                                      + (beta A)^-1 P (I - Pi_L) r
+                             with H_c the Gauss-Newton Hessian on the grid
+                             n_j / coarse_factor (images restricted to the
+                             modes L = {|k_j| < n_j / (2 coarse_factor)},
+                             linearised at the restricted v every Newton
+                             step), inverted by PCG to coarse_tol; the
+                             Newton steps then by flexible PCG.  Sec. I
+                             names multilevel preconditioning as the
+                             remedy for the beta dependence of (beta A)^-1
+                             (Table 5).  Each n_j / coarse_factor must be
+                             an integer >= 8.  0 or 1: off               (0) */
+    double coarse_tol;    /* inner PCG relative residual tolerance       (0.1) */
+    int coarse_max;       /* inner PCG iteration cap                      (10) */
 } reg_solve_opts;
 
 typedef struct {
@@ -210,6 +225,7 @@ typedef struct {
     double J0, J, gnorm0, gnorm, gnorm_rel, mismatch_rel;
     double ms_total;          /* wall time of the solve (host clock) */
     int stages;               /* continuation stages run (1 without) */
+    int coarse_matvecs;       /* coarse-grid Hessian matvecs (two-level) */
 } reg_solve_stats;
 
 /* Set the regularisation weight beta > 0 (e.g. between the stages of a
@@ -217,6 +233,20 @@ typedef struct {
  * transports do not depend on beta).  REG_EINVAL unless beta is finite and
  * positive. */
 int reg_set_beta(reg_ctx* ctx, double beta);
+
+/* The two-level preconditioner of reg_solve_opts.coarse_factor, applied
+ * alone (normalised half-spectrum coefficients, as for
+ * reg_gradient_spectral).  reg_twolevel_setup creates the coarse grid's
+ * context (n_j / coarse_factor; once per factor), restricts the images to
+ * it, and linearises its Gauss-Newton Hessian at the restriction of v_hat.
+ * reg_twolevel_apply: z_hat = M^-1 r_hat with the inner PCG stopped at
+ * ||r_c|| <= inner_tol ||r_c,0|| or after inner_max iterations
+ * (inner_tol = 0: exactly inner_max unless it converges or meets negative
+ * curvature); *inner_iters (may be NULL) receives the count.  REG_ENOTREADY
+ * before a setup. */
+int reg_twolevel_setup(reg_ctx* ctx, int coarse_factor, const float* v_hat);
+int reg_twolevel_apply(reg_ctx* ctx, const float* r_hat, float* z_hat, double inner_tol,
+                       int inner_max, int* inner_iters);
 
 /* Fill *opts with the defaults listed above. */
 int reg_solve_opts_default(reg_solve_opts* opts);

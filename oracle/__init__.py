@@ -18,12 +18,16 @@ section and equation:
                    (Eq. (sml-trajectory), Eq. (sml-advection), Algorithm 2).
 * ``problem``   -- objective, gradient and Gauss-Newton Hessian matvec
                    (Eq. (varopt), Eq. (gradient), Eq. (hessian)).
-* ``solver``    -- PCG and the inexact Gauss-Newton method with Armijo line
-                   search (Sec. III-A, Sec. IV-A3).
+* ``solver``    -- PCG (and flexible PCG), the inexact Gauss-Newton method
+                   with Armijo line search, parameter continuation on beta
+                   (Sec. III-A, Sec. IV-A3).
+* ``precond``   -- the two-level (coarse-grid Hessian plus inverse
+                   regularisation) preconditioner (Sec. I limitations,
+                   Sec. III-A, Table 5).
 
 Readings of places where the paper is silent or garbled are listed in each
 function's docstring.  Floating point throughout is float64; FFTs are
 ``numpy.fft`` (a library primitive used as one step).
 """
 
-from . import spectral, interp, transport, problem, solver  # noqa: F401
+from . import spectral, interp, transport, problem, solver, precond  # noqa: F401

@@ -51,15 +51,47 @@ def pcg(matvec, precond, rhs, tol_abs, max_iter):
     return s, max_iter, 'max_iter'
 
 
+def fpcg(matvec, precond, rhs, tol_abs, max_iter):
+    """Flexible preconditioned CG for H s = rhs from s = 0 (the direction
+    update beta = -alpha <z_new, q> / <r, z>, q = H p).  Same return
+    convention as solver.pcg: (s, iters, flag)."""
+    s = np.zeros_like(rhs)
+    r = rhs.copy()
+    if np.sqrt(inner(r, r)) <= tol_abs:
+        return s, 0, 'converged'
+    z = precond(r)
+    p = z.copy()
+    rz = inner(r, z)
+    for it in range(1, max_iter + 1):
+        q = matvec(p)
+        pq = inner(p, q)
+        if pq <= 0.0:
+            if it == 1:
+                return p, it, 'negative_curvature'
+            return s, it, 'negative_curvature'
+        alpha = rz / pq
+        s = s + alpha * p
+        r = r - alpha * q
+        if np.sqrt(inner(r, r)) <= tol_abs:
+            return s, it, 'converged'
+        z = precond(r)
+        bk = -alpha * inner(z, q) / rz
+        rz = inner(r, z)
+        p = z + bk * p
+    return s, max_iter, 'max_iter'
+
+
 def gauss_newton(problem, v0, gtol=1e-2, max_gn=50, max_pcg=500,
-                 armijo_c=1e-4, armijo_max=10, log=None, gnorm_ref=None):
+                 armijo_c=1e-4, armijo_max=10, log=None, gnorm_ref=None, flexible=False):
     """Inexact GN-Krylov with Armijo line search.  Returns (v, stats).
 
     gnorm_ref: the reference ||g_0|| of the stop test ||g|| <= gtol ||g_0||
     and of the forcing term eta = min(0.5, ||g|| / ||g_0||); None takes the
     gradient norm at v0 (the paper's solves start from v = 0).  A solve
     resumed from one of its own iterates with the original ||g_0|| takes the
-    same steps as the uninterrupted solve.
+    same steps as the uninterrupted solve.  flexible: the Newton steps by
+    flexible PCG (for a preconditioner that varies with its argument, such
+    as the two-level one of oracle.precond).
     """
     v = problem.project(np.array(v0, dtype=np.float64))
     g, J = problem.gradient(v)
@@ -73,8 +105,8 @@ def gauss_newton(problem, v0, gtol=1e-2, max_gn=50, max_pcg=500,
         if gn <= gtol * g0 or g0 == 0.0:
             break
         eta = min(0.5, gn / g0)
-        s, its, flag = pcg(problem.hessian_matvec, problem.precond, -g,
-                           eta * gn, max_pcg)
+        krylov = fpcg if flexible else pcg
+        s, its, flag = krylov(problem.hessian_matvec, problem.precond, -g, eta * gn, max_pcg)
         stats['pcg_iters'] += its
         stats['matvecs'] += its
         stats['pcg_per_step'].append(its)

@@ -273,6 +273,16 @@ cudaError_t launch_sp_dot(const Dims& g, const float2* a, const float2* b, doubl
 cudaError_t launch_sp_normalise(const Dims& g, const float2* in, float2* out, int project,
                                 cudaStream_t st);
 
+// Two-level preconditioner between a fine grid gf and a coarse grid gc (both
+// with normalised half-spectrum coefficients, 3 fields): restriction to the
+// modes L = {|k_j| < nc_j / 2} scaled by `scale` (coarse Nyquist planes 0);
+// z = y on L, M P r elsewhere, with partials <r, z>.
+cudaError_t launch_sp_restrict(const Dims& gf, const Dims& gc, const float2* in, float2* out,
+                               float scale, cudaStream_t st);
+cudaError_t launch_sp_twolevel(const Dims& gf, const Dims& gc, const float2* r, const float2* y,
+                               float2* z, double beta, double shift, int kind, int project,
+                               double* partials, int nblk, cudaStream_t st);
+
 // blas.cu
 int blas_blocks();   // number of partial-sum blocks used by reductions
 cudaError_t launch_dot_partials(const float* a, const float* b, long long count,

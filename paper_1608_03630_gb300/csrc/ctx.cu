@@ -545,8 +545,9 @@ static void free_ctx(reg_ctx* c) {
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i)
         if (c->sv[i]) cudaFree(c->sv[i]);
-    for (int i = 0; i < 8; ++i)
+    for (int i = 0; i < 9; ++i)
         if (c->ss[i]) cudaFree(c->ss[i]);
+    if (c->coarse) free_ctx(c->coarse);
     if (c->hsc) cudaFreeHost(c->hsc);
     if (c->pcg_exec) cudaGraphExecDestroy(c->pcg_exec);
     if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
@@ -762,6 +763,7 @@ int reg_set_images(reg_ctx* c, const float* rho_T, const float* rho_R, int presm
     CHECK_PTR(c, rho_R);
     const long long n = c->g.n;
     c->have_lin = false;
+    c->img_version++;
     if (rho_T != c->rho_T)
         REG_CK(c, cudaMemcpyAsync(c->rho_T, rho_T, sizeof(float) * n, cudaMemcpyDeviceToDevice,
                                   c->stream));

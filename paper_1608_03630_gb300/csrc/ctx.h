@@ -67,10 +67,17 @@ struct reg_ctx {
     float* lam_lin;      // [(nt+1) n] lam(t_j) at the linearisation point
     float* rt_hist;      // [nt n] carried incremental state u_j, j < nt
 
-    // solver vectors: real [3n] each, spectral [3 nc] each
+    // solver vectors: real [3n] each, spectral [3 nc] each (ss[8], the
+    // flexible PCG's H p, only with the two-level preconditioner)
     float* sv[4];
-    float2* ss[8];
+    float2* ss[9];
     bool have_solver;
+
+    // two-level preconditioner: a context on the coarse grid (n_j / factor)
+    // holding the restricted images, linearised at the restricted velocity
+    reg_ctx* coarse;
+    int coarse_factor;
+    long long img_version, coarse_img_version;   // restrict the images again when they change
 
     // timing
     bool timing;

@@ -35,7 +35,7 @@ static const double kTwoPi3 = 248.05021344239856;   // (2 pi)^3
 // real vectors
 enum { R_V = 0, R_P = 1, R_HOST = 2 };
 // spectral vectors
-enum { S_V = 0, S_VT = 1, S_G = 2, S_S = 3, S_R = 4, S_P = 5, S_PC = 6 };
+enum { S_V = 0, S_VT = 1, S_G = 2, S_S = 3, S_R = 4, S_P = 5, S_PC = 6, S_Z = 7, S_Q = 8 };
 
 static int finalize_to(reg_ctx* c, int t, int nb, double scale, int slot) {
     if ((long long)(t + 1) * nb > c->npartials)
@@ -166,8 +166,9 @@ static cudaGraphExec_t build_pcg_loop(reg_ctx* c) {
     return exec;
 }
 
+// rel_tol > 0: the tolerance is rel_tol ||P r_0|| instead of tol.
 static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verbose,
-                     PcgResult* res) {
+                     PcgResult* res, double rel_tol = 0.0) {
     const int nb = blas_blocks();
     const int proj = c->incompressible;
     float2** S = c->ss;
@@ -184,6 +185,7 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
     REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZ));
     REG_TRY(finalize_to(c, 2, nb, kTwoPi3, SC_PAP));
     REG_TRY(read_scalars(c, SC_RZ, 13));
+    if (rel_tol > 0.0) tol = rel_tol * std::sqrt(c->hsc[SC_RR]);
     if (verbose > 1)
         fprintf(stderr, "  pcg 0  rr %.6e  rz %.6e  pap %.6e  tol %.6e\n", c->hsc[SC_RR],
                 c->hsc[SC_RZ], c->hsc[SC_PAP], tol);
@@ -305,6 +307,192 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
     if (graph) cudaGraphDestroy(graph);
     release_graph_timing(c);
     return status;
+}
+
+// ------------------------------------------------ two-level preconditioner
+// M^-1 r = Pi_L H_c^-1 Pi_L r + (beta A)^-1 P (I - Pi_L) r: H_c is the
+// Gauss-Newton Hessian on the coarse grid n_j / factor (the images restricted
+// to the modes L = {|k_j| < n_j / (2 factor)}, linearised at the restriction
+// of v), inverted by the coarse context's own device-controlled PCG to a
+// relative tolerance; the modes outside L get the inverse regularisation
+// operator.  Normalised coefficients of the modes in L are the same numbers
+// on both grids, so restriction and prolongation are copies.
+
+static int child_fail(reg_ctx* c, int s) {
+    if (s != REG_OK && c->coarse && !c->coarse->err.empty())
+        fail(c, s, "coarse grid: " + c->coarse->err);
+    if (s == REG_ECUDA) c->dead = true;
+    return s;
+}
+
+// Create (or keep) the coarse context and give it the restricted images.
+static int twolevel_setup(reg_ctx* c, int factor) {
+    const Dims& g = c->g;
+    if (factor < 2 || g.n1 % factor || g.n2 % factor || g.n3 % factor ||
+        g.n1 / factor < 8 || g.n2 / factor < 8 || g.n3 / factor < 8)
+        return fail(c, REG_EINVAL, "coarse factor: >= 2, dividing every n_j, n_j / factor >= 8");
+    if (!c->have_images) return fail(c, REG_ENOTREADY, "reg_set_images first");
+    if (c->coarse && c->coarse_factor != factor) {
+        reg_destroy(c->coarse);
+        c->coarse = nullptr;
+    }
+    if (!c->coarse) {
+        reg_ctx* k = nullptr;
+        const int s = reg_create(g.n1 / factor, g.n2 / factor, g.n3 / factor, c->nt, c->beta,
+                                 c->kind, c->incompressible, &k);
+        if (s != REG_OK) return fail(c, s, std::string("coarse grid: ") + reg_last_error(nullptr));
+        c->coarse = k;
+        c->coarse_factor = factor;
+        c->coarse_img_version = -1;
+    }
+    reg_ctx* k = c->coarse;
+    REG_TRY(child_fail(c, bind_stream(k, c->stream)));
+    REG_TRY(child_fail(c, ensure_solver(k)));
+    k->beta = c->beta;
+    k->pshift = 0.0;
+    k->hessian = REG_HESS_GAUSS_NEWTON;
+    if (c->coarse_img_version != c->img_version) {
+        const int nin[3] = {g.n1, g.n2, g.n3}, nout[3] = {k->g.n1, k->g.n2, k->g.n3};
+        int s = reg_spectral_resample(nin, nout, 1, c->rho_T, k->rho_T, c->stream);
+        if (s == REG_OK) s = reg_spectral_resample(nin, nout, 1, c->rho_R, k->rho_R, c->stream);
+        if (s != REG_OK) return fail(c, s, "coarse grid: image restriction failed");
+        REG_TRY(child_fail(c, reg_set_images(k, k->rho_T, k->rho_R, 0)));
+        c->coarse_img_version = c->img_version;
+    }
+    return REG_OK;
+}
+
+// Linearise the coarse Hessian at the restriction of the fine v_hat.
+static int twolevel_linearize(reg_ctx* c, const float2* v_hat) {
+    reg_ctx* k = c->coarse;
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 24.0 * 2.0 * (double)k->g.nc);
+        REG_CK(c, launch_sp_restrict(c->g, k->g, v_hat, k->ss[S_V], 1.f, c->stream));
+    }
+    float* vc = k->sv[R_V];
+    REG_TRY(child_fail(c, to_physical(k, k->ss[S_V], vc)));
+    return child_fail(c, op_linearize(k, vc));
+}
+
+// z_hat = M^-1 r_hat and dsc[slot] = <r, z>; *inner = coarse PCG iterations.
+static int twolevel_apply(reg_ctx* c, const float2* r_hat, float2* z_hat, double tol_rel,
+                          int max_it, int slot, int* inner) {
+    reg_ctx* k = c->coarse;
+    const int nb = blas_blocks();
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 24.0 * 2.0 * (double)k->g.nc);
+        REG_CK(c, launch_sp_restrict(c->g, k->g, r_hat, k->ss[S_G], -1.f, c->stream));
+    }
+    PcgResult pr;
+    // the coarse PCG solves H_c s = -g_c = Pi_L r
+    const int s = pcg_solve(k, 0.0, max_it, 2, 0, &pr, tol_rel > 0.0 ? tol_rel : 1e-30);
+    if (s != REG_OK) return child_fail(c, s);
+    if (inner) *inner = pr.iters;
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 24.0 * 3.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_twolevel(c->g, k->g, r_hat, k->ss[S_S], z_hat, c->beta, 0.0, c->kind,
+                                     c->incompressible, c->partials, nb, c->stream));
+    }
+    return finalize_to(c, 0, nb, kTwoPi3, slot);
+}
+
+// Flexible PCG on H s = -g (Sec. III-A with the two-level preconditioner):
+// the direction p_{k+1} = z_{k+1} + b p_k with b = -alpha <z_{k+1}, H p_k> /
+// <r_k, z_k>, H-conjugate to the last direction however M^-1 varies.
+// Host-driven (it reads the scalars every iteration); the same stopping
+// tests as pcg_solve.
+static int pcg_solve_twolevel(reg_ctx* c, double tol, int max_it, double ctol, int cmax,
+                              PcgResult* res, int* coarse_iters) {
+    const int nb = blas_blocks();
+    const int proj = c->incompressible;
+    float2** S = c->ss;
+    res->iters = 0;
+    res->neg_curv = false;
+    res->converged = false;
+    // r = -g, s = 0 (p, pc are overwritten below)
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 5.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_init(c->g, S[S_G], S[S_R], S[S_S], S[S_P], S[S_PC], c->beta, 0.0,
+                                 c->kind, proj, c->partials, nb, c->stream));
+    }
+    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
+    REG_TRY(read_scalars(c, SC_RR, 1));
+    if (std::sqrt(c->hsc[SC_RR]) <= tol) { res->converged = true; return REG_OK; }
+    int it_in = 0;
+    REG_TRY(twolevel_apply(c, S[S_R], S[S_Z], ctol, cmax, SC_RZ, &it_in));
+    *coarse_iters += it_in;
+    REG_CK(c, cudaMemcpyAsync(S[S_P], S[S_Z], sizeof(float2) * 3 * (size_t)c->g.nc,
+                              cudaMemcpyDeviceToDevice, c->stream));
+    for (int it = 1; it <= max_it; ++it) {
+        // q = H p on the coefficients
+        REG_TRY(to_physical(c, S[S_P], c->sv[R_P]));
+        REG_TRY(op_matvec_transport(c, c->sv[R_P], nullptr, 0));
+        REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
+        {
+            Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
+            REG_CK(c, launch_sp_gradient(c->g, S[S_P], c->spec[1], S[S_Q], c->beta, c->kind, proj,
+                                         c->partials, nb, c->stream));
+        }
+        {
+            Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
+            REG_CK(c, launch_sp_dot(c->g, S[S_P], S[S_Q], c->partials, nb, c->stream));
+        }
+        REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_PQ));
+        REG_TRY(read_scalars(c, SC_RZ, 2));   // RZ, PQ
+        res->iters = it;
+        const double rz = c->hsc[SC_RZ], pq = c->hsc[SC_PQ];
+        if (!std::isfinite(pq) || !std::isfinite(rz))
+            return fail(c, REG_ENONFINITE, "non-finite value in PCG");
+        if (pq <= 0.0) {
+            res->neg_curv = true;
+            if (it == 1)   // first direction: s = p = M^-1 r
+                REG_CK(c, cudaMemcpyAsync(S[S_S], S[S_P], sizeof(float2) * 3 * (size_t)c->g.nc,
+                                          cudaMemcpyDeviceToDevice, c->stream));
+            break;
+        }
+        const float alpha = (float)(rz / pq);
+        {
+            Phase ph(c, REG_PH_SPECTRAL, 2.0 * 3.0 * 24.0 * (double)c->g.nc);
+            REG_CK(c, launch_sp_axpy(c->g, S[S_S], nullptr, S[S_S], S[S_P], alpha, c->kind, 0,
+                                     c->partials, nb, c->stream));
+            REG_CK(c, launch_sp_axpy(c->g, S[S_R], nullptr, S[S_R], S[S_Q], -alpha, c->kind, 0,
+                                     c->partials, nb, c->stream));
+            REG_CK(c, launch_sp_dot(c->g, S[S_R], S[S_R], c->partials, nb, c->stream));
+        }
+        REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
+        REG_TRY(read_scalars(c, SC_RR, 1));
+        if (!std::isfinite(c->hsc[SC_RR])) return fail(c, REG_ENONFINITE, "non-finite residual");
+        if (std::sqrt(c->hsc[SC_RR]) <= tol) { res->converged = true; break; }
+        if (it == max_it) break;
+        REG_TRY(twolevel_apply(c, S[S_R], S[S_Z], ctol, cmax, SC_RZNEW, &it_in));
+        *coarse_iters += it_in;
+        {
+            Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
+            REG_CK(c, launch_sp_dot(c->g, S[S_Z], S[S_Q], c->partials, nb, c->stream));
+        }
+        REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_TMP));
+        REG_TRY(read_scalars(c, SC_RZNEW, 1));
+        REG_TRY(read_scalars(c, SC_TMP, 1));
+        const float bk = (float)(-(double)alpha * c->hsc[SC_TMP] / rz);
+        {
+            Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
+            REG_CK(c, launch_sp_axpy(c->g, S[S_P], nullptr, S[S_Z], S[S_P], bk, c->kind, 0,
+                                     c->partials, nb, c->stream));
+        }
+        REG_CK(c, cudaMemcpyAsync(c->dsc + SC_RZ, c->dsc + SC_RZNEW, sizeof(double),
+                                  cudaMemcpyDeviceToDevice, c->stream));
+    }
+    return REG_OK;
+}
+
+static int ensure_flexible(reg_ctx* c) {
+    if (c->ss[S_Q]) return REG_OK;
+    if (cudaMalloc(&c->ss[S_Q], sizeof(float2) * 3 * (size_t)c->g.nc) != cudaSuccess) {
+        cudaGetLastError();
+        c->ss[S_Q] = nullptr;
+        return fail(c, REG_ENOMEM, "cannot allocate the flexible PCG vector");
+    }
+    return REG_OK;
 }
 
 // g_hat = beta A v_hat + P b_hat at the spectral iterate; J and ||g||.
@@ -429,7 +617,13 @@ static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solv
         const double ratio = gn / g0;
         const double eta = std::fmin(0.5, o->forcing == 1 ? std::sqrt(ratio) : ratio);
         PcgResult pr;
-        REG_TRY(pcg_solve(c, eta * gn, o->max_pcg, o->use_graph, o->verbose, &pr));
+        if (o->coarse_factor >= 2) {
+            REG_TRY(twolevel_linearize(c, S[S_V]));
+            REG_TRY(pcg_solve_twolevel(c, eta * gn, o->max_pcg, o->coarse_tol, o->coarse_max, &pr,
+                                       &st->coarse_matvecs));
+        } else {
+            REG_TRY(pcg_solve(c, eta * gn, o->max_pcg, o->use_graph, o->verbose, &pr));
+        }
         st->pcg_iters += pr.iters;
         st->matvecs += pr.iters;
         st->negative_curvature += pr.neg_curv ? 1 : 0;
@@ -499,6 +693,36 @@ int reg_solve_opts_default(reg_solve_opts* o) {
     o->precond_shift = 0.0;
     o->beta_start = 0.0;
     o->beta_factor = 10.0;
+    o->coarse_factor = 0;
+    o->coarse_tol = 0.1;
+    o->coarse_max = 10;
+    return REG_OK;
+}
+
+int reg_twolevel_setup(reg_ctx* c, int coarse_factor, const float* v_hat) {
+    if (!c) return REG_EINVAL;
+    if (c->dead) return fail(c, REG_ECUDA, "context unusable after a CUDA error");
+    if (!v_hat || ((uintptr_t)v_hat & 15u)) return fail(c, REG_EINVAL, "bad v_hat");
+    REG_TRY(ensure_solver(c));
+    REG_TRY(twolevel_setup(c, coarse_factor));
+    return twolevel_linearize(c, reinterpret_cast<const float2*>(v_hat));
+}
+
+int reg_twolevel_apply(reg_ctx* c, const float* r_hat, float* z_hat, double inner_tol,
+                       int inner_max, int* inner_iters) {
+    if (!c) return REG_EINVAL;
+    if (c->dead) return fail(c, REG_ECUDA, "context unusable after a CUDA error");
+    if (!r_hat || !z_hat || ((uintptr_t)r_hat & 15u) || ((uintptr_t)z_hat & 15u) ||
+        r_hat == z_hat)
+        return fail(c, REG_EINVAL, "r_hat / z_hat: null, unaligned or overlapping");
+    if (!(inner_tol >= 0.0) || inner_max < 1) return fail(c, REG_EINVAL, "bad inner options");
+    if (!c->coarse || !c->coarse->have_lin)
+        return fail(c, REG_ENOTREADY, "reg_twolevel_setup first");
+    c->coarse->beta = c->beta;
+    int it = 0;
+    REG_TRY(twolevel_apply(c, reinterpret_cast<const float2*>(r_hat),
+                           reinterpret_cast<float2*>(z_hat), inner_tol, inner_max, SC_TMP, &it));
+    if (inner_iters) *inner_iters = it;
     return REG_OK;
 }
 
@@ -524,7 +748,17 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
     if (!(o.beta_start >= 0.0) || !std::isfinite(o.beta_start) || !(o.beta_factor > 1.0) ||
         !std::isfinite(o.beta_factor))
         return fail(c, REG_EINVAL, "bad continuation options");
+    if (o.coarse_factor != 0 && o.coarse_factor != 1) {
+        if (!(o.coarse_tol >= 0.0) || o.coarse_max < 1)
+            return fail(c, REG_EINVAL, "bad coarse-grid options");
+    }
     REG_TRY(ensure_solver(c));
+    if (o.coarse_factor >= 2) {
+        REG_TRY(ensure_flexible(c));
+        REG_TRY(twolevel_setup(c, o.coarse_factor));
+    } else {
+        o.coarse_factor = 0;
+    }
     c->pshift = o.precond_shift;
     reg_solve_stats local;
     memset(&local, 0, sizeof local);
@@ -543,6 +777,7 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
     for (int stage = 0; !last; ++stage) {
         last = !(b > target * (1.0 + 1e-12));
         c->beta = last ? target : b;
+        if (c->coarse) c->coarse->beta = c->beta;
         reg_solve_stats st;
         memset(&st, 0, sizeof st);
         s = solve_impl(c, v_inout, &o, &st);
@@ -558,6 +793,7 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
         local.gradient_evals += st.gradient_evals;
         local.line_search_failed |= st.line_search_failed;
         local.negative_curvature += st.negative_curvature;
+        local.coarse_matvecs += st.coarse_matvecs;
         local.gnorm0 = st.gnorm0;
         local.J = st.J;
         local.gnorm = st.gnorm;
@@ -568,6 +804,7 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
         b /= o.beta_factor;
     }
     c->beta = target;
+    if (c->coarse) c->coarse->beta = target;
     local.ms_total =
         std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (stats) *stats = local;

@@ -398,6 +398,65 @@ k_sp_normalise(Dims g, const float2* in, float2* out, int project, float inv_n) 
     }
 }
 
+// Two-level preconditioner (coarse grid gc of the fine grid gf): the modes
+// L = {|k_j| < nc_j / 2} are the same normalised coefficients on both grids.
+__device__ __forceinline__ int fft_k(int i, int n) { return 2 * i < n ? i : i - n; }
+
+// out (coarse) = scale * in (fine) on L, 0 on the coarse Nyquist planes.
+__global__ void __launch_bounds__(kThreads)
+k_sp_restrict(Dims gf, Dims gc, const float2* __restrict__ in, float2* __restrict__ out,
+              float scale) {
+    const long long ncf = gf.nc, ncc = gc.nc;
+    for (int idx = blockIdx.x * kThreads + threadIdx.x; idx < gc.nc; idx += gridDim.x * kThreads) {
+        const int i3 = idx % gc.m3;
+        const int r = idx / gc.m3;
+        const int i2 = r % gc.n2, i1 = r / gc.n2;
+        const int k1 = fft_k(i1, gc.n1), k2 = fft_k(i2, gc.n2);
+        const bool keep = 2 * abs(k1) < gc.n1 && 2 * abs(k2) < gc.n2 && 2 * i3 < gc.n3;
+        const int f1 = k1 >= 0 ? k1 : k1 + gf.n1, f2 = k2 >= 0 ? k2 : k2 + gf.n2;
+        const long long fi = ((long long)f1 * gf.n2 + f2) * gf.m3 + i3;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            out[c * ncc + idx] = keep ? scale2(in[c * ncf + fi], scale) : make_float2(0.f, 0.f);
+    }
+}
+
+// z = y (coarse) on L, M P r elsewhere; partials: <r, z>.
+__global__ void __launch_bounds__(kThreads)
+k_sp_twolevel(Dims gf, Dims gc, const float2* __restrict__ r, const float2* __restrict__ y,
+              float2* __restrict__ z, float beta, float shift, int kind, int project,
+              double* partials) {
+    const long long ncf = gf.nc, ncc = gc.nc;
+    double acc[1] = {0.0};
+    for (int idx = blockIdx.x * kThreads + threadIdx.x; idx < gf.nc; idx += gridDim.x * kThreads) {
+        const Wave w = wave(gf, idx);
+        const int k1 = (int)w.k1, k2 = (int)w.k2, k3 = (int)w.k3;
+        float2 rr[3] = {r[idx], r[ncf + idx], r[2 * ncf + idx]};
+        float2 zz[3];
+        if (2 * abs(k1) < gc.n1 && 2 * abs(k2) < gc.n2 && 2 * k3 < gc.n3) {
+            const int c1 = k1 >= 0 ? k1 : k1 + gc.n1, c2 = k2 >= 0 ? k2 : k2 + gc.n2;
+            const long long ci = ((long long)c1 * gc.n2 + c2) * gc.m3 + k3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) zz[c] = y[c * ncc + ci];
+        } else {
+            zz[0] = rr[0]; zz[1] = rr[1]; zz[2] = rr[2];
+            if (project) leray3(w, zz[0], zz[1], zz[2]);
+            const float m = mprec(reg_symbol(w, kind), beta, shift);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) zz[c] = scale2(zz[c], m);
+        }
+        float sdot = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            z[c * ncf + idx] = zz[c];
+            sdot = fmaf(rr[c].x, zz[c].x, sdot);
+            sdot = fmaf(rr[c].y, zz[c].y, sdot);
+        }
+        acc[0] += (double)(w.herm * sdot);
+    }
+    store_partials<1>(acc, partials);
+}
+
 }  // namespace
 
 cudaError_t launch_sp_init(const Dims& g, const float2* gh, float2* r, float2* s, float2* p,
@@ -454,6 +513,21 @@ cudaError_t launch_sp_normalise(const Dims& g, const float2* in, float2* out, in
     const int nb = (g.nc + kThreads - 1) / kThreads;
     k_sp_normalise<<<nb < 152 * 8 ? nb : 152 * 8, kThreads, 0, st>>>(g, in, out, project,
                                                                      1.0f / (float)g.n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_restrict(const Dims& gf, const Dims& gc, const float2* in, float2* out,
+                               float scale, cudaStream_t st) {
+    const int nb = (gc.nc + kThreads - 1) / kThreads;
+    k_sp_restrict<<<nb < 152 * 8 ? nb : 152 * 8, kThreads, 0, st>>>(gf, gc, in, out, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_twolevel(const Dims& gf, const Dims& gc, const float2* r, const float2* y,
+                               float2* z, double beta, double shift, int kind, int project,
+                               double* partials, int nblk, cudaStream_t st) {
+    k_sp_twolevel<<<nblk, kThreads, 0, st>>>(gf, gc, r, y, z, (float)beta, (float)shift, kind,
+                                             project, partials);
     return cudaGetLastError();
 }
 

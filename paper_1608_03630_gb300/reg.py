@@ -35,7 +35,8 @@ class SolveOpts(ctypes.Structure):
                 ('armijo_max', ctypes.c_int), ('use_graph', ctypes.c_int),
                 ('verbose', ctypes.c_int), ('gnorm_ref', ctypes.c_double),
                 ('precond_shift', ctypes.c_double), ('beta_start', ctypes.c_double),
-                ('beta_factor', ctypes.c_double)]
+                ('beta_factor', ctypes.c_double), ('coarse_factor', ctypes.c_int),
+                ('coarse_tol', ctypes.c_double), ('coarse_max', ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -46,7 +47,8 @@ class SolveStats(ctypes.Structure):
                 ('J0', ctypes.c_double), ('J', ctypes.c_double),
                 ('gnorm0', ctypes.c_double), ('gnorm', ctypes.c_double),
                 ('gnorm_rel', ctypes.c_double), ('mismatch_rel', ctypes.c_double),
-                ('ms_total', ctypes.c_double), ('stages', ctypes.c_int)]
+                ('ms_total', ctypes.c_double), ('stages', ctypes.c_int),
+                ('coarse_matvecs', ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -85,6 +87,8 @@ _SIGS = {
     'reg_hessian_matvec_spectral': [_P, _P, _P],
     'reg_solve_opts_default': [ctypes.POINTER(SolveOpts)],
     'reg_set_beta': [_P, _D],
+    'reg_twolevel_setup': [_P, _I, _P],
+    'reg_twolevel_apply': [_P, _P, _P, _D, _I, ctypes.POINTER(_I)],
     'reg_solve': [_P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)],
     'reg_solve_host': [_P, _P, _P, _I, _P, ctypes.POINTER(SolveOpts),
                        ctypes.POINTER(SolveStats)],
@@ -314,6 +318,19 @@ class Registration:
         self._call('reg_hessian_matvec_spectral', self._cptr(vt_hat, 'vt_hat'),
                    self._cptr(o, 'Hvt_hat'))
         return o
+
+    def twolevel_setup(self, factor, v_hat):
+        """Coarse grid n / factor, restricted images, coarse Hessian at the
+        restriction of v_hat (reg_twolevel_setup)."""
+        self._call('reg_twolevel_setup', int(factor), self._cptr(v_hat, 'v_hat'))
+
+    def twolevel_apply(self, r_hat, inner_tol=0.1, inner_max=10, out=None):
+        """(z_hat, inner iterations) = two-level M^-1 r_hat (reg_twolevel_apply)."""
+        o = torch.empty(self.sshape, device='cuda', dtype=torch.complex64) if out is None else out
+        it = ctypes.c_int()
+        self._call('reg_twolevel_apply', self._cptr(r_hat, 'r_hat'), self._cptr(o, 'z_hat'),
+                   float(inner_tol), int(inner_max), ctypes.byref(it))
+        return o, it.value
 
     def precond(self, r, out=None):
         o = self._new(self.vshape) if out is None else out
