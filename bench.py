@@ -6,15 +6,18 @@ initial velocity (input images resampled to 64^3, prediction band-limited and
 resampled to 256^3), then the inexact Gauss-Newton-Krylov solve (every step
 of the path: semi-Lagrangian points, transports, spectral operators,
 gradient, Hessian matvecs, preconditioner, PCG, Armijo) in mixed precision
-(bf16 images, FP32 fields, interpolation and FFTs, FP64 reductions) to
-||g|| <= 1e-2 ||g(v = 0)||.  --init zero --precision fp32 is
-the plain FP32 solver from v = 0; every other form is timed once after the
-main measurement ("arms").  Inputs are resident in HBM when the timed region
+(bf16 images, FP32 fields, interpolation and FFTs, FP64 reductions), its
+Newton steps by flexible PCG with the two-level preconditioner (coarse grid
+n/4), to ||g|| <= 1e-2 ||g(v = 0)||.  --init zero --precision fp32
+--precond spectral is the paper's plain solver from v = 0 (FP32); every
+other form is timed once after the main measurement ("arms").  Inputs are resident in HBM when the timed region
 starts; the working set (several GB) is far larger than the 129 MB L2, so no
 flush is needed between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--init learned|zero] [--precision mixed_bf16|fp32]
+                    [--precond twolevel|spectral] [--coarse-factor F]
+                    [--workload phantom256|batched|beta_sweep]
 
 Prints one JSON line.  Two timed regions of K steps each: the first, as a
 user runs the solve (each Newton step's PCG one device-controlled CUDA
@@ -145,6 +148,45 @@ def max_over_ranks(value, world):
     return float(t.item())
 
 
+def partition_pairs(costs, world):
+    """Independent pairs to ranks by cost (longest processing time first:
+    each pair, largest first, to the least loaded rank).  Returns, per rank,
+    the pair indices in ascending order.  The most loaded rank carries at
+    most sum(costs) / world + max(costs)."""
+    loads = [0.0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(costs)), key=lambda i: (-costs[i], i)):
+        r = min(range(world), key=lambda r: (loads[r], r))
+        loads[r] += costs[i]
+        out[r].append(i)
+    return [sorted(x) for x in out]
+
+
+def merge_rank_results(parts, npairs):
+    """Per-pair results gathered from the ranks ([(indices, results), ...])
+    back in pair order; every pair must appear exactly once."""
+    merged = [None] * npairs
+    for idx, res in parts:
+        for i, r in zip(idx, res):
+            if merged[i] is not None:
+                raise ValueError('pair %d solved twice' % i)
+            merged[i] = r
+    missing = [i for i, r in enumerate(merged) if r is None]
+    if missing:
+        raise ValueError('pairs %s not solved' % missing)
+    return merged
+
+
+def gather_objects(obj, world):
+    """Every rank's object on every rank (host-side statistics only)."""
+    if world <= 1:
+        return [obj]
+    import torch.distributed as dist
+    out = [None] * world
+    dist.all_gather_object(out, obj)
+    return out
+
+
 def dist_env():
     world = int(os.environ.get('WORLD_SIZE', '1'))
     rank = int(os.environ.get('RANK', '0'))
@@ -152,13 +194,37 @@ def dist_env():
     return world, rank, local
 
 
-def cpu_oracle_sample(precision_note, counts):
-    """Oracle timing on the host cores: one gradient, one Hessian matvec and
-    one objective at 64^3 (nt = 8, same phantom recipe), scaled to 256^3 by
-    grid points (x64) and combined with the operation counts of the GPU solve."""
+def host_cpu():
+    """(logical cores, CPU model) of this host."""
+    model = None
+    try:
+        with open('/proc/cpuinfo') as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith('model name') or low.startswith('cpu part') and model is None:
+                    model = line.split(':', 1)[1].strip()
+                    if low.startswith('model name'):
+                        break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(['lscpu'], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.lower().startswith('model name'):
+                    model = line.split(':', 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return os.cpu_count() or 1, model or 'unknown'
+
+
+def _oracle_ops(shape):
+    """Seconds of one oracle gradient, Hessian matvec and objective at
+    `shape` (the phantom recipe, nt = 8, H2, beta = 1e-3); one process, one
+    core (the NumPy oracle runs single-threaded)."""
     from oracle import problem as opr
     from paper_1608_03630_gb300 import synth
-    shape = (64, 64, 64)
     rho_T, rho_R, _ = synth.phantom_problem(shape, SEED)
     P = opr.Problem(rho_T, rho_R, NT, BETA, KIND, False, presmooth=True)
     v = np.zeros((3,) + shape)
@@ -166,14 +232,48 @@ def cpu_oracle_sample(precision_note, counts):
     t0 = time.perf_counter(); P.gradient(v); tg = time.perf_counter() - t0
     t0 = time.perf_counter(); P.hessian_matvec(w); tm = time.perf_counter() - t0
     t0 = time.perf_counter(); P.objective(0.1 * w); to = time.perf_counter() - t0
+    return tg, tm, to
+
+
+def cpu_oracle_sample(precision_note, counts):
+    """Oracle timing on the host cores: one gradient, one Hessian matvec and
+    one objective at 64^3 (nt = 8, same phantom recipe) on one core, scaled to
+    256^3 by grid points (x64) and combined with the operation counts of the
+    GPU solve (coarse-grid matvecs of the two-level preconditioner by their
+    share of the points).  All cores: the same sample in one process per
+    core at once, the solve time divided by the processes (the throughput of
+    the box running independent oracle solves)."""
+    import multiprocessing as mp
+    shape = (64, 64, 64)
+    tg, tm, to = _oracle_ops(shape)
     scale = (SHAPE[0] * SHAPE[1] * SHAPE[2]) / float(64 ** 3)
-    est = scale * (counts['gradient_evals'] * tg + counts['matvecs'] * tm +
-                   counts['objective_evals'] * to)
+
+    def solve_time(tg, tm, to):
+        return scale * (counts['gradient_evals'] * tg + counts['objective_evals'] * to +
+                        (counts['matvecs'] + counts['coarse_matvecs'] *
+                         counts['coarse_points_ratio']) * tm)
+
+    est = solve_time(tg, tm, to)
+    cores, model = host_cpu()
+    procs = max(1, min(cores, 64))
+    t0 = time.perf_counter()
+    with mp.get_context('spawn').Pool(procs) as pool:
+        res = pool.map(_oracle_ops, [shape] * procs)
+    wall = time.perf_counter() - t0
+    # each process timed its own operations while all of them ran
+    all_cores = float(np.mean([solve_time(*r) for r in res])) / procs
     return {'value': est, 'unit': UNIT, 'cores': 1, 'kind': 'oracle',
+            'host': {'nproc': cores, 'cpu_model': model},
+            'all_cores': {'value': all_cores, 'unit': UNIT, 'cores': procs,
+                          'sample': '%d concurrent processes of the same 64^3 sample (%.1f s '
+                                    'wall), each scaled as above; mean solve time / processes'
+                                    % (procs, wall)},
             'sample': ('FP64 NumPy oracle at 64^3 nt=8 (gradient %.2fs, matvec %.2fs, objective '
                        '%.2fs on 1 host core), scaled x%d by grid points and by the GPU solve\'s '
-                       'counts (%d gradients, %d matvecs, %d objectives); %s'
+                       'counts (%d gradients, %d matvecs, %d coarse matvecs x %.4f, %d '
+                       'objectives); %s'
                        % (tg, tm, to, int(scale), counts['gradient_evals'], counts['matvecs'],
+                          counts['coarse_matvecs'], counts['coarse_points_ratio'],
                           counts['objective_evals'], precision_note))}
 
 
@@ -238,7 +338,8 @@ def gpu_bench(args):
     __graft_entry__.build()
     from paper_1608_03630_gb300 import learned_init, reg
 
-    rho_T, rho_R = make_inputs()
+    # every rank registers its own pair (independent problems; no collective)
+    rho_T, rho_R = make_inputs(seed=SEED + 7 * rank)
     n = SHAPE[0] * SHAPE[1] * SHAPE[2]
     learned = args.init == 'learned'
     stream = torch.cuda.Stream()
@@ -250,21 +351,25 @@ def gpu_bench(args):
         R = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=args.precision,
                              stream=stream)
 
-        def solve_from_images(ctx, init):
+        def solve_from_images(ctx, init, precond):
             """One registration from images on the device: the network's
             prediction for the learned guess, then the solve to
-            ||g|| <= 1e-2 ||g(0)||."""
+            ||g|| <= 1e-2 ||g(0)||, preconditioned by the inverse
+            regularisation operator ('spectral', the paper's) or the
+            two-level coarse-grid operator ('twolevel')."""
             ctx.set_images(dT, dR, presmooth=True)
+            pc = ({'coarse_factor': args.coarse_factor, 'coarse_tol': 0.1, 'coarse_max': 20}
+                  if precond == 'twolevel' else {})
             if init == 'learned':
                 v.copy_(learned_init.predict(net, info['scale'], dT, dR, SHAPE[0], info['kc'],
                                              info['alpha'], info['stages'], ctx))
                 # stop at 1e-2 ||g(0)||, ||g(0)|| from its closed form at v = 0
-                return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500, gnorm_ref=-1.0)
+                return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500, gnorm_ref=-1.0, **pc)
             v.zero_()
-            return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500)
+            return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500, **pc)
 
         def step():
-            return solve_from_images(R, args.init)
+            return solve_from_images(R, args.init, args.precond)
 
         for _ in range(args.warmup):
             step()
@@ -308,47 +413,57 @@ def gpu_bench(args):
         hT = torch.from_numpy(rho_T).pin_memory()
         hR = torch.from_numpy(rho_R).pin_memory()
         hv = torch.zeros((3,) + SHAPE).pin_memory()
-        e2e_steps = max(1, min(2, args.steps))
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
+        e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        for _ in range(args.steps):
             dT.copy_(hT, non_blocking=True)
             dR.copy_(hR, non_blocking=True)
-            solve_from_images(R, args.init)
+            solve_from_images(R, args.init, args.precond)
             hv.copy_(v, non_blocking=True)
-            torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e5.record(stream)
+        torch.cuda.synchronize()
+        e2e_s = e4.elapsed_time(e5) / 1e3 / args.steps
 
         # the other forms of the method, the faster of two timed solves each after a warm-up,
         # to the same stopping test (the plain FP32 solver is the target's
         # comparison)
         arms = {}
         ctxs = {args.precision: R}
-        for name, init, prec in (('plain_fp32', 'zero', 'fp32'),
-                                 ('zero_mixed_bf16', 'zero', 'mixed_bf16'),
-                                 ('learned_fp32', 'learned', 'fp32'),
-                                 ('learned_mixed_bf16', 'learned', 'mixed_bf16')):
-            if (init == args.init and prec == args.precision) or (init == 'learned' and not net):
+        for name, init, prec, pcd in (('plain_fp32', 'zero', 'fp32', 'spectral'),
+                                      ('twolevel_fp32', 'zero', 'fp32', 'twolevel'),
+                                      ('zero_mixed_bf16_twolevel', 'zero', 'mixed_bf16',
+                                       'twolevel'),
+                                      ('learned_mixed_bf16_spectral', 'learned', 'mixed_bf16',
+                                       'spectral'),
+                                      ('learned_fp32_twolevel', 'learned', 'fp32', 'twolevel')):
+            if ((init, prec, pcd) == (args.init, args.precision, args.precond) or
+                    (init == 'learned' and not net)):
                 continue
             if prec not in ctxs:
                 ctxs[prec] = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=prec,
                                               stream=stream)
-            solve_from_images(ctxs[prec], init)
+            solve_from_images(ctxs[prec], init, pcd)
             best = None
             for _ in range(2):   # the faster of two timed solves
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                _, st = solve_from_images(ctxs[prec], init)
+                _, st = solve_from_images(ctxs[prec], init, pcd)
                 e1.record(stream)
                 torch.cuda.synchronize()
                 t = e0.elapsed_time(e1) / 1e3
                 best = t if best is None else min(best, t)
-            arms[name] = {'time_to_solution_s': best,
+            arms[name] = {'time_to_solution_s': best, 'precond': pcd,
                           'gn_iters': st['gn_iters'], 'matvecs': st['matvecs'],
+                          'coarse_matvecs': st['coarse_matvecs'],
                           'gnorm_rel': st['gnorm_rel'], 'mismatch_rel': st['mismatch_rel']}
         for c in ctxs.values():
             c.close()
+    batched = None
+    if not args.no_batched:
+        # the batched workload (uneven sizes), its pairs partitioned over the ranks
+        batched = run_batched(args.pairs, max(1, min(args.steps, 2)), world, rank)
 
     if rank != 0:
         if world > 1:
@@ -381,8 +496,11 @@ def gpu_bench(args):
         st = info['stages']
         launches += args.steps * (st * (unet_launches(net.channels) + 3) + (st - 1) * (NT + 2))
     counts = {'gradient_evals': last['gradient_evals'], 'matvecs': last['matvecs'],
-              'objective_evals': last['objective_evals']}
-    form = '%s guess, %s' % (args.init, args.precision)
+              'objective_evals': last['objective_evals'],
+              'coarse_matvecs': last['coarse_matvecs'],
+              'coarse_points_ratio': (1.0 / args.coarse_factor ** 3
+                                      if args.precond == 'twolevel' else 0.0)}
+    form = '%s guess, %s, %s preconditioner' % (args.init, args.precision, args.precond)
     line = {
         'metric': METRIC, 'value': value, 'unit': UNIT, 'n_gpus': world,
         'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': per_step_s * 1e3,
@@ -396,10 +514,16 @@ def gpu_bench(args):
                                if args.precision == 'mixed_bf16' else 'fp32'),
                    'grid': list(SHAPE), 'nt': NT, 'beta': BETA, 'regularisation': KIND,
                    'gtol': '1e-2 of ||g(v=0)||', 'precision': args.precision,
-                   'parallelism': 'replicas',
+                   'precond': ('two-level: coarse grid n/%d Gauss-Newton Hessian (inner PCG '
+                               'to 0.1, <= 20 iterations) + (beta A)^-1 on the other modes, '
+                               'flexible PCG' % args.coarse_factor
+                               if args.precond == 'twolevel' else '(beta A)^-1 spectral'),
+                   'parallelism': ('independent pairs, one per rank' if world > 1
+                                   else 'one GPU'),
                    'l2': 'inputs larger than L2 (working set > 4 GB), no flush'},
         'solve': {'gn_iters': last['gn_iters'], 'pcg_iters': last['pcg_iters'],
-                  'matvecs': last['matvecs'], 'gnorm_rel': last['gnorm_rel'],
+                  'matvecs': last['matvecs'], 'coarse_matvecs': last['coarse_matvecs'],
+                  'gnorm_rel': last['gnorm_rel'],
                   'mismatch_rel': last['mismatch_rel']},
         'arms': arms,
         'speedup_vs_plain_fp32': (arms['plain_fp32']['time_to_solution_s'] / value
@@ -418,6 +542,8 @@ def gpu_bench(args):
         'e2e': {'value': e2e_s, 'unit': UNIT, 'h2d_bytes_per_step': 4 * n * 2,
                 'd2h_bytes_per_step': 12 * n},
     }
+    if batched is not None:
+        line['batched'] = batched
     if world == 1 and not args.no_cpu_baseline:
         line['cpu_baseline'] = cpu_oracle_sample(form, counts)
     print(json.dumps(line), flush=True)
@@ -447,29 +573,40 @@ def profile_matvec(n, nt, count, precision):
     R.close()
 
 
-def batched_bench(args):
-    """Independent phantom pairs of uneven sizes solved as one batch: 48 pairs,
-    sizes drawn uniformly from {64, 96, 128, 160, 192}^3 (default_rng(4999)),
-    phantom seeds 4000 + 3 i, nt = 4, H2, beta = 1e-3, FP32.  Reports pairs/s
-    and the per-pair latency percentiles (submission to stopping test)."""
+BATCH_SIZES = (64, 96, 128, 160, 192)
+
+
+def batch_workload(npairs):
+    """The batched workload: pair i of `npairs` has the grid n_i^3, n_i drawn
+    uniformly from {64, 96, 128, 160, 192} (default_rng(4999)), phantom seed
+    4000 + 3 i, nt = 4, H2, beta = 1e-3, FP32."""
+    rng = np.random.default_rng(4999)
+    return [(int(n),) * 3 for n in rng.choice(BATCH_SIZES, size=npairs)]
+
+
+def run_batched(npairs, steps, world=1, rank=0, one_graph=True):
+    """Solve this rank's share of the batch (pairs assigned by cost n^3 nt,
+    no collective on the data path), `steps` timed batch solves after one
+    warm-up; returns the whole job's figures (max wall time over ranks,
+    statistics gathered on the host)."""
     import torch
 
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_1608_03630_gb300 import reg, synth
-    rng = np.random.default_rng(4999)
-    sizes = rng.choice([64, 96, 128, 160, 192], size=args.pairs)
-    shapes = [(int(n),) * 3 for n in sizes]
+    shapes = batch_workload(npairs)
+    costs = [float(s[0] * s[1] * s[2] * 4) for s in shapes]
+    parts = partition_pairs(costs, world)
+    mine = parts[rank]
     T, Rr = [], []
-    for i, s in enumerate(shapes):
-        rt, rr, _ = synth.phantom_problem(s, 4000 + 3 * i)
+    for i in mine:
+        rt, rr, _ = synth.phantom_problem(shapes[i], 4000 + 3 * i)
         T.append(torch.from_numpy(rt.astype(np.float32)).cuda())
         Rr.append(torch.from_numpy(rr.astype(np.float32)).cuda())
-    B = reg.Batch(shapes, 4, BETA, KIND)
-    vs = [torch.zeros((3,) + s, device='cuda') for s in shapes]
+    B = reg.Batch([shapes[i] for i in mine], 4, BETA, KIND)
+    B.set_mode(one_graph)
+    vs = [torch.zeros((3,) + shapes[i], device='cuda') for i in mine]
     B.solve(vs, T, Rr, autotune=True)          # warm-up: plans, graphs, tile cache
     times, lats, last = [], [], None
-    for _ in range(args.steps):
+    for _ in range(steps):
         for v in vs:
             v.zero_()
         torch.cuda.synchronize()
@@ -477,20 +614,53 @@ def batched_bench(args):
         st, stats, lat = B.solve(vs, T, Rr, autotune=True)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
-        lats += lat
+        lats.append(lat)
         last = stats
+    graphs = B.graphs_launched()
     B.close()
-    wall = float(np.mean(times))
-    line = {'metric': 'batched registration throughput', 'value': args.pairs / wall,
-            'unit': 'pairs/s', 'n_gpus': 1, 'steps': args.steps, 'higher_is_better': True,
-            'latency_ms': {'p50': float(np.percentile(lats, 50)),
-                           'p99': float(np.percentile(lats, 99))},
-            'config': {'workload': '%d phantom pairs, sizes {64..192}^3, nt=4, H2 beta=1e-3'
-                       % args.pairs, 'sizes': [int(x) for x in sizes]},
-            'matvecs_total': int(sum(s['matvecs'] for s in last)),
-            'gn_iters_total': int(sum(s['gn_iters'] for s in last)),
-            'gnorm_rel_max': float(max(s['gnorm_rel'] for s in last))}
-    print(json.dumps(line), flush=True)
+    wall = max_over_ranks(float(np.mean(times)), world)
+    gathered = gather_objects((mine, [dict(s, latency_ms=float(np.mean([l[k] for l in lats])))
+                                      for k, s in enumerate(last)]), world)
+    per_pair = merge_rank_results(gathered, npairs)
+    lat_all = [p['latency_ms'] for p in per_pair]
+    loads = [sum(costs[i] for i in part) for part in parts]
+    return {'value': npairs / wall, 'unit': 'pairs/s', 'wall_s': wall,
+            'latency_ms': {'p50': float(np.percentile(lat_all, 50)),
+                           'p99': float(np.percentile(lat_all, 99)),
+                           'kind': 'service time: batch start to the pair\'s stopping test'},
+            'mode': 'one PCG graph per lockstep Newton step' if one_graph else 'worker threads',
+            'pcg_graphs_per_solve': graphs,
+            'workload': '%d phantom pairs, sizes {64..192}^3, nt=4, H2 beta=1e-3, fp32' % npairs,
+            'partition': {'ranks': world, 'pairs_per_rank': [len(p) for p in parts],
+                          'load_imbalance': max(loads) / (sum(loads) / world)},
+            'matvecs_total': int(sum(p['matvecs'] for p in per_pair)),
+            'gn_iters_total': int(sum(p['gn_iters'] for p in per_pair)),
+            'gnorm_rel_max': float(max(p['gnorm_rel'] for p in per_pair)),
+            'timing': 'host clock around each synchronous batch solve (the pairs run on '
+                      'their own streams), mean of the timed solves'}
+
+
+def batched_bench(args):
+    """The batched workload alone: one JSON line (pairs/s, whole job)."""
+    import torch
+
+    import __graft_entry__
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl')
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    res = run_batched(args.pairs, args.steps, world, rank, not args.batch_threads)
+    if rank == 0:
+        line = {'metric': 'batched registration throughput', 'value': res['value'],
+                'unit': 'pairs/s', 'n_gpus': world, 'steps': args.steps,
+                'higher_is_better': True, 'scaling': 'strong',
+                'config': {'workload': res['workload']}, 'batched': res}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 def beta_sweep(args):
@@ -564,6 +734,9 @@ def main():
     ap.add_argument('--precision', default='mixed_bf16', choices=['fp32', 'mixed_bf16'])
     ap.add_argument('--init', default='learned', choices=['learned', 'zero'],
                     help='initial velocity: the trained U-Net prediction or v = 0')
+    ap.add_argument('--precond', default='twolevel', choices=['twolevel', 'spectral'],
+                    help='two-level coarse-grid preconditioner or the paper\'s (beta A)^-1')
+    ap.add_argument('--coarse-factor', type=int, default=4)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='phantom256',
                     choices=['phantom256', 'batched', 'beta_sweep'])
@@ -571,6 +744,11 @@ def main():
     ap.add_argument('--betas', type=float, nargs='+', default=[1e-1, 1e-2, 1e-3, 1e-4, 1e-5])
     ap.add_argument('--coarse-factors', type=int, nargs='*', default=[2, 4])
     ap.add_argument('--pairs', type=int, default=48)
+    ap.add_argument('--batch-threads', action='store_true',
+                    help='batched workload: whole solves on worker threads instead of one '
+                         'PCG graph per lockstep Newton step')
+    ap.add_argument('--no-batched', action='store_true',
+                    help='leave the batched workload out of the main bench line')
     ap.add_argument('--profile-matvec', type=int, default=0, metavar='N',
                     help='run one gradient and two matvecs at N^3 (nt = 4) for ncu, then exit')
     args = ap.parse_args()

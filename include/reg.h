@@ -397,20 +397,38 @@ int reg_autotune(reg_ctx* ctx, int* k, int* wy);
 /* Independent registrations of image pairs of uneven sizes solved together
  * (one GPU).  Pair i has grid dims[3i..3i+2]; all share nt, beta, reg_kind,
  * incompressible and precision (REG_FP32 / REG_MIXED_BF16).  Each pair gets
- * its own context and non-blocking stream; worker host threads take pairs
- * largest first and run their solves concurrently, so the kernels of small
- * pairs overlap on the GPU. */
+ * its own context (cuFFT plans of its size) and non-blocking stream.
+ * Modes (reg_batch_set_mode):
+ *  REG_BATCH_ONE_GRAPH (default): the pairs take their Newton steps in
+ *      lockstep.  Gradients and line searches run on host worker threads,
+ *      each pair on its stream; the PCG solves of one Newton step of every
+ *      pair still iterating are ONE CUDA graph, a device-controlled
+ *      while-loop per pair side by side, each with its pair's scalars on the
+ *      device and its own stopping test (a pair whose test is met stops
+ *      while the others go on).  The graph is kept across steps and calls
+ *      while the pairs' captured kernels stay the same.  Plain solver
+ *      options only (no continuation, no two-level preconditioner:
+ *      REG_EINVAL).
+ *  REG_BATCH_THREADS: worker threads take whole solves largest first and run
+ *      them concurrently, each with its own per-step PCG graph. */
+enum { REG_BATCH_ONE_GRAPH = 0, REG_BATCH_THREADS = 1 };
 typedef struct reg_batch reg_batch;
 int reg_batch_create(int npairs, const int* dims, int nt, double beta, int reg_kind,
                      int incompressible, int precision, reg_batch** out);
 int reg_batch_destroy(reg_batch* batch);
+int reg_batch_set_mode(reg_batch* batch, int mode);
+/* PCG graphs launched by the last reg_batch_solve in REG_BATCH_ONE_GRAPH
+ * mode (one per lockstep Newton step with a pair still iterating). */
+int reg_batch_graphs_launched(const reg_batch* batch, int* count);
 
 /* Solve every pair: v_inout[i] (device, [3 n_i]) is pair i's initial guess
  * and solution, rho_T[i], rho_R[i] its images (device, [n_i]).  autotune != 0
  * runs reg_autotune on each pair first (cached per grid size).  Per pair
- * (arrays of npairs, each may be NULL): stats, latency_ms (from the call's
- * start until that pair's stopping test), status_out (REG_OK / REG_EMAXITER
- * / error).  Returns the first hard error, else REG_OK. */
+ * (arrays of npairs, each may be NULL): stats, latency_ms (the pair's service
+ * time: from the start of its work -- the call's start in lockstep mode,
+ * its dequeue in threads mode -- until its stopping test), status_out
+ * (REG_OK / REG_EMAXITER / error).  Returns the first hard error, else
+ * REG_OK. */
 int reg_batch_solve(reg_batch* batch, float* const* v_inout, const float* const* rho_T,
                     const float* const* rho_R, int presmooth, int autotune,
                     const reg_solve_opts* opts, reg_solve_stats* stats, double* latency_ms,
@@ -509,7 +527,8 @@ typedef struct {
  * counters. */
 int reg_set_timing(reg_ctx* ctx, int on);
 
-/* Synchronise the stream and return the accumulated per-phase figures. */
+/* Synchronise the stream and return the accumulated per-phase figures
+ * (including the coarse grid's work of the two-level preconditioner). */
 int reg_get_timing(reg_ctx* ctx, reg_timing* out);
 
 #ifdef __cplusplus

@@ -1,13 +1,17 @@
 // Batched registration of independent image pairs of uneven sizes, and the
 // interpolation-tile autotuner.
 //
-// Every pair owns a context and a non-blocking CUDA stream; worker threads
-// take pairs from a queue ordered by cost (grid points x time steps, largest
-// first) and run the pair's solve on its stream, so the kernels of small
-// pairs overlap on the GPU.  Each pair's PCG iteration is one CUDA graph
-// replayed until its own stopping test (solver.cu).  The autotuner times the
-// interpolation kernels of a linearised context for a few tile shapes and
-// keeps the fastest; results are cached per (grid, halo) for the process.
+// Every pair owns a context and a non-blocking CUDA stream.  Default mode
+// (REG_BATCH_ONE_GRAPH): the pairs advance in lockstep Newton steps; the
+// gradients and line searches run on host worker threads, each pair on its
+// stream, and the PCG solves of a Newton step of every active pair are one
+// CUDA graph holding one device-controlled while-loop per pair, each ending
+// at its own stopping test (solver.cu, batch_solve_graph).  REG_BATCH_THREADS:
+// worker threads take whole solves from a queue ordered by cost (grid points
+// x time steps, largest first), each solve with its own device-controlled PCG
+// graph per Newton step.  The autotuner times the interpolation kernels of a
+// linearised context for a few tile shapes and keeps the fastest; results are
+// cached per (grid, halo) for the process.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -26,6 +30,10 @@ struct reg_batch {
     std::vector<reg_ctx*> ctx;
     std::vector<cudaStream_t> streams;
     int workers;
+    int mode;                      // REG_BATCH_ONE_GRAPH or REG_BATCH_THREADS
+    cudaStream_t launch;           // the one-graph mode's launch stream
+    reg::BatchGraphCache cache;
+    int graphs_launched;
     std::string err;
 };
 
@@ -120,7 +128,15 @@ int reg_batch_create(int npairs, const int* dims, int nt, double beta, int reg_k
     reg_batch* b = new (std::nothrow) reg_batch();
     if (!b) return REG_ENOMEM;
     b->workers = std::min(npairs, 8);
+    b->mode = REG_BATCH_ONE_GRAPH;
+    b->launch = nullptr;
+    b->graphs_launched = 0;
     int status = REG_OK;
+    if (cudaStreamCreateWithFlags(&b->launch, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete b;
+        return REG_ECUDA;
+    }
     for (int i = 0; i < npairs && status == REG_OK; ++i) {
         reg_ctx* c = nullptr;
         status = reg_create(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], nt, beta, reg_kind,
@@ -140,6 +156,7 @@ int reg_batch_create(int npairs, const int* dims, int nt, double beta, int reg_k
     if (status != REG_OK) {
         for (auto c : b->ctx) reg_destroy(c);
         for (auto s : b->streams) cudaStreamDestroy(s);
+        cudaStreamDestroy(b->launch);
         delete b;
         return status;
     }
@@ -149,9 +166,24 @@ int reg_batch_create(int npairs, const int* dims, int nt, double beta, int reg_k
 
 int reg_batch_destroy(reg_batch* b) {
     if (!b) return REG_OK;
+    if (b->launch) cudaStreamSynchronize(b->launch);
+    if (b->cache.exec) cudaGraphExecDestroy(b->cache.exec);
     for (auto c : b->ctx) reg_destroy(c);
     for (auto s : b->streams) cudaStreamDestroy(s);
+    if (b->launch) cudaStreamDestroy(b->launch);
     delete b;
+    return REG_OK;
+}
+
+int reg_batch_set_mode(reg_batch* b, int mode) {
+    if (!b || (mode != REG_BATCH_ONE_GRAPH && mode != REG_BATCH_THREADS)) return REG_EINVAL;
+    b->mode = mode;
+    return REG_OK;
+}
+
+int reg_batch_graphs_launched(const reg_batch* b, int* count) {
+    if (!b || !count) return REG_EINVAL;
+    *count = b->graphs_launched;
     return REG_OK;
 }
 
@@ -161,6 +193,12 @@ int reg_batch_solve(reg_batch* b, float* const* v_inout, const float* const* rho
                     int* status_out) {
     if (!b || !v_inout || !rho_T || !rho_R) return REG_EINVAL;
     const int np = (int)b->ctx.size();
+    if (b->mode == REG_BATCH_ONE_GRAPH) {
+        b->graphs_launched = 0;
+        return batch_solve_graph(b->ctx, v_inout, rho_T, rho_R, presmooth, autotune, opts, stats,
+                                 latency_ms, status_out, b->workers, b->launch, &b->cache,
+                                 &b->graphs_launched);
+    }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return REG_ECUDA;
     // cost order, largest first
@@ -175,13 +213,13 @@ int reg_batch_solve(reg_batch* b, float* const* v_inout, const float* const* rho
     std::vector<int> st(np, REG_OK);
     std::vector<reg_solve_stats> local(np);
     std::vector<double> lat(np, 0.0);
-    const auto t0 = std::chrono::steady_clock::now();
     auto work = [&]() {
         cudaSetDevice(dev);
         for (;;) {
             const int q = next.fetch_add(1);
             if (q >= np) break;
             const int i = order[q];
+            const auto t_start = std::chrono::steady_clock::now();
             reg_ctx* c = b->ctx[i];
             int s = reg_set_images(c, rho_T[i], rho_R[i], presmooth);
             if (s == REG_OK && autotune) {
@@ -200,7 +238,8 @@ int reg_batch_solve(reg_batch* b, float* const* v_inout, const float* const* rho
             }
             cudaStreamSynchronize(c->stream);
             st[i] = s;
-            lat[i] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+            lat[i] = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                               t_start)
                          .count();
         }
     };

@@ -1016,6 +1016,7 @@ int reg_get_tile(const reg_ctx* c, int* k, int* wy) {
 
 int reg_set_timing(reg_ctx* c, int on) {
     CHECK_CTX(c);
+    if (c->coarse) REG_TRY(reg_set_timing(c->coarse, on));
     REG_CK(c, cudaStreamSynchronize(c->stream));
     for (auto& p : c->pending) {
         c->free_events.push_back(p.a);
@@ -1042,6 +1043,15 @@ int reg_get_timing(reg_ctx* c, reg_timing* out) {
     }
     c->pending.clear();
     *out = c->acc;
+    if (c->coarse) {   // the two-level preconditioner's coarse-grid work
+        reg_timing k;
+        REG_TRY(reg_get_timing(c->coarse, &k));
+        for (int p = 0; p < REG_NPHASES; ++p) {
+            out->ms[p] += k.ms[p];
+            out->launches[p] += k.launches[p];
+            out->bytes[p] += k.bytes[p];
+        }
+    }
     return REG_OK;
 }
 

@@ -161,6 +161,20 @@ int op_halo(reg_ctx* c, const float* d, int* halo, float scale = 1.f);
 reg::Tile tile_with(const reg_ctx* c, int halo);
 int ensure_solver(reg_ctx* c);
 
+// Batches (solver.cu): the executable graph of one Newton step's PCG loops of
+// all active pairs, kept while the pairs' captured kernels stay the same.
+struct BatchGraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<double> key;
+};
+// Lockstep Gauss-Newton over the pairs (see solver.cu); the per-pair outputs
+// as reg_batch_solve; *graphs_launched = PCG graphs launched (one per step).
+int batch_solve_graph(const std::vector<reg_ctx*>& ctx, float* const* v_io,
+                      const float* const* rho_T, const float* const* rho_R, int presmooth,
+                      int autotune, const reg_solve_opts* opts, reg_solve_stats* stats,
+                      double* latency_ms, int* status_out, int workers, cudaStream_t launch,
+                      BatchGraphCache* cache, int* graphs_launched);
+
 // Device scalar slots.
 enum {
     SC_JMIS = 0, SC_JREG = 1, SC_J = 2, SC_TMP = 3,

@@ -20,11 +20,16 @@
 // host waits once per Newton step.  use_graph = 1: the iteration is a graph
 // replayed by the host, which reads p.Hp and ||r|| after each one.
 // use_graph = 0: plain launches.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <thread>
 #include <utility>
+#include <vector>
 
 #include "ctx.h"
 
@@ -112,45 +117,47 @@ __global__ void k_pcg_control(double* dsc, cudaGraphConditionalHandle h) {
     cudaGraphSetConditional(h, flag == PCG_RUN ? 1u : 0u);
 }
 
+// Add c's PCG loop to `graph` with no dependencies: a while-node whose body
+// is one PCG iteration and its stopping test (k_pcg_control), captured on the
+// context's capture stream.  false when the driver does not take it.
+static bool add_pcg_loop(reg_ctx* c, cudaGraph_t graph) {
+    cudaGraphConditionalHandle h;
+    if (cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+        return false;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) != cudaSuccess) return false;
+    cudaGraph_t body = p.conditional.phGraph_out[0];
+    cudaStream_t user = c->stream;
+    bool ok = bind_stream(c, c->capture_stream) == REG_OK;
+    if (ok && cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        int s = pcg_iteration(c);
+        if (s == REG_OK) {
+            k_pcg_control<<<1, 1, 0, c->stream>>>(c->dsc, h);
+            if (cudaGetLastError() != cudaSuccess) s = REG_ECUDA;
+        }
+        cudaGraph_t captured = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->stream, &captured);
+        ok = s == REG_OK && e == cudaSuccess;
+    } else {
+        ok = false;
+    }
+    if (bind_stream(c, user) != REG_OK) ok = false;
+    return ok;
+}
+
 // The PCG loop as one executable graph (a while-node around the iteration),
 // or nullptr (with the context's error state untouched) when the driver does
 // not take it.
 static cudaGraphExec_t build_pcg_loop(reg_ctx* c) {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphConditionalHandle h;
-    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess &&
-              cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) ==
-                  cudaSuccess;
-    cudaGraph_t body = nullptr;
-    if (ok) {
-        cudaGraphNodeParams p = {};
-        p.type = cudaGraphNodeTypeConditional;
-        p.conditional.handle = h;
-        p.conditional.type = cudaGraphCondTypeWhile;
-        p.conditional.size = 1;
-        cudaGraphNode_t node;
-        ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) == cudaSuccess;
-        if (ok) body = p.conditional.phGraph_out[0];
-    }
-    if (ok) {
-        cudaStream_t user = c->stream;
-        ok = bind_stream(c, c->capture_stream) == REG_OK;
-        if (ok && cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
-                                                cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-            int s = pcg_iteration(c);
-            if (s == REG_OK) {
-                k_pcg_control<<<1, 1, 0, c->stream>>>(c->dsc, h);
-                if (cudaGetLastError() != cudaSuccess) s = REG_ECUDA;
-            }
-            cudaGraph_t captured = nullptr;
-            const cudaError_t e = cudaStreamEndCapture(c->stream, &captured);
-            ok = s == REG_OK && e == cudaSuccess;
-        } else {
-            ok = false;
-        }
-        if (bind_stream(c, user) != REG_OK) ok = false;
-    }
+    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess && add_pcg_loop(c, graph);
     if (ok && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
         exec = nullptr;
         ok = false;
@@ -166,30 +173,63 @@ static cudaGraphExec_t build_pcg_loop(reg_ctx* c) {
     return exec;
 }
 
+// r = -g, s = 0, p = M P r and the initial scalars; res->converged when the
+// initial residual already meets *tol (rel_tol > 0: *tol becomes
+// rel_tol ||P r_0||).
+static int pcg_prologue(reg_ctx* c, double* tol, int verbose, PcgResult* res,
+                        double rel_tol = 0.0) {
+    const int nb = blas_blocks();
+    float2** S = c->ss;
+    res->iters = 0;
+    res->neg_curv = false;
+    res->converged = false;
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 5.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_init(c->g, S[S_G], S[S_R], S[S_S], S[S_P], S[S_PC], c->beta,
+                                 c->pshift, c->kind, c->incompressible, c->partials, nb,
+                                 c->stream));
+    }
+    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
+    REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZ));
+    REG_TRY(finalize_to(c, 2, nb, kTwoPi3, SC_PAP));
+    REG_TRY(read_scalars(c, SC_RZ, 13));
+    if (rel_tol > 0.0) *tol = rel_tol * std::sqrt(c->hsc[SC_RR]);
+    if (verbose > 1)
+        fprintf(stderr, "  pcg 0  rr %.6e  rz %.6e  pap %.6e  tol %.6e\n", c->hsc[SC_RR],
+                c->hsc[SC_RZ], c->hsc[SC_PAP], *tol);
+    if (std::sqrt(c->hsc[SC_RR]) <= *tol) res->converged = true;
+    return REG_OK;
+}
+
+// After a device-controlled PCG loop ran on c->stream: its count and exit
+// flag (waits for the stream); on negative curvature in the first iteration
+// the step becomes the preconditioned steepest-descent direction.
+static int pcg_loop_result(reg_ctx* c, PcgResult* res) {
+    REG_TRY(read_scalars(c, 0, SC_MAXIT + 1));
+    res->iters = (int)c->hsc[SC_IT];
+    const int flag = (int)c->hsc[SC_FLAG];
+    if (flag == PCG_NONFINITE) return fail(c, REG_ENONFINITE, "non-finite value in PCG");
+    res->converged = flag == PCG_CONVERGED;
+    if (flag == PCG_NEGCURV) {
+        res->neg_curv = true;
+        if (res->iters == 1) {
+            float2** S = c->ss;
+            REG_CK(c, launch_sp_direction(c->g, S[S_R], S[S_S], nullptr, c->dsc, SC_ZERO, SC_RZ, 1,
+                                          c->beta, c->pshift, c->kind, c->incompressible,
+                                          c->partials, blas_blocks(), c->stream));
+        }
+    }
+    return REG_OK;
+}
+
 // rel_tol > 0: the tolerance is rel_tol ||P r_0|| instead of tol.
 static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verbose,
                      PcgResult* res, double rel_tol = 0.0) {
     const int nb = blas_blocks();
     const int proj = c->incompressible;
     float2** S = c->ss;
-    res->iters = 0;
-    res->neg_curv = false;
-    res->converged = false;
-    // r = -g, s = 0, p = M P r
-    {
-        Phase ph(c, REG_PH_SPECTRAL, 5.0 * 24.0 * (double)c->g.nc);
-        REG_CK(c, launch_sp_init(c->g, S[S_G], S[S_R], S[S_S], S[S_P], S[S_PC], c->beta,
-                                 c->pshift, c->kind, proj, c->partials, nb, c->stream));
-    }
-    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
-    REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZ));
-    REG_TRY(finalize_to(c, 2, nb, kTwoPi3, SC_PAP));
-    REG_TRY(read_scalars(c, SC_RZ, 13));
-    if (rel_tol > 0.0) tol = rel_tol * std::sqrt(c->hsc[SC_RR]);
-    if (verbose > 1)
-        fprintf(stderr, "  pcg 0  rr %.6e  rz %.6e  pap %.6e  tol %.6e\n", c->hsc[SC_RR],
-                c->hsc[SC_RZ], c->hsc[SC_PAP], tol);
-    if (std::sqrt(c->hsc[SC_RR]) <= tol) { res->converged = true; return REG_OK; }
+    REG_TRY(pcg_prologue(c, &tol, verbose, res, rel_tol));
+    if (res->converged) return REG_OK;
 
     if (use_graph >= 2 && !c->timing && verbose <= 1) {
         // reuse the captured loop while its kernels and launch shapes are
@@ -208,28 +248,11 @@ static int pcg_solve(reg_ctx* c, double tol, int max_it, int use_graph, int verb
         }
         cudaGraphExec_t loop = c->pcg_exec;
         if (loop) {
-            int status = REG_OK;
             k_pcg_setup<<<1, 1, 0, c->stream>>>(c->dsc, tol * tol, max_it);
             cudaError_t e = cudaGetLastError();
             if (e == cudaSuccess) e = cudaGraphLaunch(loop, c->stream);
-            if (e != cudaSuccess) status = fail_cuda(c, e, "PCG loop launch", __LINE__);
-            if (status == REG_OK) status = read_scalars(c, 0, SC_MAXIT + 1);
-            if (status != REG_OK) return status;
-            res->iters = (int)c->hsc[SC_IT];
-            const int flag = (int)c->hsc[SC_FLAG];
-            if (flag == PCG_NONFINITE) return fail(c, REG_ENONFINITE, "non-finite value in PCG");
-            res->converged = flag == PCG_CONVERGED;
-            if (flag == PCG_NEGCURV) {
-                res->neg_curv = true;
-                if (res->iters == 1) {
-                    // first direction: the preconditioned steepest-descent step
-                    e = launch_sp_direction(c->g, S[S_R], S[S_S], nullptr, c->dsc, SC_ZERO, SC_RZ,
-                                            1, c->beta, c->pshift, c->kind, proj, c->partials, nb,
-                                            c->stream);
-                    if (e != cudaSuccess) return fail_cuda(c, e, "launch_sp_direction", __LINE__);
-                }
-            }
-            return REG_OK;
+            if (e != cudaSuccess) return fail_cuda(c, e, "PCG loop launch", __LINE__);
+            return pcg_loop_result(c, res);
         }
     }
 
@@ -346,6 +369,7 @@ static int twolevel_setup(reg_ctx* c, int factor) {
         c->coarse_img_version = -1;
     }
     reg_ctx* k = c->coarse;
+    if (k->timing != c->timing) REG_TRY(child_fail(c, reg_set_timing(k, c->timing ? 1 : 0)));
     REG_TRY(child_fail(c, bind_stream(k, c->stream)));
     REG_TRY(child_fail(c, ensure_solver(k)));
     k->beta = c->beta;
@@ -582,94 +606,333 @@ static int gradient_norm_at_zero(reg_ctx* c, double* g0) {
     return REG_OK;
 }
 
-static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solve_stats* st) {
-    const auto t0 = std::chrono::steady_clock::now();
+// The Gauss-Newton loop in steps, so that the batch driver can interleave the
+// pairs of a batch: begin (initial gradient), per Newton step the PCG
+// tolerance, the PCG solve, then the line search and the new gradient, end.
+struct SolveState {
+    std::chrono::steady_clock::time_point t0;
+    double m0 = 0, g0 = 0, J = 0, gn = 0, jmis = 0;
+    int k = 0;
+    int status = REG_EMAXITER;
+    bool done = false;
+};
+
+static int solve_begin(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solve_stats* st,
+                       SolveState* S) {
+    S->t0 = std::chrono::steady_clock::now();
     const long long n = c->g.n;
-    const int nb = blas_blocks();
-    float2** S = c->ss;
+    float2** V = c->ss;
     // v_hat = F v / n (projected when incompressible)
     REG_TRY(op_fft_r2c(c, v_io, c->spec[0], 3));
     {
         Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
-        REG_CK(c, launch_sp_normalise(c->g, c->spec[0], S[S_V], c->incompressible, c->stream));
+        REG_CK(c, launch_sp_normalise(c->g, c->spec[0], V[S_V], c->incompressible, c->stream));
     }
     // ||rho_T - rho_R|| for the relative mismatch
     REG_CK(c, launch_axpby_out(c->tmp3, c->rho_T, c->rho_R, 1.f, -1.f, n, c->stream));
     REG_TRY(op_inner(c, c->tmp3, c->tmp3, n, SC_TMP));
     REG_TRY(read_scalars(c, SC_TMP, 1));
-    const double m0 = std::sqrt(c->hsc[SC_TMP]);
-
+    S->m0 = std::sqrt(c->hsc[SC_TMP]);
     double gz = 0.0;
     if (o->gnorm_ref < 0.0) REG_TRY(gradient_norm_at_zero(c, &gz));
-    double J, gn;
-    REG_TRY(evaluate_gradient(c, &J, &gn));
+    REG_TRY(evaluate_gradient(c, &S->J, &S->gn));
     st->gradient_evals++;
     // the stop test and the forcing term are relative to ||g_0||: the
     // gradient at the initial guess, or a reference norm (the caller's, or
     // the gradient at v = 0 when the guess is a prediction)
-    const double g0 = o->gnorm_ref > 0.0 ? o->gnorm_ref : (o->gnorm_ref < 0.0 ? gz : gn);
-    st->J0 = J;
-    st->gnorm0 = g0;
-    double jmis = c->hsc[SC_JMIS];
-    int status = REG_EMAXITER;
-    for (int k = 0; k < o->max_gn; ++k) {
-        if (gn <= o->gtol * g0 || g0 == 0.0) { status = REG_OK; break; }
-        const double ratio = gn / g0;
-        const double eta = std::fmin(0.5, o->forcing == 1 ? std::sqrt(ratio) : ratio);
-        PcgResult pr;
-        if (o->coarse_factor >= 2) {
-            REG_TRY(twolevel_linearize(c, S[S_V]));
-            REG_TRY(pcg_solve_twolevel(c, eta * gn, o->max_pcg, o->coarse_tol, o->coarse_max, &pr,
-                                       &st->coarse_matvecs));
-        } else {
-            REG_TRY(pcg_solve(c, eta * gn, o->max_pcg, o->use_graph, o->verbose, &pr));
-        }
-        st->pcg_iters += pr.iters;
-        st->matvecs += pr.iters;
-        st->negative_curvature += pr.neg_curv ? 1 : 0;
-        {
-            Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
-            REG_CK(c, launch_sp_dot(c->g, S[S_G], S[S_S], c->partials, nb, c->stream));
-        }
-        REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_GS));
-        REG_TRY(read_scalars(c, SC_GS, 1));
-        const double slope = c->hsc[SC_GS];
-        double alpha = 1.0, Jt = J;
-        bool accepted = false;
-        for (int m = 0; m < o->armijo_max; ++m) {
-            REG_TRY(evaluate_trial(c, alpha, &Jt));
-            st->objective_evals++;
-            if (std::isfinite(Jt) && Jt <= J + o->armijo_c * alpha * slope) {
-                accepted = true;
-                break;
-            }
-            alpha *= o->armijo_shrink;
-        }
-        if (!accepted) {
-            st->line_search_failed = 1;
-            status = REG_EMAXITER;
+    S->g0 = o->gnorm_ref > 0.0 ? o->gnorm_ref : (o->gnorm_ref < 0.0 ? gz : S->gn);
+    st->J0 = S->J;
+    st->gnorm0 = S->g0;
+    S->jmis = c->hsc[SC_JMIS];
+    return REG_OK;
+}
+
+// True when another Newton step is due; *tol = eta ||g|| (quadratic or
+// square-root forcing).  Marks the solve done (converged or at max_gn).
+static bool solve_step_due(const reg_solve_opts* o, SolveState* S, double* tol) {
+    if (S->done) return false;
+    if (S->gn <= o->gtol * S->g0 || S->g0 == 0.0) {
+        S->status = REG_OK;
+        S->done = true;
+        return false;
+    }
+    if (S->k >= o->max_gn) {
+        S->done = true;
+        return false;
+    }
+    const double ratio = S->gn / S->g0;
+    const double eta = std::fmin(0.5, o->forcing == 1 ? std::sqrt(ratio) : ratio);
+    *tol = eta * S->gn;
+    return true;
+}
+
+// After the PCG solve of step S->k: Armijo line search along s, the gradient
+// at the accepted point.
+static int solve_step_finish(reg_ctx* c, const reg_solve_opts* o, reg_solve_stats* st,
+                             SolveState* S, const PcgResult& pr) {
+    const int nb = blas_blocks();
+    float2** V = c->ss;
+    st->pcg_iters += pr.iters;
+    st->matvecs += pr.iters;
+    st->negative_curvature += pr.neg_curv ? 1 : 0;
+    {
+        Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
+        REG_CK(c, launch_sp_dot(c->g, V[S_G], V[S_S], c->partials, nb, c->stream));
+    }
+    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_GS));
+    REG_TRY(read_scalars(c, SC_GS, 1));
+    const double slope = c->hsc[SC_GS];
+    double alpha = 1.0, Jt = S->J;
+    bool accepted = false;
+    for (int m = 0; m < o->armijo_max; ++m) {
+        REG_TRY(evaluate_trial(c, alpha, &Jt));
+        st->objective_evals++;
+        if (std::isfinite(Jt) && Jt <= S->J + o->armijo_c * alpha * slope) {
+            accepted = true;
             break;
         }
-        std::swap(S[S_V], S[S_VT]);
-        REG_TRY(evaluate_gradient(c, &J, &gn, true));
-        jmis = c->hsc[SC_JMIS];
-        st->gradient_evals++;
-        st->gn_iters = k + 1;
-        if (o->verbose)
-            fprintf(stderr, "GN %3d  J %.6e  |g|/|g0| %.3e  pcg %3d  alpha %.3g%s\n", k + 1, J,
-                    gn / g0, pr.iters, alpha, pr.neg_curv ? "  (negative curvature)" : "");
+        alpha *= o->armijo_shrink;
     }
-    if (status == REG_EMAXITER && (gn <= o->gtol * g0 || g0 == 0.0)) status = REG_OK;
-    REG_TRY(to_physical(c, S[S_V], v_io));
-    st->J = J;
-    st->gnorm = gn;
-    st->gnorm_rel = g0 > 0 ? gn / g0 : 0.0;
-    st->mismatch_rel = m0 > 0 ? std::sqrt(2.0 * jmis) / m0 : 0.0;
+    if (!accepted) {
+        st->line_search_failed = 1;
+        S->status = REG_EMAXITER;
+        S->done = true;
+        return REG_OK;
+    }
+    std::swap(V[S_V], V[S_VT]);
+    REG_TRY(evaluate_gradient(c, &S->J, &S->gn, true));
+    S->jmis = c->hsc[SC_JMIS];
+    st->gradient_evals++;
+    S->k++;
+    st->gn_iters = S->k;
+    if (o->verbose)
+        fprintf(stderr, "GN %3d  J %.6e  |g|/|g0| %.3e  pcg %3d  alpha %.3g%s\n", S->k, S->J,
+                S->gn / S->g0, pr.iters, alpha, pr.neg_curv ? "  (negative curvature)" : "");
+    return REG_OK;
+}
+
+static int solve_end(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solve_stats* st,
+                     SolveState* S) {
+    if (S->status == REG_EMAXITER && (S->gn <= o->gtol * S->g0 || S->g0 == 0.0))
+        S->status = REG_OK;
+    REG_TRY(to_physical(c, c->ss[S_V], v_io));
+    st->J = S->J;
+    st->gnorm = S->gn;
+    st->gnorm_rel = S->g0 > 0 ? S->gn / S->g0 : 0.0;
+    st->mismatch_rel = S->m0 > 0 ? std::sqrt(2.0 * S->jmis) / S->m0 : 0.0;
     REG_CK(c, cudaStreamSynchronize(c->stream));
-    st->ms_total =
-        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    if (status == REG_EMAXITER) fail(c, REG_EMAXITER, "Gauss-Newton stopped before gtol");
-    return status;
+    st->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() -
+                                                             S->t0)
+                       .count();
+    if (S->status == REG_EMAXITER) fail(c, REG_EMAXITER, "Gauss-Newton stopped before gtol");
+    return S->status;
+}
+
+static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solve_stats* st) {
+    SolveState S;
+    REG_TRY(solve_begin(c, v_io, o, st, &S));
+    double tol = 0.0;
+    while (solve_step_due(o, &S, &tol)) {
+        PcgResult pr;
+        if (o->coarse_factor >= 2) {
+            REG_TRY(twolevel_linearize(c, c->ss[S_V]));
+            REG_TRY(pcg_solve_twolevel(c, tol, o->max_pcg, o->coarse_tol, o->coarse_max, &pr,
+                                       &st->coarse_matvecs));
+        } else {
+            REG_TRY(pcg_solve(c, tol, o->max_pcg, o->use_graph, o->verbose, &pr));
+        }
+        REG_TRY(solve_step_finish(c, o, st, &S, pr));
+    }
+    return solve_end(c, v_io, o, st, &S);
+}
+
+// ------------------------------------------------------------ batches
+// Independent pairs advanced in lockstep Newton steps: the gradients and line
+// searches of the active pairs run on host worker threads (each pair on its
+// own stream), and the PCG solves of one Newton step of every active pair are
+// ONE CUDA graph: a while-node per pair, side by side, each running that
+// pair's iterations until its own device-side stopping test.
+
+static void parallel_for(const std::vector<int>& items, int workers, int dev,
+                         const std::function<void(int)>& fn) {
+    if (items.empty()) return;
+    std::atomic<size_t> next(0);
+    auto run = [&]() {
+        cudaSetDevice(dev);
+        for (;;) {
+            const size_t q = next.fetch_add(1);
+            if (q >= items.size()) break;
+            fn(items[q]);
+        }
+    };
+    const int nw = std::max(1, std::min<int>(workers, (int)items.size()));
+    std::vector<std::thread> pool;
+    for (int w = 1; w < nw; ++w) pool.emplace_back(run);
+    run();
+    for (auto& t : pool) t.join();
+}
+
+int batch_solve_graph(const std::vector<reg_ctx*>& ctx, float* const* v_io,
+                      const float* const* rho_T, const float* const* rho_R, int presmooth,
+                      int autotune, const reg_solve_opts* opts, reg_solve_stats* stats,
+                      double* latency_ms, int* status_out, int workers, cudaStream_t launch,
+                      BatchGraphCache* cache, int* graphs_launched) {
+    const int np = (int)ctx.size();
+    reg_solve_opts o;
+    reg_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.beta_start > 0.0 || o.coarse_factor >= 2 || o.max_gn < 0 || o.max_pcg < 1 ||
+        o.armijo_max < 1 || !(o.armijo_shrink > 0.0 && o.armijo_shrink < 1.0) ||
+        !(o.gtol >= 0.0) || !(o.precond_shift >= 0.0) || !std::isfinite(o.gnorm_ref))
+        return REG_EINVAL;   // the batch graph runs the plain solver options
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return REG_ECUDA;
+    std::vector<SolveState> S(np);
+    std::vector<reg_solve_stats> st(np);
+    std::vector<int> status(np, REG_OK), need(np, 0);
+    std::vector<PcgResult> pr(np);
+    std::vector<double> tol(np, 0.0), lat(np, 0.0);
+    std::vector<cudaEvent_t> ev(np, nullptr);
+    cudaEvent_t done_ev = nullptr;
+    for (int i = 0; i < np; ++i) memset(&st[i], 0, sizeof(reg_solve_stats));
+    for (int i = 0; i < np; ++i)
+        if (cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming) != cudaSuccess) return REG_ECUDA;
+    if (cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming) != cudaSuccess) return REG_ECUDA;
+    const auto t0 = std::chrono::steady_clock::now();
+    auto ms_since = [&]() {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+            .count();
+    };
+    // the pair is finished: velocity out, statistics, latency
+    auto finish = [&](int i) {
+        reg_ctx* c = ctx[i];
+        const int s = status[i] != REG_OK ? status[i] : solve_end(c, v_io[i], &o, &st[i], &S[i]);
+        status[i] = s;
+        st[i].stages = 1;
+        lat[i] = ms_since();
+    };
+    std::vector<int> all(np);
+    for (int i = 0; i < np; ++i) all[i] = i;
+    parallel_for(all, workers, dev, [&](int i) {
+        reg_ctx* c = ctx[i];
+        int s = reg_set_images(c, rho_T[i], rho_R[i], presmooth);
+        if (s == REG_OK) s = ensure_solver(c);
+        if (s == REG_OK && autotune) {
+            s = reg_gradient(c, v_io[i], c->sv[3], nullptr);
+            if (s == REG_OK) s = reg_autotune(c, nullptr, nullptr);
+        }
+        c->pshift = o.precond_shift;
+        if (s == REG_OK) s = solve_begin(c, v_io[i], &o, &st[i], &S[i]);
+        if (s != REG_OK) {
+            status[i] = s;
+            S[i].done = true;
+            lat[i] = ms_since();
+        }
+    });
+    int launched = 0;
+    for (;;) {
+        // Newton step due?  PCG prologue (r = -g, p = M P r, first scalars)
+        std::vector<int> active;
+        for (int i = 0; i < np; ++i)
+            if (!S[i].done || status[i] == REG_OK) active.push_back(i);
+        std::vector<int> stepping;
+        for (int i : active) {
+            if (status[i] != REG_OK) continue;
+            if (solve_step_due(&o, &S[i], &tol[i])) stepping.push_back(i);
+        }
+        // pairs that stopped this round: finish them
+        std::vector<int> stopped;
+        for (int i : active)
+            if (status[i] == REG_OK && S[i].done && lat[i] == 0.0) stopped.push_back(i);
+        parallel_for(stopped, workers, dev, finish);
+        if (stepping.empty()) break;
+        parallel_for(stepping, workers, dev, [&](int i) {
+            reg_ctx* c = ctx[i];
+            int s = pcg_prologue(c, &tol[i], 0, &pr[i]);
+            need[i] = 0;
+            if (s == REG_OK && !pr[i].converged) {
+                k_pcg_setup<<<1, 1, 0, c->stream>>>(c->dsc, tol[i] * tol[i], o.max_pcg);
+                cudaError_t e = cudaGetLastError();
+                if (e == cudaSuccess) e = cudaEventRecord(ev[i], c->stream);
+                if (e != cudaSuccess) s = fail_cuda(c, e, "batch PCG set-up", __LINE__);
+                need[i] = 1;
+            }
+            if (s != REG_OK) {
+                status[i] = s;
+                need[i] = 0;
+            }
+        });
+        std::vector<int> loops;
+        for (int i : stepping)
+            if (need[i]) loops.push_back(i);
+        if (!loops.empty()) {
+            // one graph with every pair's PCG loop, rebuilt when a pair's
+            // captured kernels change (halos, tile, Hessian, beta, shift)
+            std::vector<double> key;
+            for (int i : loops) {
+                const reg_ctx* c = ctx[i];
+                key.insert(key.end(), {(double)i, (double)c->halo_fwd, (double)c->halo_adj,
+                                       (double)c->tile.k, (double)c->tile.wy, (double)c->hessian,
+                                       c->beta, c->pshift});
+            }
+            if (cache->exec && cache->key != key) {
+                cudaGraphExecDestroy(cache->exec);
+                cache->exec = nullptr;
+            }
+            if (!cache->exec) {
+                cudaGraph_t graph = nullptr;
+                bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+                for (int i : loops) ok = ok && add_pcg_loop(ctx[i], graph);
+                if (ok && cudaGraphInstantiate(&cache->exec, graph, 0) != cudaSuccess) {
+                    cache->exec = nullptr;
+                    ok = false;
+                }
+                if (graph) cudaGraphDestroy(graph);
+                if (!ok) {
+                    cudaGetLastError();
+                    for (int i : loops) status[i] = REG_ECUDA;
+                    break;
+                }
+                cache->key = key;
+            }
+            bool ok = true;
+            for (int i : loops) ok = ok && cudaStreamWaitEvent(launch, ev[i], 0) == cudaSuccess;
+            ok = ok && cudaGraphLaunch(cache->exec, launch) == cudaSuccess &&
+                 cudaEventRecord(done_ev, launch) == cudaSuccess;
+            for (int i : loops) ok = ok && cudaStreamWaitEvent(ctx[i]->stream, done_ev, 0) == cudaSuccess;
+            if (!ok) {
+                cudaGetLastError();
+                for (int i : loops) status[i] = REG_ECUDA;
+                break;
+            }
+            ++launched;
+        }
+        parallel_for(stepping, workers, dev, [&](int i) {
+            if (status[i] != REG_OK) return;
+            reg_ctx* c = ctx[i];
+            int s = need[i] ? pcg_loop_result(c, &pr[i]) : REG_OK;
+            if (s == REG_OK) s = solve_step_finish(c, &o, &st[i], &S[i], pr[i]);
+            if (s != REG_OK) status[i] = s;
+        });
+        for (int i : stepping)
+            if (status[i] != REG_OK && lat[i] == 0.0) {
+                S[i].done = true;
+                lat[i] = ms_since();
+            }
+    }
+    int first_err = REG_OK;
+    for (int i = 0; i < np; ++i) {
+        if (lat[i] == 0.0) lat[i] = ms_since();
+        if (stats) stats[i] = st[i];
+        if (latency_ms) latency_ms[i] = lat[i];
+        if (status_out) status_out[i] = status[i];
+        if (status[i] != REG_OK && status[i] != REG_EMAXITER && first_err == REG_OK)
+            first_err = status[i];
+    }
+    for (auto e : ev) if (e) cudaEventDestroy(e);
+    if (done_ev) cudaEventDestroy(done_ev);
+    if (graphs_launched) *graphs_launched = launched;
+    return first_err;
 }
 
 }  // namespace reg

@@ -110,6 +110,8 @@ _SIGS = {
     'reg_autotune': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_batch_create': [_I, _P, _I, _D, _I, _I, _I, ctypes.POINTER(_P)],
     'reg_batch_destroy': [_P],
+    'reg_batch_set_mode': [_P, _I],
+    'reg_batch_graphs_launched': [_P, ctypes.POINTER(_I)],
     'reg_batch_solve': [_P, _P, _P, _P, _I, _I, ctypes.POINTER(SolveOpts), _P, _P, _P],
     'reg_spectral_resample': [_P, _P, _I, _P, _P, _P],
     'reg_deformation': [_P, _P, _P],
@@ -473,6 +475,18 @@ class Batch:
                                    ctypes.byref(self._b))
         if s != 0:
             raise RegError(s, lib().reg_last_error(None).decode())
+
+    def set_mode(self, one_graph):
+        """True: lockstep Newton steps, one PCG graph per step for all pairs
+        (default); False: whole solves on worker threads."""
+        s = lib().reg_batch_set_mode(self._b, 0 if one_graph else 1)
+        if s != 0:
+            raise RegError(s, 'reg_batch_set_mode')
+
+    def graphs_launched(self):
+        n = ctypes.c_int()
+        lib().reg_batch_graphs_launched(self._b, ctypes.byref(n))
+        return n.value
 
     def solve(self, vs, rho_Ts, rho_Rs, presmooth=True, autotune=True, **opts):
         """Solve all pairs in place; returns (statuses, stats dicts, latencies ms)."""

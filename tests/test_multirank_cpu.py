@@ -64,3 +64,63 @@ def test_reference_arm_prints_on_rank_zero_only():
                        capture_output=True, text=True, env=env, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ''
+
+
+def _fake_solve(i, shape):
+    """A stand-in for one pair's solve: deterministic statistics of the pair."""
+    return {'matvecs': 3 * i + shape[0] // 32, 'gn_iters': 1 + i % 4, 'pair': i}
+
+
+def _partition_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR='127.0.0.1', MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group('gloo', rank=rank, world_size=world)
+    shapes = bench.batch_workload(48)
+    costs = [float(s[0] ** 3 * 4) for s in shapes]
+    mine = bench.partition_pairs(costs, world)[rank]
+    res = [_fake_solve(i, shapes[i]) for i in mine]
+    merged = bench.merge_rank_results(bench.gather_objects((mine, res), world), len(shapes))
+    dist.barrier()
+    dist.destroy_process_group()
+    q.put((rank, mine, merged))
+
+
+def test_partition_covers_every_pair_once_within_the_load_bound():
+    import bench
+    shapes = bench.batch_workload(48)
+    costs = [float(s[0] ** 3 * 4) for s in shapes]
+    for world in (1, 2, 3, 4, 8):
+        parts = bench.partition_pairs(costs, world)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(48))
+        loads = [sum(costs[i] for i in p) for p in parts]
+        assert max(loads) <= sum(costs) / world + max(costs)
+    with pytest.raises(ValueError):
+        bench.merge_rank_results([([0, 1], ['a', 'b']), ([1], ['c'])], 2)
+    with pytest.raises(ValueError):
+        bench.merge_rank_results([([0], ['a'])], 2)
+
+
+def test_two_gloo_ranks_solve_disjoint_shares_and_merge_like_one_rank():
+    """Each rank solves its share of the batch (no data-path collective);
+    the host gathers the statistics, and the merged result equals the
+    single-rank run pair by pair."""
+    import bench
+    ctx = torch.multiprocessing.get_context('spawn')
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_partition_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted((q.get(timeout=120) for _ in procs), key=lambda x: x[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    shapes = bench.batch_workload(48)
+    single = [_fake_solve(i, s) for i, s in enumerate(shapes)]
+    assert set(out[0][1]).isdisjoint(out[1][1])
+    assert sorted(out[0][1] + out[1][1]) == list(range(48))
+    assert out[0][2] == single and out[1][2] == single
