@@ -198,23 +198,21 @@ def host_cpu():
     """(logical cores, CPU model) of this host."""
     model = None
     try:
-        with open('/proc/cpuinfo') as f:
-            for line in f:
-                low = line.lower()
-                if low.startswith('model name') or low.startswith('cpu part') and model is None:
-                    model = line.split(':', 1)[1].strip()
-                    if low.startswith('model name'):
-                        break
-    except OSError:
+        out = subprocess.run(['lscpu'], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith('model name'):
+                model = line.split(':', 1)[1].strip()
+                break
+    except Exception:
         pass
     if model is None:
         try:
-            out = subprocess.run(['lscpu'], capture_output=True, text=True, timeout=10).stdout
-            for line in out.splitlines():
-                if line.lower().startswith('model name'):
-                    model = line.split(':', 1)[1].strip()
-                    break
-        except Exception:
+            with open('/proc/cpuinfo') as f:
+                for line in f:
+                    if line.lower().startswith('model name'):
+                        model = line.split(':', 1)[1].strip()
+                        break
+        except OSError:
             pass
     return os.cpu_count() or 1, model or 'unknown'
 
@@ -402,6 +400,7 @@ def gpu_bench(args):
         torch.cuda.synchronize()
         phased_ms = ev2.elapsed_time(ev3)
         timing = R.get_timing()
+        coarse_timing = R.get_coarse_timing()
         R.set_timing(False)
         clk = clocks.stop()
         if world > 1:
@@ -488,6 +487,7 @@ def gpu_bench(args):
     # plus the device loop's kernels of the first region (one set-up per
     # Newton step, one stopping-test kernel per PCG iteration)
     launches = sum(int(v['launches']) for k, v in timing.items() if k != 'fft')
+    launches += sum(int(v['launches']) for k, v in coarse_timing.items() if k != 'fft')
     launches += sum(s['gn_iters'] + s['pcg_iters'] for s in stats)
     if learned:
         # per step and prediction stage: the network forward and three
@@ -533,6 +533,8 @@ def gpu_bench(args):
         'interp_gbs': ib / (ims / 1e3) / 1e9 if ims > 0 else None,
         'spectral_gbs': sb / (sms / 1e3) / 1e9 if sms > 0 else None,
         'phase_ms_per_step': {k: v['ms'] / args.steps for k, v in timing.items()},
+        'coarse_phase_ms_per_step': {k: v['ms'] / args.steps for k, v in coarse_timing.items()
+                                     if v['launches']},
         'roofline': {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': peak,
                      'unit': 'GB/s', 'frac': achieved / peak, 'peak_source': peak_kind,
                      'bytes_per_launch': d['bytes'] / max(1, d['launches']),
@@ -725,6 +727,61 @@ def beta_sweep(args):
     print(json.dumps(line), flush=True)
 
 
+def twolevel_sweep(args):
+    """Settings of the two-level preconditioner on the 256^3 phantom (nt = 8,
+    H2, FP32, v = 0, ||g|| <= 1e-2 ||g_0||): coarse factor, coarse time steps,
+    inner tolerance and cap; per setting the faster of two timed solves (CUDA
+    events), Newton steps, fine and coarse matvecs, final gradient and
+    mismatch, at each beta of --betas."""
+    import torch
+
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1608_03630_gb300 import reg
+    n = args.sweep_n
+    shape = (n, n, n)
+    rho_T, rho_R = make_inputs(shape)
+    settings = [(4, 0, 0.1, 20), (4, 4, 0.1, 20), (4, 2, 0.1, 20), (8, 0, 0.1, 20),
+                (8, 4, 0.1, 20), (4, 0, 0.25, 10), (4, 0, 0.05, 40), (4, 4, 0.25, 10),
+                (2, 4, 0.1, 20)]
+    stream = torch.cuda.Stream()
+    rows = []
+    with torch.cuda.stream(stream):
+        dT = torch.from_numpy(rho_T).cuda()
+        dR = torch.from_numpy(rho_R).cuda()
+        v = torch.zeros((3,) + shape, device='cuda')
+        R = reg.Registration(shape, NT, args.betas[0], KIND, False, stream=stream)
+        R.set_images(dT, dR, presmooth=True)
+        for beta in args.betas:
+            R.set_beta(beta)
+            for cf, cnt, ctol, cmax in [(0, 0, 0.0, 1)] + settings:
+                opts = ({'coarse_factor': cf, 'coarse_nt': cnt, 'coarse_tol': ctol,
+                         'coarse_max': cmax} if cf else {})
+                best = None
+                for _ in range(3):   # warm-up, then the faster of two
+                    v.zero_()
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    s, st = R.solve(v, gtol=1e-2, **opts)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    t = e0.elapsed_time(e1) / 1e3
+                    if best is None or t < best[0]:
+                        best = (t, s, st)
+                t, s, st = best
+                row = {'beta': beta, 'coarse_factor': cf, 'coarse_nt': cnt, 'coarse_tol': ctol,
+                       'coarse_max': cmax, 'status': s, 'time_s': t, 'gn_iters': st['gn_iters'],
+                       'matvecs': st['matvecs'], 'coarse_matvecs': st['coarse_matvecs'],
+                       'gnorm_rel': st['gnorm_rel'], 'mismatch_rel': st['mismatch_rel']}
+                rows.append(row)
+                print(json.dumps(row), file=sys.stderr, flush=True)
+        R.close()
+    print(json.dumps({'metric': 'two-level preconditioner settings, 256^3 time to solution',
+                      'workload': 'phantom %d^3 nt=%d H2 fp32 v=0' % (n, NT), 'rows': rows}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -739,7 +796,7 @@ def main():
     ap.add_argument('--coarse-factor', type=int, default=4)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='phantom256',
-                    choices=['phantom256', 'batched', 'beta_sweep'])
+                    choices=['phantom256', 'batched', 'beta_sweep', 'twolevel_sweep'])
     ap.add_argument('--sweep-n', type=int, default=256)
     ap.add_argument('--betas', type=float, nargs='+', default=[1e-1, 1e-2, 1e-3, 1e-4, 1e-5])
     ap.add_argument('--coarse-factors', type=int, nargs='*', default=[2, 4])
@@ -758,6 +815,8 @@ def main():
         batched_bench(args)
     elif args.workload == 'beta_sweep' and args.impl != 'reference':
         beta_sweep(args)
+    elif args.workload == 'twolevel_sweep' and args.impl != 'reference':
+        twolevel_sweep(args)
     elif args.impl == 'reference':
         cpu_reference(args)
     else:

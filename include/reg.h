@@ -216,6 +216,8 @@ typedef struct {
                              an integer >= 8.  0 or 1: off               (0) */
     double coarse_tol;    /* inner PCG relative residual tolerance       (0.1) */
     int coarse_max;       /* inner PCG iteration cap                      (10) */
+    int coarse_nt;        /* semi-Lagrangian steps of the coarse Hessian,
+                             1..64; 0: the context's nt                   (0) */
 } reg_solve_opts;
 
 typedef struct {
@@ -245,6 +247,8 @@ int reg_set_beta(reg_ctx* ctx, double beta);
  * curvature); *inner_iters (may be NULL) receives the count.  REG_ENOTREADY
  * before a setup. */
 int reg_twolevel_setup(reg_ctx* ctx, int coarse_factor, const float* v_hat);
+/* The same with the coarse Hessian's number of time steps (0: the context's). */
+int reg_twolevel_setup_nt(reg_ctx* ctx, int coarse_factor, int coarse_nt, const float* v_hat);
 int reg_twolevel_apply(reg_ctx* ctx, const float* r_hat, float* z_hat, double inner_tol,
                        int inner_max, int* inner_iters);
 
@@ -370,10 +374,18 @@ int reg_get_tile(const reg_ctx* ctx, int* k, int* wy);
  *                         (in every stored copy) after its copies, so the
  *                         next objective or gradient returns REG_ENONFINITE
  *                         and the context stays usable;
+ *  REG_INJECT_STAGE_TIMEOUT  the next launch of a staged interpolation
+ *                         kernel that stages its box by TMA issues no
+ *                         copy and waits for it at most ~1e-4 s of SM
+ *                         clock (instead of ~1 s): every block's bounded
+ *                         mbarrier wait runs out, the block writes NaN for
+ *                         its points (nothing is in flight), and the call
+ *                         that launched it reports REG_ENONFINITE; the
+ *                         context stays usable (after must be 0);
  *  REG_INJECT_NONE        disarm.
  * REG_EINVAL on an unknown kind or after < 0. */
 enum { REG_INJECT_NONE = 0, REG_INJECT_ALLOC = 1, REG_INJECT_CUFFT_PLAN = 2,
-       REG_INJECT_NAN_IMAGE = 3 };
+       REG_INJECT_NAN_IMAGE = 3, REG_INJECT_STAGE_TIMEOUT = 4 };
 int reg_debug_inject(int what, int after);
 
 /* How the staged interpolation kernels fill their shared-memory box.
@@ -527,9 +539,12 @@ typedef struct {
  * counters. */
 int reg_set_timing(reg_ctx* ctx, int on);
 
-/* Synchronise the stream and return the accumulated per-phase figures
- * (including the coarse grid's work of the two-level preconditioner). */
+/* Synchronise the stream and return the accumulated per-phase figures. */
 int reg_get_timing(reg_ctx* ctx, reg_timing* out);
+
+/* The same figures for the coarse grid of the two-level preconditioner
+ * (its context follows reg_set_timing of ctx); zeros without one. */
+int reg_get_coarse_timing(reg_ctx* ctx, reg_timing* out);
 
 #ifdef __cplusplus
 }

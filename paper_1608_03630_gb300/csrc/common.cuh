@@ -221,6 +221,8 @@ cudaError_t launch_to_bf16(const float* in, __nv_bfloat16* out, long long count,
 cudaError_t launch_from_bf16(const __nv_bfloat16* in, float* out, long long count,
                              cudaStream_t st);
 int march_blocks(const Dims& g, Tile t);   // blocks of one marching launch
+// Arm (1) or disarm (0) the bounded-wait test of the next TMA-staged launch.
+void arm_stage_timeout(int on);
 bool tile_staged(const Tile& t);           // t runs the shared-memory staged kernel
 
 // spectral.cu -- multipliers on the half spectrum (cufftComplex = float2).

@@ -993,7 +993,13 @@ int reg_set_tile(reg_ctx* c, int k, int wy) {
 }
 
 int reg_debug_inject(int what, int after) {
-    if (what < REG_INJECT_NONE || what > REG_INJECT_NAN_IMAGE || after < 0) return REG_EINVAL;
+    if (what < REG_INJECT_NONE || what > REG_INJECT_STAGE_TIMEOUT || after < 0) return REG_EINVAL;
+    if (what == REG_INJECT_STAGE_TIMEOUT) {
+        if (after != 0) return REG_EINVAL;
+        arm_stage_timeout(1);
+        return REG_OK;
+    }
+    if (what == REG_INJECT_NONE) arm_stage_timeout(0);
     g_inject_what.store(REG_INJECT_NONE);
     g_inject_left.store(after);
     g_inject_what.store(what);
@@ -1043,15 +1049,18 @@ int reg_get_timing(reg_ctx* c, reg_timing* out) {
     }
     c->pending.clear();
     *out = c->acc;
-    if (c->coarse) {   // the two-level preconditioner's coarse-grid work
-        reg_timing k;
-        REG_TRY(reg_get_timing(c->coarse, &k));
-        for (int p = 0; p < REG_NPHASES; ++p) {
-            out->ms[p] += k.ms[p];
-            out->launches[p] += k.launches[p];
-            out->bytes[p] += k.bytes[p];
-        }
+    return REG_OK;
+}
+
+int reg_get_coarse_timing(reg_ctx* c, reg_timing* out) {
+    CHECK_CTX(c);
+    if (!out) return fail(c, REG_EINVAL, "out is NULL");
+    if (!c->coarse) {
+        memset(out, 0, sizeof *out);
+        return REG_OK;
     }
+    const int s = reg_get_timing(c->coarse, out);
+    if (s != REG_OK) return fail(c, s, "coarse grid: " + c->coarse->err);
     return REG_OK;
 }
 

@@ -349,19 +349,21 @@ static int child_fail(reg_ctx* c, int s) {
 }
 
 // Create (or keep) the coarse context and give it the restricted images.
-static int twolevel_setup(reg_ctx* c, int factor) {
+static int twolevel_setup(reg_ctx* c, int factor, int coarse_nt) {
     const Dims& g = c->g;
     if (factor < 2 || g.n1 % factor || g.n2 % factor || g.n3 % factor ||
         g.n1 / factor < 8 || g.n2 / factor < 8 || g.n3 / factor < 8)
         return fail(c, REG_EINVAL, "coarse factor: >= 2, dividing every n_j, n_j / factor >= 8");
+    if (coarse_nt < 0 || coarse_nt > 64) return fail(c, REG_EINVAL, "coarse_nt must be 0..64");
+    const int nt = coarse_nt > 0 ? coarse_nt : c->nt;
     if (!c->have_images) return fail(c, REG_ENOTREADY, "reg_set_images first");
-    if (c->coarse && c->coarse_factor != factor) {
+    if (c->coarse && (c->coarse_factor != factor || c->coarse->nt != nt)) {
         reg_destroy(c->coarse);
         c->coarse = nullptr;
     }
     if (!c->coarse) {
         reg_ctx* k = nullptr;
-        const int s = reg_create(g.n1 / factor, g.n2 / factor, g.n3 / factor, c->nt, c->beta,
+        const int s = reg_create(g.n1 / factor, g.n2 / factor, g.n3 / factor, nt, c->beta,
                                  c->kind, c->incompressible, &k);
         if (s != REG_OK) return fail(c, s, std::string("coarse grid: ") + reg_last_error(nullptr));
         c->coarse = k;
@@ -395,7 +397,9 @@ static int twolevel_linearize(reg_ctx* c, const float2* v_hat) {
     }
     float* vc = k->sv[R_V];
     REG_TRY(child_fail(c, to_physical(k, k->ss[S_V], vc)));
-    return child_fail(c, op_linearize(k, vc));
+    REG_TRY(child_fail(c, op_linearize(k, vc)));
+    // the coarse grid's launches are small: its own tile (cached per grid and halo)
+    return child_fail(c, reg_autotune(k, nullptr, nullptr));
 }
 
 // z_hat = M^-1 r_hat and dsc[slot] = <r, z>; *inner = coarse PCG iterations.
@@ -959,16 +963,21 @@ int reg_solve_opts_default(reg_solve_opts* o) {
     o->coarse_factor = 0;
     o->coarse_tol = 0.1;
     o->coarse_max = 10;
+    o->coarse_nt = 0;
     return REG_OK;
 }
 
-int reg_twolevel_setup(reg_ctx* c, int coarse_factor, const float* v_hat) {
+int reg_twolevel_setup_nt(reg_ctx* c, int coarse_factor, int coarse_nt, const float* v_hat) {
     if (!c) return REG_EINVAL;
     if (c->dead) return fail(c, REG_ECUDA, "context unusable after a CUDA error");
     if (!v_hat || ((uintptr_t)v_hat & 15u)) return fail(c, REG_EINVAL, "bad v_hat");
     REG_TRY(ensure_solver(c));
-    REG_TRY(twolevel_setup(c, coarse_factor));
+    REG_TRY(twolevel_setup(c, coarse_factor, coarse_nt));
     return twolevel_linearize(c, reinterpret_cast<const float2*>(v_hat));
+}
+
+int reg_twolevel_setup(reg_ctx* c, int coarse_factor, const float* v_hat) {
+    return reg_twolevel_setup_nt(c, coarse_factor, 0, v_hat);
 }
 
 int reg_twolevel_apply(reg_ctx* c, const float* r_hat, float* z_hat, double inner_tol,
@@ -1018,7 +1027,7 @@ int reg_solve(reg_ctx* c, float* v_inout, const reg_solve_opts* opts, reg_solve_
     REG_TRY(ensure_solver(c));
     if (o.coarse_factor >= 2) {
         REG_TRY(ensure_flexible(c));
-        REG_TRY(twolevel_setup(c, o.coarse_factor));
+        REG_TRY(twolevel_setup(c, o.coarse_factor, o.coarse_nt));
     } else {
         o.coarse_factor = 0;
     }

@@ -16,6 +16,7 @@
 // only the new plane (16 values) is loaded and the other 48 are reused.  The
 // plane slots rotate with a period of four unrolled steps, so every register
 // index is static.
+#include <atomic>
 #include <climits>
 #include <cstdint>
 #include <cstring>
@@ -458,12 +459,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
 // when it gave up (the copy never completed).
 constexpr long long kStageWaitCycles = 2000000000LL;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  long long limit = kStageWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kStageWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
+
+// Host-armed test of the bounded wait (reg_debug_inject with
+// REG_INJECT_STAGE_TIMEOUT): the next launch of the staged kernel that
+// stages by TMA issues no copy, so its mbarrier phase never completes, and
+// waits only kInjectWaitCycles before giving up.  No copy is in flight when
+// its blocks exit.
+constexpr long long kInjectWaitCycles = 200000LL;
+std::atomic<int> g_inject_stage{0};
 
 // Box of the 3-D tensor map at element coordinates (x3, x2, x1) = (x, y, z);
 // x * 4 bytes must be a multiple of 16.  Coordinates outside the grid read
@@ -617,7 +627,7 @@ __device__ void load_wrapped(float* box, const float* __restrict__ f, const Dims
 template <class Epi, int H, int WY>
 __global__ void __launch_bounds__(32 * WY, 1024 / (32 * WY))
 k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict__ d, Epi epi,
-             const __grid_constant__ CUtensorMap box_map, int use_tma) {
+             const __grid_constant__ CUtensorMap box_map, int use_tma, int inject_timeout) {
     constexpr int E2 = WY + 3 + 2 * H;
     constexpr int P3 = 64;
     constexpr int C0 = 3 - H, C1 = 38 + H;   // columns read by the tile's stencils
@@ -641,7 +651,7 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
         __syncthreads();
         if (tid == 0) {
             mbar_expect_tx(bar, (unsigned)(sizeof(float) * E1 * E23));
-            tma_load_box(box, &box_map, bar, o3, o2, o1);
+            if (!inject_timeout) tma_load_box(box, &box_map, bar, o3, o2, o1);
         }
     }
     Ahead<Epi> ah[2];
@@ -651,8 +661,9 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
     }
     bool staged = true;
     if (tma) {
-        staged = mbar_wait_bounded(bar, 0);
-        if (!staged) mbar_wait_bounded(bar, 0);   // let a late copy land before exit
+        const long long limit = inject_timeout ? kInjectWaitCycles : kStageWaitCycles;
+        staged = mbar_wait_bounded(bar, 0, limit);
+        if (!staged) mbar_wait_bounded(bar, 0, limit);   // let a late copy land before exit
         // in-grid index ranges of the box along each axis
         const int a_lo = min(max(-o1, 0), E1), a_hi = max(min(g.n1 - o1, E1), a_lo);
         const int b_lo = min(max(-o2, 0), E2), b_hi = max(min(g.n2 - o2, E2), b_lo);
@@ -803,8 +814,9 @@ cudaError_t run_tile_fixed(const Dims& g, Tile t, const float* f, const float* d
     }
     CUtensorMap map;
     const int use_tma = t.tma && box_tensor_map(&map, g, f, E1, E2) ? 1 : 0;
+    const int inject = use_tma && g_inject_stage.exchange(0) ? 1 : 0;
     k_tile_fixed<Epi, H, WY><<<march_grid(g, t), dim3(32, WY), smem, st>>>(g, t.k, f, d, epi, map,
-                                                                            use_tma);
+                                                                            use_tma, inject);
     return cudaGetLastError();
 }
 
@@ -1036,6 +1048,8 @@ __global__ void k_from_bf16(const __nv_bfloat16* __restrict__ in, float* __restr
 }
 
 }  // namespace
+
+void arm_stage_timeout(int on) { g_inject_stage.store(on ? 1 : 0); }
 
 cudaError_t launch_absmax(const float* d, long long count, unsigned int* out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned int), st);

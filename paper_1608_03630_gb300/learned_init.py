@@ -262,6 +262,13 @@ ARMS = (('plain', 'zero', 'fp32'), ('learned_fp32', 'learned', 'fp32'),
         ('mixed', 'zero', 'mixed_bf16'), ('learned_mixed', 'learned', 'mixed_bf16'))
 
 
+def twolevel_arms(factor):
+    """The arms again with the two-level preconditioner (coarse grid n /
+    factor): solver options as the fourth element of an arm."""
+    opts = {'coarse_factor': factor, 'coarse_tol': 0.1, 'coarse_max': 20}
+    return tuple((name + '_twolevel', init, prec, opts) for name, init, prec in ARMS)
+
+
 def evaluate(net, scale, seeds, n, kc=None, alpha=1.0, nt=8, beta=1e-3, gtol=1e-2,
              arms=ARMS, stages=1, log=print):
     """Each arm (name, initial guess 'zero' | 'learned', precision) solves the
@@ -276,6 +283,7 @@ def evaluate(net, scale, seeds, n, kc=None, alpha=1.0, nt=8, beta=1e-3, gtol=1e-
     ctxs = {p: reg.Registration(shape, nt, beta, 'H2', precision=p)
             for p in sorted({a[2] for a in arms} | {'fp32'})}
     c32 = ctxs['fp32']
+    arms = [tuple(a) + ({},) if len(a) == 3 else tuple(a) for a in arms]
     out = []
     for seed in seeds:
         rho_T, rho_R, _ = phantom(n, seed)
@@ -283,7 +291,7 @@ def evaluate(net, scale, seeds, n, kc=None, alpha=1.0, nt=8, beta=1e-3, gtol=1e-
         for c in ctxs.values():
             c.set_images(rho_T, rho_R, presmooth=True)
         rec = {'seed': int(seed)}
-        for name, init, prec in arms:
+        for name, init, prec, extra in arms:
             ctx = ctxs[prec]
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -291,7 +299,7 @@ def evaluate(net, scale, seeds, n, kc=None, alpha=1.0, nt=8, beta=1e-3, gtol=1e-
                 v = torch.zeros((3,) + shape, device='cuda')
             else:
                 v = predict(net, scale, rho_T, rho_R, n, kc, alpha, stages, ctx)
-            s, st = ctx.solve(v, gtol=gtol, gnorm_ref=-1.0)   # relative to ||g(0)||
+            s, st = ctx.solve(v, gtol=gtol, gnorm_ref=-1.0, **extra)   # relative to ||g(0)||
             torch.cuda.synchronize()
             st['seconds'] = time.perf_counter() - t0
             st['status'] = s
@@ -308,17 +316,17 @@ def evaluate(net, scale, seeds, n, kc=None, alpha=1.0, nt=8, beta=1e-3, gtol=1e-
                 '%s gn %d mv %d %.3f s J %.5e' % (name, rec[name]['gn_iters'],
                                                   rec[name]['matvecs'], rec[name]['seconds'],
                                                   rec[name]['J_fp32'])
-                for name, _, _ in arms))
+                for name, _, _, _ in arms))
     for c in ctxs.values():
         c.close()
     return out
 
 
 def summarise(evals, arms=ARMS):
-    keys = ('gn_iters', 'pcg_iters', 'matvecs', 'seconds', 'mismatch_rel', 'gnorm_rel',
-            'J_fp32', 'gnorm_rel_fp32')
-    return {name: {k: float(np.mean([e[name][k] for e in evals])) for k in keys}
-            for name, _, _ in arms}
+    keys = ('gn_iters', 'pcg_iters', 'matvecs', 'coarse_matvecs', 'seconds', 'mismatch_rel',
+            'gnorm_rel', 'J_fp32', 'gnorm_rel_fp32')
+    return {a[0]: {k: float(np.mean([e[a[0]][k] for e in evals])) for k in keys}
+            for a in arms}
 
 
 def he_normal(net, seed):
@@ -379,6 +387,9 @@ def main(argv=None):
     ap.add_argument('--eval-seed', type=int, default=7000)
     ap.add_argument('--out', default='learned_init_out')
     ap.add_argument('--load', default=None, help='skip training: evaluate these parameters')
+    ap.add_argument('--twolevel', type=int, default=0,
+                    help='also evaluate every arm with the two-level preconditioner '
+                         '(coarse grid n / this)')
     a = ap.parse_args(argv)
     os.makedirs(a.out, exist_ok=True)
     logf = open(os.path.join(a.out, 'log.txt'), 'a')
@@ -431,16 +442,19 @@ def main(argv=None):
                     stages)
     if a.stages:
         stages = a.stages
+    arms = ARMS + (twolevel_arms(a.twolevel) if a.twolevel else ())
     if a.eval > 0:
         ev = evaluate(net, scale, range(a.eval_seed, a.eval_seed + a.eval), a.eval_n, kc, alpha,
-                      stages=stages, log=log)
+                      stages=stages, arms=arms, log=log)
         report['eval'] = ev
-        report['eval_summary'] = summarise(ev)
+        report['eval_summary'] = summarise(ev, arms)
         log('summary ' + json.dumps(report['eval_summary']))
     if a.eval_large > 0:
         ev = evaluate(net, scale, [a.eval_large_seed], a.eval_large, kc, alpha, stages=stages,
-                      log=log)
+                      arms=arms, log=log)
         report['eval_large'] = ev
+        report['eval_large_summary'] = summarise(ev, arms)
+        log('summary large ' + json.dumps(report['eval_large_summary']))
     with open(os.path.join(a.out, 'report.json'), 'w') as f:
         json.dump(report, f, indent=1)
     return report

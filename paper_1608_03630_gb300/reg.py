@@ -36,7 +36,8 @@ class SolveOpts(ctypes.Structure):
                 ('verbose', ctypes.c_int), ('gnorm_ref', ctypes.c_double),
                 ('precond_shift', ctypes.c_double), ('beta_start', ctypes.c_double),
                 ('beta_factor', ctypes.c_double), ('coarse_factor', ctypes.c_int),
-                ('coarse_tol', ctypes.c_double), ('coarse_max', ctypes.c_int)]
+                ('coarse_tol', ctypes.c_double), ('coarse_max', ctypes.c_int),
+                ('coarse_nt', ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -88,6 +89,7 @@ _SIGS = {
     'reg_solve_opts_default': [ctypes.POINTER(SolveOpts)],
     'reg_set_beta': [_P, _D],
     'reg_twolevel_setup': [_P, _I, _P],
+    'reg_twolevel_setup_nt': [_P, _I, _I, _P],
     'reg_twolevel_apply': [_P, _P, _P, _D, _I, ctypes.POINTER(_I)],
     'reg_solve': [_P, _P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)],
     'reg_solve_host': [_P, _P, _P, _I, _P, ctypes.POINTER(SolveOpts),
@@ -107,6 +109,7 @@ _SIGS = {
     'reg_set_staging': [_P, _I],
     'reg_debug_inject': [_I, _I],
     'reg_get_timing': [_P, ctypes.POINTER(Timing)],
+    'reg_get_coarse_timing': [_P, ctypes.POINTER(Timing)],
     'reg_autotune': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_batch_create': [_I, _P, _I, _D, _I, _I, _I, ctypes.POINTER(_P)],
     'reg_batch_destroy': [_P],
@@ -160,14 +163,15 @@ def status_name(s):
         return 'status %d' % s
 
 
-INJECT = {'none': 0, 'alloc': 1, 'cufft_plan': 2, 'nan_image': 3}
+INJECT = {'none': 0, 'alloc': 1, 'cufft_plan': 2, 'nan_image': 3, 'stage_timeout': 4}
 
 
 def debug_inject(what, after=0):
     """Arm one host-side fault injection (reg_debug_inject): 'alloc' or
     'cufft_plan' fails the (after + 1)-th device allocation or cuFFT plan of
-    reg_create; 'nan_image' puts a NaN into the next reg_set_images; 'none'
-    disarms."""
+    reg_create; 'nan_image' puts a NaN into the next reg_set_images;
+    'stage_timeout' makes the next TMA-staged interpolation launch wait for a
+    copy it never issued, so its bounded waits run out; 'none' disarms."""
     s = lib().reg_debug_inject(INJECT[what], int(after))
     if s != 0:
         raise RegError(s, 'reg_debug_inject(%r, %r)' % (what, after))
@@ -321,10 +325,12 @@ class Registration:
                    self._cptr(o, 'Hvt_hat'))
         return o
 
-    def twolevel_setup(self, factor, v_hat):
-        """Coarse grid n / factor, restricted images, coarse Hessian at the
-        restriction of v_hat (reg_twolevel_setup)."""
-        self._call('reg_twolevel_setup', int(factor), self._cptr(v_hat, 'v_hat'))
+    def twolevel_setup(self, factor, v_hat, coarse_nt=0):
+        """Coarse grid n / factor, restricted images, coarse Hessian (with
+        coarse_nt time steps, 0: the context's) at the restriction of v_hat
+        (reg_twolevel_setup_nt)."""
+        self._call('reg_twolevel_setup_nt', int(factor), int(coarse_nt),
+                   self._cptr(v_hat, 'v_hat'))
 
     def twolevel_apply(self, r_hat, inner_tol=0.1, inner_max=10, out=None):
         """(z_hat, inner iterations) = two-level M^-1 r_hat (reg_twolevel_apply)."""
@@ -459,6 +465,12 @@ class Registration:
     def get_timing(self):
         t = Timing()
         self._call('reg_get_timing', ctypes.byref(t))
+        return t.as_dict()
+
+    def get_coarse_timing(self):
+        """Per-phase figures of the two-level preconditioner's coarse grid."""
+        t = Timing()
+        self._call('reg_get_coarse_timing', ctypes.byref(t))
         return t.as_dict()
 
 

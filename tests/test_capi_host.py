@@ -80,11 +80,13 @@ def test_null_context_is_rejected(lib):
 
 def test_fault_injection_arguments(lib):
     """Arming and disarming the host-side injection touches no GPU."""
-    assert lib.reg_debug_inject(4, 0) == 1
+    assert lib.reg_debug_inject(5, 0) == 1
     assert lib.reg_debug_inject(-1, 0) == 1
     assert lib.reg_debug_inject(1, -1) == 1
+    assert lib.reg_debug_inject(4, 1) == 1      # the wait test fires on the next launch only
     for what in (1, 2, 3):
         assert lib.reg_debug_inject(what, 2) == 0
+    assert lib.reg_debug_inject(4, 0) == 0
     assert lib.reg_debug_inject(0, 0) == 0
 
 

@@ -1,9 +1,11 @@
 """Error paths under host-side fault injection (reg_debug_inject).
 
 No GPU fault is provoked: the injected failures are a device allocation or
-a cuFFT plan that reg_create is told has failed, and a NaN written into a
-template image.  Each test checks the status, that nothing is left behind,
-and that the library keeps working afterwards.
+a cuFFT plan that reg_create is told has failed, a NaN written into a
+template image, and a TMA-staged interpolation launch told to issue no copy
+and to wait for it only briefly, so that its bounded mbarrier waits run out
+(nothing is in flight when its blocks exit).  Each test checks the status,
+that nothing is left behind, and that the library keeps working afterwards.
 """
 
 import numpy as np
@@ -87,3 +89,26 @@ def test_nan_image_is_reported_and_the_context_recovers(reg, precision):
     g, J = R.gradient(zero)
     assert np.isfinite(J) and bool(torch.isfinite(g).all())
     R.close()
+
+
+def test_bounded_staging_wait_runs_out_and_the_context_stays_usable(reg):
+    """x3 = 68 stages the interpolation boxes by TMA copies.  With the copy of
+    the next staged launch withheld, every block of that launch gives up its
+    wait after ~1e-4 s and writes NaN: the gradient reports REG_ENONFINITE,
+    and the next gradient, with nothing armed, equals the clean one."""
+    shape = (20, 24, 68)
+    rho_T, rho_R, vs = synth.sinusoid_problem(shape, 0.5)
+    R = reg.Registration(shape, 4, 1e-3)
+    R.set_images(dev(rho_T), dev(rho_R))
+    v = dev(vs)
+    g_ref, J_ref = R.gradient(v)
+    g_ref = g_ref.clone()
+    reg.debug_inject('stage_timeout')
+    with pytest.raises(reg.RegError) as e:
+        R.gradient(v)
+    assert e.value.status == 6          # REG_ENONFINITE
+    g, J = R.gradient(v)
+    torch.cuda.synchronize()
+    R.close()
+    assert J == J_ref
+    assert torch.equal(g, g_ref)
