@@ -372,6 +372,13 @@ def gpu_bench(args):
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
+        if args.profile_main:
+            # a fixed launch sequence for an ncu launch list: the steps only
+            for _ in range(args.steps):
+                step()
+            torch.cuda.synchronize()
+            R.close()
+            return
         if world > 1:
             dist.barrier()
         clocks = ClockSampler(local)
@@ -806,6 +813,10 @@ def main():
                          'PCG graph per lockstep Newton step')
     ap.add_argument('--no-batched', action='store_true',
                     help='leave the batched workload out of the main bench line')
+    ap.add_argument('--profile-main', action='store_true',
+                    help='run the warm-up and the timed steps of the main form only (no '
+                         'timing, arms, e2e, batch or CPU baseline) and print nothing: a '
+                         'fixed launch sequence for ncu')
     ap.add_argument('--profile-matvec', type=int, default=0, metavar='N',
                     help='run one gradient and two matvecs at N^3 (nt = 4) for ncu, then exit')
     args = ap.parse_args()
