@@ -244,6 +244,7 @@ struct SpecArgs {
     int kind;           // REG_H1 / REG_H2 / REG_H1DIV
     int project;        // apply P
     float s1, s2, s3;   // Gaussian widths
+    int normalised;     // in_a holds normalised coefficients (F f / n): no 1/n
 };
 cudaError_t launch_spectral(const Dims& g, SpecOp op, const SpecArgs& a, cudaStream_t st);
 // Per-block FP64 partials of sum_k weight(k) A(k) |V(k)|^2 over 3 fields
@@ -284,6 +285,14 @@ cudaError_t launch_sp_restrict(const Dims& gf, const Dims& gc, const float2* in,
 cudaError_t launch_sp_twolevel(const Dims& gf, const Dims& gc, const float2* r, const float2* y,
                                float2* z, double beta, double shift, int kind, int project,
                                double* partials, int nblk, cudaStream_t st);
+
+// deriv.cu -- spectral first derivative along one axis by one-dimensional
+// FFTs in shared memory: out (+)= d_axis f (i k' with the Nyquist entry 0).
+// Grids whose axes are powers of two (n1, n2 in 16..512, n3 in 32..512);
+// cudaErrorNotSupported elsewhere.
+bool deriv_supported(const Dims& g);
+cudaError_t launch_deriv(const Dims& g, int axis, const float* f, float* out, int accumulate,
+                         cudaStream_t st);
 
 // blas.cu
 int blas_blocks();   // number of partial-sum blocks used by reductions

@@ -149,6 +149,15 @@ static SpecArgs spec_args(reg_ctx* c) {
 }
 
 int op_grad(reg_ctx* c, const float* f, float* out3) {
+    if (deriv_supported(c->g)) {
+        // one-dimensional transforms per axis: one read and one write each
+        const long long n = c->g.n;
+        for (int ax = 0; ax < 3; ++ax) {
+            Phase p(c, REG_PH_SPECTRAL, 8.0 * n);
+            REG_CK(c, launch_deriv(c->g, ax, f, out3 + ax * n, 0, c->stream));
+        }
+        return REG_OK;
+    }
     REG_TRY(op_fft_r2c(c, f, c->spec[0], 1));
     SpecArgs a = spec_args(c);
     a.in_a = c->spec[0];
@@ -158,6 +167,14 @@ int op_grad(reg_ctx* c, const float* f, float* out3) {
 }
 
 int op_div(reg_ctx* c, const float* v3, float* out) {
+    if (deriv_supported(c->g)) {
+        const long long n = c->g.n;
+        for (int ax = 0; ax < 3; ++ax) {
+            Phase p(c, REG_PH_SPECTRAL, (ax ? 12.0 : 8.0) * n);
+            REG_CK(c, launch_deriv(c->g, ax, v3 + ax * n, out, ax ? 1 : 0, c->stream));
+        }
+        return REG_OK;
+    }
     REG_TRY(op_fft_r2c(c, v3, c->spec[0], 3));
     SpecArgs a = spec_args(c);
     a.in_a = c->spec[0];
@@ -379,7 +396,7 @@ int op_trial_state(reg_ctx* c, const float* v) {
     return state_of(c, v);
 }
 
-int op_linearize(reg_ctx* c, const float* v, bool state_ready) {
+int op_linearize(reg_ctx* c, const float* v, bool state_ready, const float2* v_hat) {
     const Dims& g = c->g;
     const long long n = g.n;
     const int nt = c->nt;
@@ -388,16 +405,27 @@ int op_linearize(reg_ctx* c, const float* v, bool state_ready) {
     // points, halos, state history, lam(1) = rho_R - rho(1) and the mismatch
     if (!state_ready) REG_TRY(state_of(c, v));
     if (comp) {
-        REG_TRY(op_div(c, v, c->divv));
+        if (v_hat && !deriv_supported(g)) {
+            SpecArgs a = spec_args(c);
+            a.in_a = v_hat;
+            a.out = c->spec[1];
+            a.normalised = 1;
+            REG_TRY(op_spectral(c, SPEC_DIV, a, 4));
+            REG_TRY(op_fft_c2r(c, c->spec[1], c->divv, 1));
+        } else {
+            REG_TRY(op_div(c, v, c->divv));
+        }
         Phase p(c, REG_PH_ADJOINT, 20.0 * n);
         REG_CK(c, launch_adjoint_coef(g, tile_with(c, c->halo_adj), c->divv, c->d_adj,
                                       (float)(1.0 / nt), c->coef, c->stream));
     }
-    // spectral gradients of every level (cached for the matvecs)
-    for (int j = 0; j <= nt; ++j) {
+    // spectral gradients of every level (cached for the matvecs); level 0 is
+    // rho_T whatever v is, so its gradient is kept across linearisations
+    for (int j = c->grad0_valid ? 1 : 0; j <= nt; ++j) {
         float* gj = c->grad_hist + (long long)j * 3 * n;
         REG_TRY(op_grad(c, c->rho_hist + j * n, gj));
     }
+    c->grad0_valid = true;
     if (c->hessian == REG_HESS_FULL_NEWTON) {
         // the full Newton matvec needs every adjoint level of this point
         REG_CK(c, cudaMemcpyAsync(c->lam_lin + nt * n, c->lam_hist + nt * n, sizeof(float) * n,
@@ -725,6 +753,7 @@ int reg_set_precision(reg_ctx* c, int precision) {
     REG_CK(c, cudaStreamSynchronize(c->stream));
     c->precision = precision;
     c->have_lin = false;
+    c->grad0_valid = false;
     c->have_images = false;
     if (precision == REG_MIXED_BF16 && !c->img_bf) {
         if (cudaMalloc(&c->img_bf, sizeof(__nv_bfloat16) * 2 * c->g.n) != cudaSuccess) {
@@ -763,6 +792,7 @@ int reg_set_images(reg_ctx* c, const float* rho_T, const float* rho_R, int presm
     CHECK_PTR(c, rho_R);
     const long long n = c->g.n;
     c->have_lin = false;
+    c->grad0_valid = false;
     c->img_version++;
     if (rho_T != c->rho_T)
         REG_CK(c, cudaMemcpyAsync(c->rho_T, rho_T, sizeof(float) * n, cudaMemcpyDeviceToDevice,
@@ -879,6 +909,7 @@ int reg_jacobian_det(reg_ctx* c, const float* u, float* det) {
     if (c->nt < 2) return fail(c, REG_ENOTIMPL, "reg_jacobian_det needs nt >= 2 (scratch space)");
     const long long n = c->g.n;
     c->have_lin = false;   // the grad rho cache holds the derivatives
+    c->grad0_valid = false;
     float* gu = c->grad_hist;   // (nt + 1) 3n >= 9n floats
     for (int comp = 0; comp < 3; ++comp) REG_TRY(op_grad(c, u + comp * n, gu + comp * 3 * n));
     Phase p(c, REG_PH_OTHER, 40.0 * n);

@@ -37,6 +37,8 @@ struct reg_ctx {
     float* divv;         // [n] (compressible)
     float* rho_hist;     // [(nt+1) n]
     float* grad_hist;    // [(nt+1) 3n] grad rho(t_j), FP32 (gradient and FP32 matvec)
+    bool grad0_valid;    // grad_hist level 0 = grad rho(t_0) of the current images
+                         // (rho(t_0) = rho_T for every v: computed once per image set)
 
     // scratch
     float* lam_hist;     // [(nt+1) n] adjoint / incremental-adjoint levels
@@ -138,7 +140,10 @@ int op_inner(reg_ctx* c, const float* a, const float* b, long long count, int sl
 // levels, adjoint, and b = int lam grad rho dt into bacc.
 // state_ready: op_trial_state(c, v) ran last for this v (its points, state
 // history and mismatch are reused).
-int op_linearize(reg_ctx* c, const float* v, bool state_ready = false);
+// v_hat (may be null): the normalised coefficients of v, when the caller has
+// them (div v then needs one inverse transform).
+int op_linearize(reg_ctx* c, const float* v, bool state_ready = false,
+                 const float2* v_hat = nullptr);
 // J's mismatch at v with the points and state history kept in the
 // linearisation buffers (the solver's line search: an accepted trial point
 // is linearised next without redoing them).  Invalidates the linearisation.

@@ -397,7 +397,7 @@ static int twolevel_linearize(reg_ctx* c, const float2* v_hat) {
     }
     float* vc = k->sv[R_V];
     REG_TRY(child_fail(c, to_physical(k, k->ss[S_V], vc)));
-    REG_TRY(child_fail(c, op_linearize(k, vc)));
+    REG_TRY(child_fail(c, op_linearize(k, vc, false, k->ss[S_V])));
     // the coarse grid's launches are small: its own tile (cached per grid and halo)
     return child_fail(c, reg_autotune(k, nullptr, nullptr));
 }
@@ -531,7 +531,7 @@ static int evaluate_gradient(reg_ctx* c, double* J, double* gnorm, bool after_tr
     float2** S = c->ss;
     float* v = c->sv[R_V];
     if (!after_trial) REG_TRY(to_physical(c, S[S_V], v));
-    REG_TRY(op_linearize(c, v, after_trial));
+    REG_TRY(op_linearize(c, v, after_trial, S[S_V]));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
     {
         Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
@@ -591,6 +591,7 @@ static int gradient_norm_at_zero(reg_ctx* c, double* g0) {
         REG_CK(c, launch_axpby_out(c->tmp3, c->rho_R, r0, 1.f, -1.f, n, c->stream));
     }
     REG_TRY(op_grad(c, r0, c->grad_hist));
+    c->grad0_valid = true;   // level 0 of the cache: grad rho(t_0)
     {
         Phase p(c, REG_PH_OTHER, 28.0 * n);
         REG_CK(c, launch_mul_fields(c->tmp3, c->grad_hist, c->bacc, n, c->stream));
@@ -1095,7 +1096,7 @@ int reg_gradient_spectral(reg_ctx* c, const float* v_hat, float* g_hat, double* 
     const float2* vh = reinterpret_cast<const float2*>(v_hat);
     float* v = c->sv[R_V];
     REG_TRY(to_physical(c, vh, v));
-    REG_TRY(op_linearize(c, v));
+    REG_TRY(op_linearize(c, v, false, vh));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
     {
         Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);

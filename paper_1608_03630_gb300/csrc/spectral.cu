@@ -81,7 +81,8 @@ k_spectral(Dims g, int op, SpecArgs a, float inv_n) {
         const float2 x = a.in_a[idx], y = a.in_a[nc + idx], z = a.in_a[2 * nc + idx];
         const float re = -(w.p1 * x.y + w.p2 * y.y + w.p3 * z.y);
         const float im = w.p1 * x.x + w.p2 * y.x + w.p3 * z.x;
-        a.out[idx] = make_float2(re * inv_n, im * inv_n);
+        const float sc = a.normalised ? 1.f : inv_n;
+        a.out[idx] = make_float2(re * sc, im * sc);
         break;
     }
     case SPEC_ASSEMBLE:

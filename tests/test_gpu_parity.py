@@ -138,8 +138,10 @@ def test_state_transport(reg, shape):
     R.close()
 
 
-@pytest.mark.parametrize('shape', [(32, 32, 32), (20, 28, 44)])
+@pytest.mark.parametrize('shape', [(32, 32, 32), (20, 28, 44), (16, 64, 128), (16, 16, 512)])
 def test_spectral_operators(reg, shape):
+    """Power-of-two grids take the one-dimensional derivative kernels (axis
+    lengths 16..512), the others cuFFT; both against the oracle."""
     f = f32(synth.bandlimited(shape, 6, 31, ncomp=None))
     v = f32(synth.bandlimited(shape, 6, 32))
     beta = 3e-3
