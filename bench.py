@@ -52,7 +52,7 @@ KIND = 'H2'
 SEED = 3000
 WEIGHTS = os.path.join(ROOT, 'paper_1608_03630_gb300', 'weights', 'unet_r64.npz')
 PHASE_NAMES = ('departure', 'state', 'adjoint', 'incstate', 'incadj', 'interp', 'fft',
-               'spectral', 'blas', 'other')
+               'spectral', 'blas', 'other', 'deriv')
 
 
 def peaks():

@@ -355,11 +355,13 @@ int reg_jacobian_det(reg_ctx* ctx, const float* u, float* det);
 
 /* ------------------------------------------------------------- tuning */
 
-/* Tile of the interpolation kernels: each thread walks k points (multiple of
- * 4, 4..64) along x1 and a block is 32 x wy threads (wy in 1, 2, 4, 8, 16)
- * over (x3, x2).  wy = 16 runs only the shared-memory staged kernel (max
- * displacement up to 3 cells; beyond that the call uses wy = 8).  The default
- * is k = 8, wy = 8.  Results do not depend on the tile. */
+/* Tile of the interpolation kernels: each thread walks k points (a multiple
+ * of 4 in 4..64, or 1 or 2 with k wy >= 4) along x1 and a block is 32 x wy
+ * threads (wy in 1, 2, 4, 8, 16) over (x3, x2).  wy = 16 runs only the
+ * shared-memory staged kernel (max displacement up to 3 cells; beyond that
+ * the call uses wy = 8); k = 1, 2 (more warps for small grids) likewise, the
+ * register-window kernel taking k = 4 then.  The default is k = 8, wy = 8.
+ * Results do not depend on the tile. */
 int reg_set_tile(reg_ctx* ctx, int k, int wy);
 int reg_get_tile(const reg_ctx* ctx, int* k, int* wy);
 
@@ -525,7 +527,8 @@ enum {
     REG_PH_SPECTRAL = 7,   /* spectral multiplier kernels */
     REG_PH_BLAS = 8,       /* reductions and vector updates */
     REG_PH_OTHER = 9,      /* pointwise set-up kernels */
-    REG_NPHASES = 10
+    REG_PH_DERIV = 10,     /* spectral first derivatives by 1-D FFT kernels */
+    REG_NPHASES = 11
 };
 
 typedef struct {

@@ -92,7 +92,10 @@ int reg_autotune(reg_ctx* c, int* k_out, int* wy_out) {
     const Tile keep = c->tile;
     const bool timing = c->timing;
     c->timing = false;
-    static const int cand[][2] = {{4, 8}, {8, 8}, {16, 8}, {8, 4}, {16, 4}, {8, 16}, {16, 16}};
+    // k = 1 or 2 points per thread give small grids (the two-level
+    // preconditioner's coarse grid, small batch pairs) enough warps
+    static const int cand[][2] = {{4, 8}, {8, 8}, {16, 8}, {8, 4}, {16, 4}, {8, 16}, {16, 16},
+                                  {1, 8}, {2, 8}, {1, 16}, {2, 4}};
     float best = 1e30f;
     int bk = keep.k, bw = keep.wy;
     for (const auto& kw : cand) {

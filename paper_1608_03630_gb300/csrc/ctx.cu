@@ -153,7 +153,7 @@ int op_grad(reg_ctx* c, const float* f, float* out3) {
         // one-dimensional transforms per axis: one read and one write each
         const long long n = c->g.n;
         for (int ax = 0; ax < 3; ++ax) {
-            Phase p(c, REG_PH_SPECTRAL, 8.0 * n);
+            Phase p(c, REG_PH_DERIV, 8.0 * n);
             REG_CK(c, launch_deriv(c->g, ax, f, out3 + ax * n, 0, c->stream));
         }
         return REG_OK;
@@ -170,7 +170,7 @@ int op_div(reg_ctx* c, const float* v3, float* out) {
     if (deriv_supported(c->g)) {
         const long long n = c->g.n;
         for (int ax = 0; ax < 3; ++ax) {
-            Phase p(c, REG_PH_SPECTRAL, (ax ? 12.0 : 8.0) * n);
+            Phase p(c, REG_PH_DERIV, (ax ? 12.0 : 8.0) * n);
             REG_CK(c, launch_deriv(c->g, ax, v3 + ax * n, out, ax ? 1 : 0, c->stream));
         }
         return REG_OK;
@@ -245,7 +245,9 @@ Tile tile_with(const reg_ctx* c, int halo) {
     while (!tile_staged(t) && t.k > 4) t.k = ((t.k / 2) + 3) & ~3;
     if (!tile_staged(t)) {   // register-window kernel, configured tile
         t = c->tile;
+        t.halo = halo;
         if (t.wy == 16) t.wy = 8;
+        if (t.k < 4) t.k = 4;   // it marches in groups of four points
     }
     return t;
 }
@@ -1015,9 +1017,11 @@ int reg_inner(reg_ctx* c, const float* a, const float* b, size_t count, double* 
 
 int reg_set_tile(reg_ctx* c, int k, int wy) {
     CHECK_CTX(c);
-    if (k < 4 || k > 64 || (k & 3) || !(wy == 1 || wy == 2 || wy == 4 || wy == 8 || wy == 16))
+    const bool kok = (k == 1 || k == 2) ? wy * k >= 4 : (k >= 4 && k <= 64 && !(k & 3));
+    if (!kok || !(wy == 1 || wy == 2 || wy == 4 || wy == 8 || wy == 16))
         return fail(c, REG_EINVAL,
-                    "tile: k must be a multiple of 4 in [4, 64], wy in {1,2,4,8,16}");
+                    "tile: k in {1, 2} (with k wy >= 4) or a multiple of 4 in [4, 64]; "
+                    "wy in {1,2,4,8,16}");
     c->tile.k = k;
     c->tile.wy = wy;
     return REG_OK;

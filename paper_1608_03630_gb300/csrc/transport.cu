@@ -949,7 +949,10 @@ dim3 march_grid(const Dims& g, Tile t) {
 template <class Epi>
 cudaError_t run_march(const Dims& g, Tile t, const float* f, const float* d, const Epi& epi,
                       cudaStream_t st) {
-    if (t.k < 4 || (t.k & 3) || t.wy < 1) return cudaErrorInvalidValue;
+    if (t.k < 1 || t.wy < 1) return cudaErrorInvalidValue;
+    // the register-window kernel marches in groups of 4 points; 1 or 2
+    // points per thread only for the staged kernels (small grids)
+    if ((t.k < 4 || (t.k & 3)) && !tile_staged(t)) return cudaErrorInvalidValue;
     if (t.wy == 16) {
         // 16-row blocks exist only as the fixed-halo staged kernel
         if (!tile_staged(t) || t.halo > 3) return cudaErrorInvalidValue;

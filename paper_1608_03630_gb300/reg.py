@@ -19,7 +19,7 @@ H1, H2, H1DIV = 1, 2, 3
 KINDS = {'H1': H1, 'H2': H2, 'H1DIV': H1DIV}
 FP32, MIXED_BF16 = 0, 1
 PHASES = ('departure', 'state', 'adjoint', 'incstate', 'incadj', 'interp', 'fft',
-          'spectral', 'blas', 'other')
+          'spectral', 'blas', 'other', 'deriv')
 
 
 class RegError(RuntimeError):
@@ -55,7 +55,7 @@ class SolveStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
-NPHASES = 10
+NPHASES = 11
 
 
 class Timing(ctypes.Structure):

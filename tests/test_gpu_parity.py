@@ -152,10 +152,16 @@ def test_spectral_operators(reg, shape):
             assert rel(host(R.spectral_div(dev(v))), osp.divergence(v)) < 1e-5
             assert rel(host(R.leray(dev(v))), osp.leray(v)) < 1e-5
             # A amplifies FP32 FFT roundoff that lands in modes outside the
-            # band of v by up to |k|max^4 / |k|band^4 (about 450 for H2 here):
-            # the bound is 1e-7 * 450 ~ 5e-5 relative
-            assert rel(host(R.apply_regularisation(dev(v))),
-                       beta * osp.apply_regularisation(v, kind)) < 1e-4
+            # band of v by up to (|k|max / |k|band)^4 for H2 (about 450 at
+            # 32^3; |k|band = 6): the bound is 2e-7 times that ratio, at
+            # least 1e-4; a grid whose bound would exceed 1e-2 is not checked
+            # this way (the solver applies beta A to coefficients instead)
+            kmax2 = sum((m // 2) ** 2 for m in shape)
+            amp = (kmax2 / 36.0) ** (2 if kind == 'H2' else 1)
+            tol = max(1e-4, 2e-7 * amp)
+            if tol < 1e-2:
+                assert rel(host(R.apply_regularisation(dev(v))),
+                           beta * osp.apply_regularisation(v, kind)) < tol
             assert rel(host(R.precond(dev(v))),
                        osp.preconditioner(v, beta, kind, incompressible)) < 1e-5
             s = (0.2, 0.3, 0.1)
@@ -327,6 +333,28 @@ def test_tensor_copy_and_per_thread_staging_agree_bit_for_bit(reg, shape, wy):
     assert np.array_equal(res[0][0], res[1][0])
     assert res[0][1] == res[1][1]
     assert np.array_equal(res[0][2], res[1][2])
+
+
+@pytest.mark.parametrize('shape', [(32, 32, 64), (20, 24, 68)])
+def test_small_tiles_give_the_same_results(reg, shape):
+    """Tiles of 1 or 2 points per thread (more warps on small grids) run the
+    same per-point arithmetic as the default tile: identical fields, the
+    objective up to the order of its block sums."""
+    rho_T, rho_R, v = _problem_case(shape, 'H2', False, 1e-3, 4, True)
+    w = dev(synth.bandlimited(shape, 3, 1301))
+    out = []
+    for k, wy in ((8, 8), (1, 8), (2, 8), (1, 16), (2, 4)):
+        R = reg.Registration(shape, 4, 1e-3, 'H2', False)
+        R.set_tile(k, wy)
+        R.set_images(dev(rho_T), dev(rho_R))
+        g, J = R.gradient(dev(v))
+        h = R.hessian_matvec(w)
+        out.append((host(g), J, host(h)))
+        R.close()
+    for g, J, h in out[1:]:
+        assert np.array_equal(g, out[0][0])
+        assert np.array_equal(h, out[0][2])
+        assert abs(J - out[0][1]) <= 1e-12 * abs(out[0][1])
 
 
 def test_matvec_before_gradient_is_refused(reg):
