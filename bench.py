@@ -789,6 +789,21 @@ def twolevel_sweep(args):
           flush=True)
 
 
+def cpu_oracle_workload(args):
+    """The FP64 oracle's gradient, Hessian matvec and objective measured at
+    n^3 (--sweep-n; the phantom recipe, nt = 8) on one host core, next to the
+    64^3 sample scaled by grid points as the bench's cpu_baseline does."""
+    t_n = _oracle_ops((args.sweep_n,) * 3)
+    t_64 = _oracle_ops((64, 64, 64))
+    scale = (args.sweep_n / 64.0) ** 3
+    cores, model = host_cpu()
+    print(json.dumps({'metric': 'oracle seconds per operation', 'grid': args.sweep_n,
+                      'measured': {'gradient': t_n[0], 'matvec': t_n[1], 'objective': t_n[2]},
+                      'scaled_from_64': {'gradient': t_64[0] * scale, 'matvec': t_64[1] * scale,
+                                         'objective': t_64[2] * scale},
+                      'cores': 1, 'host': {'nproc': cores, 'cpu_model': model}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument('--gpus', type=int, default=1)
@@ -803,7 +818,8 @@ def main():
     ap.add_argument('--coarse-factor', type=int, default=4)
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='phantom256',
-                    choices=['phantom256', 'batched', 'beta_sweep', 'twolevel_sweep'])
+                    choices=['phantom256', 'batched', 'beta_sweep', 'twolevel_sweep',
+                             'cpu_oracle'])
     ap.add_argument('--sweep-n', type=int, default=256)
     ap.add_argument('--betas', type=float, nargs='+', default=[1e-1, 1e-2, 1e-3, 1e-4, 1e-5])
     ap.add_argument('--coarse-factors', type=int, nargs='*', default=[2, 4])
@@ -828,6 +844,8 @@ def main():
         beta_sweep(args)
     elif args.workload == 'twolevel_sweep' and args.impl != 'reference':
         twolevel_sweep(args)
+    elif args.workload == 'cpu_oracle':
+        cpu_oracle_workload(args)
     elif args.impl == 'reference':
         cpu_reference(args)
     else:

@@ -35,6 +35,7 @@ struct reg_unet {
     size_t np;
     float *p, *grad, *m, *v;     // FP32 parameters, gradients, Adam moments
     bf16 *wbf, *wtbf;            // bf16 weights [k][ci][co] and transposed [k][co][ci]
+    bf16* wmbf;                  // bf16 weights with mirrored offsets [K-1-k][ci][co]
     int tc;                      // forward 3x3x3 convolutions on tcgen05 where they fit (1)
                                  // or on the wmma path (0)
     long long step;
@@ -261,8 +262,14 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
 }
 
 // bf16 copies of one layer's weights: w [k][ci][co] and wt [k][co][ci]
+// BF16 copies of one layer's weights w [K][ci][co]: wb (same layout), wt
+// [K][co][ci] (transposed) and wm [K][ci][co] with the kernel offsets
+// mirrored (k -> K - 1 - k): the data gradient dX = sum_k dY(v - o_k) w_k^T is
+// the forward convolution of dY with wm, whose K-major B operand for output
+// channel ci is wm[k][ci][.].
 __global__ void k_wconvert(const float* __restrict__ w, bf16* __restrict__ wb,
-                           bf16* __restrict__ wt, int K, int ci, int co) {
+                           bf16* __restrict__ wt, bf16* __restrict__ wm, int K, int ci,
+                           int co) {
     const long long n = (long long)K * ci * co;
     for (long long i = (long long)blockIdx.x * kT + threadIdx.x; i < n;
          i += (long long)gridDim.x * kT) {
@@ -273,6 +280,7 @@ __global__ void k_wconvert(const float* __restrict__ w, bf16* __restrict__ wb,
         const bf16 b = __float2bfloat16(w[i]);
         wb[i] = b;
         wt[(k * co + o) * ci + c] = b;
+        wm[((K - 1 - k) * ci + c) * co + o] = b;
     }
 }
 
@@ -320,6 +328,20 @@ int conv_bwd(reg_unet* u, const UConv& L, int R, const bf16* x, const bf16* d, f
     a.kchunk = 2048;
     U_CK(u, reg::unet::launch_igemm(reg::unet::MODE_BWD_WEIGHT, a, u->stream));
     if (dx) {
+        // on tcgen05: the forward convolution of dY (Ci' = co input channels)
+        // with the mirrored weights to Co' = ci output channels, FP32 out
+        IgemmArgs t;
+        memset(&t, 0, sizeof t);
+        t.g = ConvGeom{R, R, R, (int)vol(R), L.co, L.ci, L.ks};
+        t.A_src = d;
+        t.Bt_src = u->wmbf + L.woff;
+        t.out_f = dx;
+        t.out_stride = L.ci;
+        t.out_off = 0;
+        if (u->tc && reg::unet::conv_fwd_tc_ok(t)) {
+            U_CK(u, reg::unet::launch_conv_fwd_tc(t, u->stream));
+            return REG_OK;
+        }
         IgemmArgs b;
         memset(&b, 0, sizeof b);
         b.g = a.g;
@@ -344,7 +366,7 @@ int convert_weights(reg_unet* u) {
     for (const auto& L : u->layers) {
         const int K = L.ks * L.ks * L.ks;
         k_wconvert<<<grid_of((long long)K * L.ci * L.co), kT, 0, u->stream>>>(
-            u->p + L.woff, u->wbf + L.woff, u->wtbf + L.woff, K, L.ci, L.co);
+            u->p + L.woff, u->wbf + L.woff, u->wtbf + L.woff, u->wmbf + L.woff, K, L.ci, L.co);
         U_CK(u, cudaGetLastError());
     }
     return REG_OK;
@@ -453,7 +475,7 @@ int loss_and_grad(reg_unet* u, const float* x, const float* t_soa, double* loss)
 void free_unet(reg_unet* u) {
     if (!u) return;
     if (u->stream) cudaStreamSynchronize(u->stream);
-    std::vector<void*> ptrs = {u->p, u->grad, u->m, u->v, u->wbf, u->wtbf, u->xin, u->y,
+    std::vector<void*> ptrs = {u->p, u->grad, u->m, u->v, u->wbf, u->wtbf, u->wmbf, u->xin, u->y,
                                u->g1, u->g2, u->gcat, u->gb, u->yt, u->dpart};
     for (auto* vec : {&u->a0, &u->a1, &u->pool, &u->cat, &u->d0, &u->d1})
         for (auto q : *vec) ptrs.push_back(q);
@@ -517,6 +539,7 @@ int reg_unet_create(int res, int levels, const int* ch, int cin, int cout, reg_u
     dalloc((void**)&u->v, sizeof(float) * off);
     dalloc((void**)&u->wbf, sizeof(bf16) * off);
     dalloc((void**)&u->wtbf, sizeof(bf16) * off);
+    dalloc((void**)&u->wmbf, sizeof(bf16) * off);
     const long long V0 = vol(res);
     dalloc((void**)&u->xin, sizeof(bf16) * V0 * cin);
     dalloc((void**)&u->y, sizeof(float) * V0 * cout);

@@ -33,8 +33,9 @@ struct IgemmArgs {
 cudaError_t launch_igemm(int mode, const IgemmArgs& a, cudaStream_t st);
 
 // Forward 3x3x3 convolution on the tcgen05 tensor cores (unet_tc.cu): usable
-// when Co is 16, 32, 64 or 128, Ci a multiple of 8, the output BF16 with row
-// stride and channel offset multiples of 8, and every pointer 16-byte aligned.
+// when Co is 16, 32, 64 or 128, Ci a multiple of 8, one output -- BF16 with
+// bias / ReLU, or FP32 plain sums (no bias, no ReLU) -- with row stride and
+// channel offset multiples of 8, and every pointer 16-byte aligned.
 bool conv_fwd_tc_ok(const IgemmArgs& a);
 cudaError_t launch_conv_fwd_tc(const IgemmArgs& a, cudaStream_t st);
 

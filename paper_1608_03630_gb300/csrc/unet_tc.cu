@@ -20,7 +20,9 @@
 // stage's mbarrier, which the threads wait on (bounded, about a second)
 // before they refill that stage.  Epilogue: warp w reads TMEM lanes 32w ..
 // 32w + 31 (its voxels) with tcgen05.ld, adds the bias, applies ReLU, and
-// stores BF16 channels-last rows with 16-byte stores.
+// stores BF16 channels-last rows with 16-byte stores -- or, for the data
+// gradient of a layer (the forward convolution of dY with the mirrored
+// weights), stores the FP32 sums as they are.
 #include <cstdint>
 
 #include "common.cuh"
@@ -280,7 +282,17 @@ __global__ void __launch_bounds__(128) k_conv_fwd_tc(IgemmArgs a) {
     for (int c0 = 0; c0 < BN; c0 += 16) {
         float v[16];
         ld_tmem16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
-        if (row_ok) {
+        if (row_ok && a.out_f) {
+            // FP32 output, no bias or activation (the data gradient)
+            float4* dst = reinterpret_cast<float4*>(a.out_f + (long long)m * a.out_stride +
+                                                    a.out_off + c0);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float4 q = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                if (!ok) q.x = q.y = q.z = q.w = __int_as_float(0x7fffffff);
+                dst[i] = q;
+            }
+        } else if (row_ok) {
             uint32_t w[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -330,11 +342,15 @@ cudaError_t launch_bn(const IgemmArgs& a, cudaStream_t st) {
 bool conv_fwd_tc_ok(const IgemmArgs& a) {
     const ConvGeom& g = a.g;
     const bool n_ok = g.Co == 16 || g.Co == 32 || g.Co == 64 || g.Co == 128;
+    // exactly one output: BF16 (bias, ReLU) or FP32 (plain sums)
+    const bool one_out = (a.out_bf != nullptr) != (a.out_f != nullptr);
     const uintptr_t al = reinterpret_cast<uintptr_t>(a.A_src) |
                          reinterpret_cast<uintptr_t>(a.Bt_src) |
-                         reinterpret_cast<uintptr_t>(a.out_bf);
-    return g.ks == 3 && n_ok && g.Ci % 8 == 0 && g.Ci > 0 && a.Bt_src && a.out_bf && !a.out_f &&
-           (al & 15) == 0 && a.out_stride % 8 == 0 && a.out_off % 8 == 0 && g.V > 0;
+                         reinterpret_cast<uintptr_t>(a.out_bf) |
+                         reinterpret_cast<uintptr_t>(a.out_f);
+    return g.ks == 3 && n_ok && g.Ci % 8 == 0 && g.Ci > 0 && a.Bt_src && one_out &&
+           (!a.out_f || (!a.bias && !a.relu)) && (al & 15) == 0 && a.out_stride % 8 == 0 &&
+           a.out_off % 8 == 0 && g.V > 0;
 }
 
 cudaError_t launch_conv_fwd_tc(const IgemmArgs& a, cudaStream_t st) {

@@ -95,7 +95,7 @@ def test_autotune_picks_a_valid_tile_and_keeps_results(reg):
     w = dev(synth.bandlimited(shape, 6, 7))
     before = R.hessian_matvec(w).clone()
     k, wy = R.autotune()
-    assert k % 4 == 0 and 4 <= k <= 64 and wy in (1, 2, 4, 8, 16)
+    assert (k in (1, 2) or (k % 4 == 0 and 4 <= k <= 64)) and wy in (1, 2, 4, 8, 16)
     after = R.hessian_matvec(w)
     assert float((after - before).norm() / before.norm()) < 1e-5
     R.close()

@@ -173,6 +173,30 @@ def test_unet_gradient_matches_oracle(reg, R, ch):
             assert rel(got[name + suf], want[name + suf]) < 3e-2, (name + suf)
 
 
+@pytest.mark.parametrize('tcgen05', [True, False])
+def test_unet_gradient_full_channels(reg, tcgen05):
+    """Every parameter gradient of the 16/32/64/128 network at 32^3 against
+    the oracle, with the data gradients of the layers whose inputs have 16..128
+    channels on tcgen05 (the forward convolution of dY with the mirrored
+    weights, FP32 out) and with every data gradient on the wmma path."""
+    ch = (16, 32, 64, 128)
+    net = reg.UNet(32, ch)
+    net.set_mma(tcgen05)
+    flat, used = make_params(net, seed=21)
+    net.set_params(flat)
+    x = make_input(32, 2, seed=22)
+    t = np.random.default_rng(23).standard_normal((3, 32, 32, 32)).astype(np.float32)
+    loss, g = net.gradient(dev(x), dev(t))
+    y, cache = oracle_forward(used, x, ch)
+    want_loss, dy = oun.mse(y, t.astype(np.float64).transpose(1, 2, 3, 0))
+    want = oun.backward(used, cache, dy, ch)
+    assert abs(loss - want_loss) < 2e-2 * want_loss
+    got = net.unpack(g.astype(np.float64))
+    for name, ws, bs in net.layer_shapes():
+        for suf in ('.w', '.b'):
+            assert rel(got[name + suf], want[name + suf]) < 3e-2, (tcgen05, name + suf)
+
+
 def test_adam_step_matches_update_formula(reg):
     """train_step recomputes the gradient; the split-K weight gradient sums in
     a run-dependent order, so entries whose gradient is within that noise of
