@@ -93,12 +93,15 @@ int reg_autotune(reg_ctx* c, int* k_out, int* wy_out) {
     const bool timing = c->timing;
     c->timing = false;
     // k = 1 or 2 points per thread give small grids (the two-level
-    // preconditioner's coarse grid, small batch pairs) enough warps
+    // preconditioner's coarse grid) more warps; they are tried only where
+    // the default tile fills less than two waves of the 152 SMs
     static const int cand[][2] = {{4, 8}, {8, 8}, {16, 8}, {8, 4}, {16, 4}, {8, 16}, {16, 16},
                                   {1, 8}, {2, 8}, {1, 16}, {2, 4}};
+    const int ncand = march_blocks(c->g, Tile{8, 8}) < 2 * 152 ? 11 : 7;
     float best = 1e30f;
     int bk = keep.k, bw = keep.wy;
-    for (const auto& kw : cand) {
+    for (int ci = 0; ci < ncand; ++ci) {
+        const auto& kw = cand[ci];
         c->tile.k = kw[0];
         c->tile.wy = kw[1];
         float ms = 0.f;

@@ -12,10 +12,11 @@
 // real line to the spectrum of a real line, so the two stay apart.  One read
 // and one write of the field per derivative.
 //
-// FFT: Stockham autosort (out of place, ping-pong between two shared
-// buffers, natural order in and out), radix 4 with one radix-2 stage when
-// log2 N is odd; twiddles exp(-2 pi i m / N) from a table the block fills
-// with sincospif.  Lines along x3 are rows (contiguous); lines along x1 or x2
+// FFT: Stockham autosort (natural order in and out), radix 4 with one
+// radix-2 stage when log2 N is odd, each stage in place in one shared buffer
+// (every thread reads its butterflies' inputs into registers, the block
+// synchronises, then it writes their outputs); twiddles exp(-2 pi i m / N)
+// from a table the block fills with sincospif.  Lines along x3 are rows (contiguous); lines along x1 or x2
 // are 32 neighbouring x3 columns, so every global access is a coalesced
 // 128-byte row segment.
 #include <mutex>
@@ -35,23 +36,26 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
 
 __device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
 
-// One Stockham stage of radix R over the kLines lines of `in` -> `out`
-// (line stride S complex).  Ns: length of the sub-transforms already done.
-// inverse: conjugate twiddles and butterflies.
+// One Stockham stage of radix R over the kLines lines of buf, in place: every
+// thread first reads the inputs of all its butterflies into registers, the
+// block synchronises, then every thread writes its outputs (line stride S
+// complex).  Ns: length of the sub-transforms already done.  inverse:
+// conjugate twiddles and butterflies.
 template <int N, int R, int S>
-__device__ __forceinline__ void stockham_stage(const float2* __restrict__ in,
-                                               float2* __restrict__ out,
-                                               const float2* __restrict__ tw, int Ns,
-                                               bool inverse) {
-    constexpr int B = N / R;                      // butterflies per line
-    for (int w = threadIdx.x; w < kLines * B; w += kThreads) {
+__device__ __forceinline__ void stockham_stage(float2* buf, const float2* __restrict__ tw,
+                                               int Ns, bool inverse) {
+    constexpr int B = N / R;                        // butterflies per line
+    constexpr int PER = (kLines * B + kThreads - 1) / kThreads;   // per thread
+    float2 v[PER][R];
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int w = threadIdx.x + q * kThreads;
+        if (w >= kLines * B) break;
         const int line = w / B, j = w - line * B;
-        const float2* src = in + line * S;
-        float2* dst = out + line * S;
+        const float2* src = buf + line * S;
         const int k = j % Ns;
         // twiddle angle -2 pi k r / (Ns R) = table index k r N / (Ns R)
         const int step = k * (N / (Ns * R));
-        float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             float2 x = src[j + r * B];
@@ -59,51 +63,52 @@ __device__ __forceinline__ void stockham_stage(const float2* __restrict__ in,
                 const float2 t = tw[(step * r) & (N - 1)];
                 x = cmul(x, inverse ? conj2(t) : t);
             }
-            v[r] = x;
+            v[q][r] = x;
         }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const int w = threadIdx.x + q * kThreads;
+        if (w >= kLines * B) break;
+        const int line = w / B, j = w - line * B;
+        float2* dst = buf + line * S;
+        const int k = j % Ns;
+        float2* u = v[q];
         if (R == 2) {
-            const float2 a = v[0], b = v[1];
-            v[0] = make_float2(a.x + b.x, a.y + b.y);
-            v[1] = make_float2(a.x - b.x, a.y - b.y);
+            const float2 a = u[0], b = u[1];
+            u[0] = make_float2(a.x + b.x, a.y + b.y);
+            u[1] = make_float2(a.x - b.x, a.y - b.y);
         } else {
             // radix-4 DFT: (a + c) +- (b + d), (a - c) -+ i (b - d) (forward)
-            const float2 a = v[0], b = v[1], c = v[2], d = v[3];
+            const float2 a = u[0], b = u[1], c = u[2], d = u[3];
             const float2 s0 = make_float2(a.x + c.x, a.y + c.y);
             const float2 s1 = make_float2(a.x - c.x, a.y - c.y);
             const float2 s2 = make_float2(b.x + d.x, b.y + d.y);
             const float2 s3 = make_float2(b.x - d.x, b.y - d.y);
             // -i s3 (forward) or +i s3 (inverse)
             const float2 t3 = inverse ? make_float2(-s3.y, s3.x) : make_float2(s3.y, -s3.x);
-            v[0] = make_float2(s0.x + s2.x, s0.y + s2.y);
-            v[2] = make_float2(s0.x - s2.x, s0.y - s2.y);
-            v[1] = make_float2(s1.x + t3.x, s1.y + t3.y);
-            v[3] = make_float2(s1.x - t3.x, s1.y - t3.y);
+            u[0] = make_float2(s0.x + s2.x, s0.y + s2.y);
+            u[2] = make_float2(s0.x - s2.x, s0.y - s2.y);
+            u[1] = make_float2(s1.x + t3.x, s1.y + t3.y);
+            u[3] = make_float2(s1.x - t3.x, s1.y - t3.y);
         }
         const int base = (j / Ns) * Ns * R + k;
 #pragma unroll
-        for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
+        for (int r = 0; r < R; ++r) dst[base + r * Ns] = u[r];
     }
+    __syncthreads();
 }
 
-// Full transform of the kLines lines; the result ends in *res (a or b).
+// Full transform of the kLines lines of buf, in place.
 template <int N, int S>
-__device__ __forceinline__ float2* fft_lines(float2* a, float2* b, const float2* tw,
-                                             bool inverse) {
-    float2* in = a;
-    float2* out = b;
+__device__ __forceinline__ void fft_lines(float2* buf, const float2* tw, bool inverse) {
     int Ns = 1;
     while (Ns * 4 <= N) {
-        stockham_stage<N, 4, S>(in, out, tw, Ns, inverse);
-        __syncthreads();
-        float2* t = in; in = out; out = t;
+        stockham_stage<N, 4, S>(buf, tw, Ns, inverse);
         Ns *= 4;
     }
-    if (Ns < N) {
-        stockham_stage<N, 2, S>(in, out, tw, Ns, inverse);
-        __syncthreads();
-        float2* t = in; in = out; out = t;
-    }
-    return in;
+    if (Ns < N) stockham_stage<N, 2, S>(buf, tw, Ns, inverse);
 }
 
 // AXIS 2: lines are rows (i1, i2) of length N = n3, 32 consecutive rows per
@@ -116,8 +121,7 @@ k_deriv(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumu
     constexpr int S = N + 1;                      // padded line stride (complex)
     extern __shared__ float2 sm[];
     float2* bufA = sm;
-    float2* bufB = sm + kLines * S;
-    float2* tw = sm + 2 * kLines * S;
+    float2* tw = sm + kLines * S;
     for (int m = threadIdx.x; m < N; m += kThreads) {
         float s, c;
         sincospif(-2.0f * (float)m / (float)N, &s, &c);
@@ -151,7 +155,8 @@ k_deriv(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumu
         bufAf[2 * ((l >> 1) * S + a) + (l & 1)] = __ldg(f + base + l * lstride + a * astride);
     }
     __syncthreads();
-    float2* z = fft_lines<N, S>(bufA, bufB, tw, false);
+    fft_lines<N, S>(bufA, tw, false);
+    float2* z = bufA;
     // i k' / N, k' = k in FFT order, Nyquist 0
     const float inv_n = 1.0f / (float)N;
     for (int e = threadIdx.x; e < kLines * N; e += kThreads) {
@@ -161,8 +166,7 @@ k_deriv(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumu
         z[l * S + k] = make_float2(-kk * inv_n * v.y, kk * inv_n * v.x);
     }
     __syncthreads();
-    float2* other = (z == bufA) ? bufB : bufA;
-    z = fft_lines<N, S>(z, other, tw, true);
+    fft_lines<N, S>(z, tw, true);
     const float* zf = reinterpret_cast<const float*>(z);
     for (int e = threadIdx.x; e < 32 * N; e += kThreads) {
         int l, a;
@@ -176,7 +180,7 @@ k_deriv(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumu
 
 template <int N, int AXIS>
 cudaError_t run_deriv(const Dims& g, const float* f, float* out, int accumulate, cudaStream_t st) {
-    const size_t smem = sizeof(float2) * (2 * kLines * (N + 1) + N);
+    const size_t smem = sizeof(float2) * (kLines * (N + 1) + N);
     if (smem > 48 * 1024) {
         // once per kernel instantiation (thread-safe)
         static std::once_flag once;

@@ -337,14 +337,16 @@ def test_tensor_copy_and_per_thread_staging_agree_bit_for_bit(reg, shape, wy):
 
 @pytest.mark.parametrize('shape', [(32, 32, 64), (20, 24, 68)])
 def test_small_tiles_give_the_same_results(reg, shape):
-    """Tiles of 1 or 2 points per thread (more warps on small grids) with the
-    fixed-halo staged kernel (wy = 8, 16) run the same per-point arithmetic
-    as the default tile: identical fields, the objective up to the order of
-    its block sums."""
+    """Tiles of 1 or 2 points per thread (more warps on small grids) of the
+    fixed-halo staged kernels with 8-row blocks run the same per-point
+    arithmetic as the default tile: identical fields, the objective up to the
+    order of its block sums.  16-row blocks take the unstaged semi-Lagrangian
+    points and 4-row blocks the generic staged kernel, which sum their
+    stencils in another order: equal to FP32 rounding."""
     rho_T, rho_R, v = _problem_case(shape, 'H2', False, 1e-3, 4, True)
     w = dev(synth.bandlimited(shape, 3, 1301))
     out = []
-    for k, wy in ((8, 8), (1, 8), (2, 8), (1, 16)):
+    for k, wy in ((8, 8), (1, 8), (2, 8)):
         R = reg.Registration(shape, 4, 1e-3, 'H2', False)
         R.set_tile(k, wy)
         R.set_images(dev(rho_T), dev(rho_R))
@@ -356,14 +358,14 @@ def test_small_tiles_give_the_same_results(reg, shape):
         assert np.array_equal(g, out[0][0]), i
         assert np.array_equal(h, out[0][2]), i
         assert abs(J - out[0][1]) <= 1e-12 * abs(out[0][1]), i
-    # the generic staged kernel (wy = 4) sums its stencil in another order
-    R = reg.Registration(shape, 4, 1e-3, 'H2', False)
-    R.set_tile(2, 4)
-    R.set_images(dev(rho_T), dev(rho_R))
-    g, J = R.gradient(dev(v))
-    h = R.hessian_matvec(w)
-    assert rel(host(g), out[0][0]) < 1e-5 and rel(host(h), out[0][2]) < 1e-5
-    R.close()
+    for k, wy in ((1, 16), (2, 4)):
+        R = reg.Registration(shape, 4, 1e-3, 'H2', False)
+        R.set_tile(k, wy)
+        R.set_images(dev(rho_T), dev(rho_R))
+        g, J = R.gradient(dev(v))
+        h = R.hessian_matvec(w)
+        assert rel(host(g), out[0][0]) < 1e-5 and rel(host(h), out[0][2]) < 1e-5, (k, wy)
+        R.close()
 
 
 def test_matvec_before_gradient_is_refused(reg):
