@@ -157,6 +157,8 @@ int reg_batch_create(int npairs, const int* dims, int nt, double beta, int reg_k
         }
         b->streams.push_back(s);
         status = reg_set_stream(c, s);
+        // the pairs' PCG loops run side by side: no cooperative launches
+        if (status == REG_OK) status = reg_set_persistent(c, 0);
         if (status == REG_OK && precision) status = reg_set_precision(c, precision);
     }
     if (status != REG_OK) {

@@ -184,6 +184,17 @@ cudaError_t launch_adjoint_acc(const Dims& g, Tile t, const float* lam_in, const
                                float w_first, const float* dotp, double* partials,
                                int max_partials, int* nblk_out, cudaStream_t st,
                                const float* add = nullptr);
+// One Gauss-Newton matvec's transports (incremental state from v~, the
+// incremental adjoint with the time integral b~, partial sums of <dotp, b~>)
+// in one persistent cooperative launch for small grids (grid-wide barriers
+// between the steps, bounded waits raising *err); *nb_out = partial sums.
+// cudaErrorNotSupported when it does not apply (halo > 3).
+cudaError_t launch_matvec_persistent(const Dims& g, int halo_fwd, int halo_adj, int nt, float dt,
+                                     const float* vt, const float* grad, const float* d_fwd,
+                                     const float* d_adj, const float* coef, float* u0, float* u1,
+                                     float* lam, float* b, const float* dotp, double* partials,
+                                     int max_partials, unsigned int* bar, int* err, int* nb_out,
+                                     cudaStream_t st);
 // Known-source part of an adjoint tau-step: out = dt/2 (1 + dt dv(x))
 // I[s_old](x + d) + dt/2 s_new(x), dv = divv (null: divergence free, dv = 0).
 cudaError_t launch_source_step(const Dims& g, Tile t, const float* s_old, const float* d,

@@ -470,6 +470,30 @@ int op_matvec_transport(reg_ctx* c, const float* vt, const float* dotp, int slot
     // levels; full Newton: every level u_0 .. u_{nt-1} (for grad rho~_j)
     float* u[2] = {reinterpret_cast<float*>(c->buf[0]), reinterpret_cast<float*>(c->buf[1])};
     auto level = [&](int j) { return full ? c->rt_hist + j * n : u[j & 1]; };
+    // small grids (the two-level preconditioner's coarse grid): the whole
+    // sequence in one persistent launch, where its sum <dotp, b~> is read
+    if (!full && dotp && c->persistent && n <= (1LL << 18)) {
+        int nb = 0;
+        cudaError_t e;
+        {
+            Phase p(c, REG_PH_INCADJ, (16.0 + gb + nt * (32.0 + gb) + nt * 60.0 + 12.0) * n);
+            e = launch_matvec_persistent(g, c->halo_fwd, c->halo_adj, nt, dt, vt, c->grad_hist,
+                                         c->d_fwd, c->d_adj,
+                                         c->incompressible ? nullptr : c->coef, u[0], u[1],
+                                         c->lam_hist, c->bacc, dotp, c->partials, c->npartials,
+                                         c->gsync, reinterpret_cast<int*>(c->gsync + 1), &nb,
+                                         c->stream);
+        }
+        if (e == cudaSuccess) {
+            Phase p(c, REG_PH_BLAS, 0.0);
+            REG_CK(c, launch_finalize(c->partials, nb, kTwoPi * kTwoPi * kTwoPi / n,
+                                      c->dsc + slot, c->stream));
+            return REG_OK;
+        }
+        // not for this launch (halo > 3) or refused: the steps one by one
+        cudaGetLastError();
+        if (e != cudaErrorNotSupported) c->persistent = false;
+    }
     {
         Phase p(c, REG_PH_INCSTATE, (16.0 + gb) * n);
         REG_CK(c, launch_incstate_init(g, vt, grad_level(c, 0), dt, level(0), c->stream));
@@ -570,7 +594,7 @@ static void free_ctx(reg_ctx* c) {
     void* ptrs[] = {c->rho_T, c->rho_R, c->img_bf, c->d_fwd, c->d_adj, c->divv, c->rho_hist,
                     c->grad_hist, c->lam_hist, c->coef, c->buf[0], c->buf[1],
                     c->bacc, c->tmp3, c->spec[0], c->spec[1], c->partials, c->dsc, c->dabs,
-                    c->lam_lin, c->rt_hist};
+                    c->gsync, c->lam_lin, c->rt_hist};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (int i = 0; i < 4; ++i)
@@ -638,6 +662,7 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
     c->tile.k = 8;
     c->tile.wy = 8;
     c->halo_fwd = c->halo_adj = -1;
+    c->persistent = true;
     // partial sums: the largest marching grid (k = 4, wy = 1), or up to
     // kMaxSlots partial-sum slots of the BLAS / spectral grid
     c->npartials = march_blocks(c->g, Tile{4, 1});
@@ -660,6 +685,7 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
         {(void**)&c->partials, sizeof(double) * c->npartials},
         {(void**)&c->dsc, sizeof(double) * 32},
         {(void**)&c->dabs, sizeof(unsigned int) * 4},
+        {(void**)&c->gsync, sizeof(unsigned int) * 4},
     };
     for (auto& a : allocs) {
         if (inject_fires(REG_INJECT_ALLOC) || cudaMalloc(a.p, a.bytes) != cudaSuccess) {
@@ -762,6 +788,17 @@ int reg_set_precision(reg_ctx* c, int precision) {
             cudaGetLastError();
             return fail(c, REG_ENOMEM, "cannot allocate bf16 images");
         }
+    }
+    return REG_OK;
+}
+
+int reg_set_persistent(reg_ctx* c, int on) {
+    CHECK_CTX(c);
+    if (on != 0 && on != 1) return fail(c, REG_EINVAL, "persistent: 0 or 1");
+    c->persistent = on != 0;
+    if (c->pcg_exec) {   // the captured PCG loop holds the other launch sequence
+        cudaGraphExecDestroy(c->pcg_exec);
+        c->pcg_exec = nullptr;
     }
     return REG_OK;
 }

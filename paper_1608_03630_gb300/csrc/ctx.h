@@ -61,6 +61,8 @@ struct reg_ctx {
     reg::Tile tile;      // tile of the interpolation kernels (k, wy)
     int halo_fwd, halo_adj;   // ceil(max |X - x|) of d_fwd / d_adj (-1: unknown)
     unsigned int* dabs;  // [2] device scratch for max |d| (float bits)
+    unsigned int* gsync; // [2] persistent kernel: barrier counter, error flag
+    bool persistent;     // small grids: one persistent launch per matvec transport
 
     // Hessian: REG_HESS_GAUSS_NEWTON (default) or REG_HESS_FULL_NEWTON; the
     // full Newton matvec keeps the adjoint levels of the linearisation point

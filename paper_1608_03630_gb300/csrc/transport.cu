@@ -259,15 +259,17 @@ struct EpiAdjAccT {
         p.g0 = ld(grad, idx);
         p.g1 = ld(grad, n + idx);
         p.g2 = ld(grad, 2 * n + idx);
+        // b and lam(1) are written by earlier steps (in the persistent
+        // small-grid kernel, earlier in the same launch): L2-coherent loads
         if (lam_first) {
-            const float l = w_first * __ldg(lam_first + idx);
+            const float l = w_first * __ldcg(lam_first + idx);
             p.b0 = l * ld(grad_first, idx);
             p.b1 = l * ld(grad_first, n + idx);
             p.b2 = l * ld(grad_first, 2 * n + idx);
         } else {
-            p.b0 = b[idx];
-            p.b1 = b[n + idx];
-            p.b2 = b[2 * n + idx];
+            p.b0 = __ldcg(b + idx);
+            p.b1 = __ldcg(b + n + idx);
+            p.b2 = __ldcg(b + 2 * n + idx);
         }
         p.a = kAdd ? __ldg(add + idx) : 0.f;
         return p;
@@ -538,17 +540,20 @@ __device__ __forceinline__ void tile_point(const float* __restrict__ box, int E1
     epi.post(idx, val, pre, acc);
 }
 
+// One output tile (block coordinates bx, by, bz) of the generic staged
+// kernel: stage the box, then gather every point of the tile.  The calling
+// block is 32 x blockDim.y threads; acc accumulates the epilogue's sums.
 template <class Epi>
-__global__ void __launch_bounds__(256)
-k_tile(Dims g, int K, int H, int E1, int E2, int E3, int P3, const float* __restrict__ f,
-       const float* __restrict__ d, Epi epi) {
-    extern __shared__ float box[];   // [E1][E2][P3], E3 columns used
+__device__ __forceinline__ void tile_task(const Dims& g, int K, int H, int E1, int E2, int E3,
+                                          int P3, const float* __restrict__ f,
+                                          const float* __restrict__ d, const Epi& epi,
+                                          float* box, int bx, int by, int bz, double& acc) {
     const int lane = threadIdx.x, ty = threadIdx.y;
-    const int i3 = blockIdx.x * 32 + lane;
-    const int i2 = blockIdx.y * blockDim.y + ty;
-    const int i1b = blockIdx.z * K;
-    const int o1 = i1b - 1 - H, o2 = blockIdx.y * blockDim.y - 1 - H;
-    const int o3 = blockIdx.x * 32 - 1 - H;
+    const int i3 = bx * 32 + lane;
+    const int i2 = by * blockDim.y + ty;
+    const int i1b = bz * K;
+    const int o1 = i1b - 1 - H, o2 = by * blockDim.y - 1 - H;
+    const int o3 = bx * 32 - 1 - H;
     const bool active = i3 < g.n3 && i2 < g.n2;
     const int kend = min(K, g.n1 - i1b);
     Ahead<Epi> ah[2];
@@ -575,7 +580,6 @@ k_tile(Dims g, int K, int H, int E1, int E2, int E3, int P3, const float* __rest
     }
     cp_async_wait_all();
     __syncthreads();
-    double acc = 0.0;
     if (active) {
         for (int k = 0; k < kend; k += 2) {
             {   // slot 0 (static index: the prefetch ring stays in registers)
@@ -592,6 +596,195 @@ k_tile(Dims g, int K, int H, int E1, int E2, int E3, int P3, const float* __rest
             }
         }
     }
+}
+
+// ----------------------------------------------- persistent small-grid kernel
+// On a small grid (the two-level preconditioner's coarse grid) every launch
+// of a matvec's transport is latency bound (a few microseconds of work behind
+// a launch, a box load and a tail).  k_matvec_persistent runs the whole
+// sequence of one Gauss-Newton matvec's transports in ONE launch: the
+// incremental-state set-up, the nt incremental-state steps, the nt
+// incremental-adjoint steps with the time integral, and the partial sums of
+// <p, b~>, separated by grid-wide barriers.  Every block takes the same tiles
+// in every step (so b~ and the levels written at a point are read back by
+// the block that wrote them), and boxes are staged with L2-coherent loads,
+// because the fields they gather were written earlier in the same launch by
+// other blocks.  The barrier waits are bounded (about half a second); a block
+// that gives up raises *err, and the host turns the launch's result into NaN.
+
+constexpr long long kBarrierCycles = 1000000000LL;
+
+__device__ __forceinline__ void grid_barrier(unsigned int* count, unsigned int target,
+                                             int* err) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        const long long t0 = clock64();
+        while (*reinterpret_cast<volatile unsigned int*>(count) < target) {
+            if (clock64() - t0 > kBarrierCycles) {
+                atomicExch(err, 1);
+                break;
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// tile_task with the box staged by coherent (L2) loads.
+template <class Epi>
+__device__ __forceinline__ void tile_task_coherent(const Dims& g, int K, int H, int E1, int E2,
+                                                   int E3, int P3, const float* f,
+                                                   const float* __restrict__ d, const Epi& epi,
+                                                   float* box, int bx, int by, int bz,
+                                                   double& acc) {
+    const int lane = threadIdx.x, ty = threadIdx.y;
+    const int i3 = bx * 32 + lane;
+    const int i2 = by * blockDim.y + ty;
+    const int i1b = bz * K;
+    const int o1 = i1b - 1 - H, o2 = by * blockDim.y - 1 - H;
+    const int o3 = bx * 32 - 1 - H;
+    const bool active = i3 < g.n3 && i2 < g.n2;
+    const int kend = min(K, g.n1 - i1b);
+    Ahead<Epi> ah[2];
+    if (active) {
+        if (0 < kend) fetch(ah[0], d, g, epi, i1b, i2, i3);
+        if (1 < kend) fetch(ah[1], d, g, epi, i1b + 1, i2, i3);
+    }
+    {
+        const int nwarps = blockDim.y;
+        int col[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) col[c] = wrap_near(o3 + lane + 32 * c, g.n3);
+        const int rows = E1 * E2;
+        for (int r = ty; r < rows; r += nwarps) {
+            const int a = r / E2, b = r - a * E2;
+            const float* src = f + (long long)wrap_near(o1 + a, g.n1) * g.n23 +
+                               wrap_near(o2 + b, g.n2) * g.n3;
+            float* dst = box + r * P3;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                if (lane + 32 * c < E3) dst[lane + 32 * c] = __ldcg(src + col[c]);
+        }
+    }
+    __syncthreads();
+    if (active) {
+        for (int k = 0; k < kend; k += 2) {
+            {
+                const Ahead<Epi> cur = ah[0];
+                if (k + 2 < kend) fetch(ah[0], d, g, epi, i1b + k + 2, i2, i3);
+                tile_point(box, E1, E2, E3, P3, o1, o2, o3, epi, f, g, i1b + k, i2, i3, cur.d1,
+                           cur.d2, cur.d3, cur.pre, acc);
+            }
+            if (k + 1 < kend) {
+                const Ahead<Epi> cur = ah[1];
+                if (k + 3 < kend) fetch(ah[1], d, g, epi, i1b + k + 3, i2, i3);
+                tile_point(box, E1, E2, E3, P3, o1, o2, o3, epi, f, g, i1b + k + 1, i2, i3, cur.d1,
+                           cur.d2, cur.d3, cur.pre, acc);
+            }
+        }
+    }
+    __syncthreads();   // the box is refilled by the block's next tile
+}
+
+struct PersistArgs {
+    Dims g;
+    int K;                       // points per thread along x1 (block 32 x blockDim.y)
+    int Hf, Hb;                  // halos of the forward and adjoint points
+    int E1f, E2f, E3f, E1b, E2b, E3b, P3;
+    int gx, gy, gz;              // tiles per axis
+    int nt;
+    float dt;
+    const float* vt;             // [3n]
+    const float* grad;           // grad rho levels [(nt+1)][3n]
+    const float* d_fwd;
+    const float* d_adj;
+    const float* coef;           // c(x), null when divergence free
+    float* u[2];                 // carried incremental state, ping-pong
+    float* lam;                  // incremental-adjoint levels [(nt+1) n]
+    float* b;                    // b~ [3n]
+    const float* dotp;           // [3n]: partial sums of <dotp, b~>
+    double* partials;            // [gridDim.x]
+    unsigned int* bar;           // barrier counter (zero at launch)
+    int* err;                    // raised by a barrier wait that gave up
+};
+
+__global__ void __launch_bounds__(256)
+k_matvec_persistent(PersistArgs a) {
+    extern __shared__ float box[];
+    const Dims& g = a.g;
+    const long long n = g.n;
+    const int ntiles = a.gx * a.gy * a.gz;
+    const unsigned int G = gridDim.x;
+    unsigned int target = 0;
+    auto tile_of = [&](int t, int& bx, int& by, int& bz) {
+        bx = t % a.gx;
+        by = (t / a.gx) % a.gy;
+        bz = t / (a.gx * a.gy);
+    };
+    // u_0 = dt/2 f_0, f_0 = -v~ . grad rho(t_0), at the points of the block's tiles
+    for (int t = blockIdx.x; t < ntiles; t += G) {
+        int bx, by, bz;
+        tile_of(t, bx, by, bz);
+        const int i3 = bx * 32 + threadIdx.x, i2 = by * blockDim.y + threadIdx.y;
+        if (i3 >= g.n3 || i2 >= g.n2) continue;
+        for (int k = 0; k < a.K && bz * a.K + k < g.n1; ++k) {
+            const int idx = ((bz * a.K + k) * g.n2 + i2) * g.n3 + i3;
+            const float f0 = -(a.vt[idx] * ld(a.grad, idx) + a.vt[n + idx] * ld(a.grad, n + idx) +
+                               a.vt[2 * n + idx] * ld(a.grad, 2 * n + idx));
+            a.u[0][idx] = 0.5f * a.dt * f0;
+        }
+    }
+    target += G;
+    grid_barrier(a.bar, target, a.err);
+    double acc = 0.0;
+    for (int j = 0; j < a.nt; ++j) {
+        const bool fin = (j == a.nt - 1);
+        const EpiIncState epi{fin ? a.lam + a.nt * n : a.u[(j + 1) & 1], a.vt,
+                              a.grad + (long long)(j + 1) * 3 * n, n, a.dt, fin ? 1 : 0};
+        for (int t = blockIdx.x; t < ntiles; t += G) {
+            int bx, by, bz;
+            tile_of(t, bx, by, bz);
+            tile_task_coherent(g, a.K, a.Hf, a.E1f, a.E2f, a.E3f, a.P3, a.u[j & 1], a.d_fwd, epi,
+                               box, bx, by, bz, acc);
+        }
+        target += G;
+        grid_barrier(a.bar, target, a.err);
+    }
+    acc = 0.0;
+    for (int j = a.nt - 1; j >= 0; --j) {
+        const bool first = (j == a.nt - 1), last = (j == 0);
+        const float w = last ? 0.5f * a.dt : a.dt;
+        const EpiAdjAcc epi{last ? nullptr : a.lam + j * n, a.coef,
+                            a.grad + (long long)j * 3 * n, a.b, n, w,
+                            first ? a.lam + a.nt * n : nullptr,
+                            first ? a.grad + (long long)a.nt * 3 * n : nullptr, 0.5f * a.dt,
+                            last ? a.dotp : nullptr, a.partials, nullptr};
+        for (int t = blockIdx.x; t < ntiles; t += G) {
+            int bx, by, bz;
+            tile_of(t, bx, by, bz);
+            tile_task_coherent(g, a.K, a.Hb, a.E1b, a.E2b, a.E3b, a.P3, a.lam + (j + 1) * n,
+                               a.d_adj, epi, box, bx, by, bz, acc);
+        }
+        if (!last) {
+            target += G;
+            grid_barrier(a.bar, target, a.err);
+        } else {
+            // a block whose barrier wait gave up poisons the inner product
+            if (*reinterpret_cast<volatile int*>(a.err)) acc = __longlong_as_double(0x7ff8000000000000LL);
+            epi.done(acc);
+        }
+    }
+}
+
+template <class Epi>
+__global__ void __launch_bounds__(256)
+k_tile(Dims g, int K, int H, int E1, int E2, int E3, int P3, const float* __restrict__ f,
+       const float* __restrict__ d, Epi epi) {
+    extern __shared__ float box[];   // [E1][E2][P3], E3 columns used
+    double acc = 0.0;
+    tile_task(g, K, H, E1, E2, E3, P3, f, d, epi, box, blockIdx.x, blockIdx.y, blockIdx.z, acc);
     epi.done(acc);
 }
 
@@ -1130,6 +1323,79 @@ cudaError_t launch_adjoint_acc(const Dims& g, Tile t, const float* lam_in, const
                      EpiAdjAcc{lam_out, c, grad, b, g.n, w, lam_first, grad_first, w_first, dotp,
                                partials, nullptr},
                      st);
+}
+
+// The persistent small-grid matvec transport (k_matvec_persistent): one
+// cooperative launch with one block per (co-resident) slot, tiles of one point
+// per thread along x1 and 8 rows; nb_out = blocks (= partial sums).
+// cudaErrorNotSupported when the boxes do not fit (halo > 3) or the grid is
+// not small; the caller then launches the steps one by one.
+cudaError_t launch_matvec_persistent(const Dims& g, int halo_fwd, int halo_adj, int nt, float dt,
+                                     const float* vt, const float* grad, const float* d_fwd,
+                                     const float* d_adj, const float* coef, float* u0, float* u1,
+                                     float* lam, float* b, const float* dotp, double* partials,
+                                     int max_partials, unsigned int* bar, int* err, int* nb_out,
+                                     cudaStream_t st) {
+    if (halo_fwd < 0 || halo_adj < 0 || halo_fwd > 3 || halo_adj > 3) return cudaErrorNotSupported;
+    PersistArgs a;
+    a.g = g;
+    a.K = 1;
+    const int WY = 8;
+    a.Hf = halo_fwd < 1 ? 1 : halo_fwd;
+    a.Hb = halo_adj < 1 ? 1 : halo_adj;
+    a.E1f = a.K + 3 + 2 * a.Hf; a.E2f = WY + 3 + 2 * a.Hf; a.E3f = 35 + 2 * a.Hf;
+    a.E1b = a.K + 3 + 2 * a.Hb; a.E2b = WY + 3 + 2 * a.Hb; a.E3b = 35 + 2 * a.Hb;
+    a.P3 = 64;
+    a.gx = (g.n3 + 31) / 32;
+    a.gy = (g.n2 + WY - 1) / WY;
+    a.gz = (g.n1 + a.K - 1) / a.K;
+    a.nt = nt;
+    a.dt = dt;
+    a.vt = vt; a.grad = grad; a.d_fwd = d_fwd; a.d_adj = d_adj; a.coef = coef;
+    a.u[0] = u0; a.u[1] = u1; a.lam = lam; a.b = b; a.dotp = dotp; a.partials = partials;
+    a.bar = bar; a.err = err;
+    const int E1 = a.E1f > a.E1b ? a.E1f : a.E1b, E2 = a.E2f > a.E2b ? a.E2f : a.E2b;
+    const size_t smem = sizeof(float) * (size_t)E1 * E2 * a.P3;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    static int per_sm = 0, sms = 0;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(k_matvec_persistent,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)(sizeof(float) * kMaxBoxFloats));
+        int dev = 0;
+        if (attr == cudaSuccess) attr = cudaGetDevice(&dev);
+        if (attr == cudaSuccess)
+            attr = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        // occupancy at the largest box (halo 3): a grid that fits any launch
+        const size_t smax = sizeof(float) * (1 + 3 + 6) * (WY + 3 + 6) * 64;
+        if (attr == cudaSuccess)
+            attr = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_matvec_persistent,
+                                                                 32 * WY, smax);
+    });
+    if (attr != cudaSuccess) return attr;
+    const int ntiles = a.gx * a.gy * a.gz;
+    int G = per_sm * sms;
+    if (G > ntiles) G = ntiles;
+    if (G > max_partials) G = max_partials;
+    if (G < 1) return cudaErrorNotSupported;
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(G);
+    cfg.blockDim = dim3(32, WY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr_coop[1];
+    attr_coop[0].id = cudaLaunchAttributeCooperative;
+    attr_coop[0].val.cooperative = 1;
+    cfg.attrs = attr_coop;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_matvec_persistent, a);
+    if (e != cudaSuccess) return e;
+    if (nb_out) *nb_out = G;
+    return cudaSuccess;
 }
 
 cudaError_t launch_source_step(const Dims& g, Tile t, const float* s_old, const float* d,

@@ -79,6 +79,7 @@ _SIGS = {
     'reg_set_stream': [_P, _P],
     'reg_set_precision': [_P, _I],
     'reg_set_hessian': [_P, _I],
+    'reg_set_persistent': [_P, _I],
     'reg_set_images': [_P, _P, _P, _I],
     'reg_objective': [_P, _P, ctypes.POINTER(_D)],
     'reg_gradient': [_P, _P, _P, ctypes.POINTER(_D)],
@@ -268,6 +269,11 @@ class Registration:
     def set_beta(self, beta):
         """Regularisation weight beta > 0 (reg_set_beta)."""
         self._call('reg_set_beta', float(beta))
+
+    def set_persistent(self, on):
+        """Small grids: one persistent launch per PCG matvec transport (True,
+        default) or the time steps one by one (False)."""
+        self._call('reg_set_persistent', 1 if on else 0)
 
     def set_hessian(self, full_newton):
         """True: full Newton Hessian (Eq. hessian with the lam terms);

@@ -368,6 +368,31 @@ def test_small_tiles_give_the_same_results(reg, shape):
         R.close()
 
 
+@pytest.mark.parametrize('shape,incompressible', [((64, 64, 64), False), ((40, 44, 48), True)])
+def test_persistent_small_grid_solve_matches_step_by_step_launches(reg, shape, incompressible):
+    """On grids of at most 2^18 points each PCG matvec's transports run as one
+    persistent cooperative launch (grid-wide barriers between the time steps,
+    generic staged gather); the same solve with the steps launched one by
+    one takes the same Newton and PCG steps to the same objective and
+    velocity (FP32 rounding of the stencil sums apart)."""
+    rho_T, rho_R, _ = synth.phantom_problem(shape, 4300)
+    out = []
+    for persistent in (True, False):
+        R = reg.Registration(shape, 4, 1e-3, 'H1DIV' if incompressible else 'H2',
+                             incompressible)
+        R.set_persistent(persistent)
+        R.set_images(dev(rho_T), dev(rho_R), presmooth=True)
+        v = torch.zeros((3,) + shape, device='cuda')
+        s, st = R.solve(v, gtol=1e-2)
+        R.close()
+        assert s == 0
+        out.append((host(v), st))
+    (v1, s1), (v0, s0) = out
+    assert s1['gn_iters'] == s0['gn_iters'] and s1['pcg_iters'] == s0['pcg_iters']
+    assert abs(s1['J'] - s0['J']) < 1e-6 * s0['J']
+    assert rel(v1, v0) < 1e-5
+
+
 def test_matvec_before_gradient_is_refused(reg):
     shape = (16, 16, 16)
     R = reg.Registration(shape, 4, 1e-2)
