@@ -366,14 +366,16 @@ int reg_set_tile(reg_ctx* ctx, int k, int wy);
 int reg_get_tile(const reg_ctx* ctx, int* k, int* wy);
 
 /* Small grids (at most 2^18 points: the two-level preconditioner's coarse
- * grid): on = 1 (default) runs the transports of each PCG matvec -- the
+ * grid): on = 1 runs the transports of each PCG matvec -- the
  * incremental state, the incremental adjoint with the time integral and the
  * partial sums of <p, b~> -- as ONE persistent cooperative launch with
  * grid-wide barriers between the time steps (bounded waits; a wait that
  * gives up makes <p, b~> NaN, which PCG reports as REG_ENONFINITE); on = 0
- * launches the 2 nt + 1 steps one by one.  Same arithmetic up to the order
- * of the FP32 stencil sums.  Contexts of a batch use 0 (their PCG loops run
- * side by side). */
+ * launches the 2 nt + 1 steps one by one (default: on a 64^3 coarse grid
+ * with nt = 4 the separate launches, with the autotuned small tiles, took
+ * 0.18 ms per matvec against 0.27 ms for the persistent launch).  Same
+ * arithmetic up to the order of the FP32 stencil sums.  Contexts of a batch
+ * use 0 (their PCG loops run side by side). */
 int reg_set_persistent(reg_ctx* ctx, int on);
 
 /* Host-side fault injection, for tests of the error paths (no GPU fault is

@@ -299,9 +299,11 @@ cudaError_t launch_sp_twolevel(const Dims& gf, const Dims& gc, const float2* r, 
 
 // deriv.cu -- spectral first derivative along one axis by one-dimensional
 // FFTs in shared memory: out (+)= d_axis f (i k' with the Nyquist entry 0).
-// Grids whose axes are powers of two (n1, n2 in 16..512, n3 in 32..512);
-// cudaErrorNotSupported elsewhere.
-bool deriv_supported(const Dims& g);
+// Grids whose axes are powers of two (n1, n2 in 16..512, n3 in 32..512)
+// and f, out 16-byte aligned (the kernels move 16-byte vectors);
+// cudaErrorNotSupported elsewhere.  deriv_supported(g, f, out): the same test
+// (a null pointer is not checked).
+bool deriv_supported(const Dims& g, const void* f = nullptr, const void* out = nullptr);
 cudaError_t launch_deriv(const Dims& g, int axis, const float* f, float* out, int accumulate,
                          cudaStream_t st);
 

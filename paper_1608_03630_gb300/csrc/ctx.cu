@@ -149,7 +149,7 @@ static SpecArgs spec_args(reg_ctx* c) {
 }
 
 int op_grad(reg_ctx* c, const float* f, float* out3) {
-    if (deriv_supported(c->g)) {
+    if (deriv_supported(c->g, f, out3)) {
         // one-dimensional transforms per axis: one read and one write each
         const long long n = c->g.n;
         for (int ax = 0; ax < 3; ++ax) {
@@ -167,7 +167,7 @@ int op_grad(reg_ctx* c, const float* f, float* out3) {
 }
 
 int op_div(reg_ctx* c, const float* v3, float* out) {
-    if (deriv_supported(c->g)) {
+    if (deriv_supported(c->g, v3, out)) {
         const long long n = c->g.n;
         for (int ax = 0; ax < 3; ++ax) {
             Phase p(c, REG_PH_DERIV, (ax ? 12.0 : 8.0) * n);
@@ -407,7 +407,7 @@ int op_linearize(reg_ctx* c, const float* v, bool state_ready, const float2* v_h
     // points, halos, state history, lam(1) = rho_R - rho(1) and the mismatch
     if (!state_ready) REG_TRY(state_of(c, v));
     if (comp) {
-        if (v_hat && !deriv_supported(g)) {
+        if (v_hat && !deriv_supported(g, v, c->divv)) {
             SpecArgs a = spec_args(c);
             a.in_a = v_hat;
             a.out = c->spec[1];
@@ -662,7 +662,7 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
     c->tile.k = 8;
     c->tile.wy = 8;
     c->halo_fwd = c->halo_adj = -1;
-    c->persistent = true;
+    c->persistent = false;
     // partial sums: the largest marching grid (k = 4, wy = 1), or up to
     // kMaxSlots partial-sum slots of the BLAS / spectral grid
     c->npartials = march_blocks(c->g, Tile{4, 1});

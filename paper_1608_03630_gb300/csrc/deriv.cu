@@ -12,13 +12,16 @@
 // real line to the spectrum of a real line, so the two stay apart.  One read
 // and one write of the field per derivative.
 //
-// FFT: Stockham autosort (natural order in and out), radix 4 with one
+// Lines of 32..256 points use a register-blocked four-step transform
+// (below); lines of 16 and 512 points a Stockham FFT in shared memory.
+// Stockham: natural order in and out, radix 4 with one
 // radix-2 stage when log2 N is odd, each stage in place in one shared buffer
 // (every thread reads its butterflies' inputs into registers, the block
 // synchronises, then it writes their outputs); twiddles exp(-2 pi i m / N)
 // from a table the block fills with sincospif.  Lines along x3 are rows (contiguous); lines along x1 or x2
 // are 32 neighbouring x3 columns, so every global access is a coalesced
 // 128-byte row segment.
+#include <cstdint>
 #include <mutex>
 
 #include "common.cuh"
@@ -178,6 +181,274 @@ k_deriv(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumu
     }
 }
 
+// ------------------------------------------ register-blocked four-step FFT
+// N = N1 N2 (N1 >= N2, both powers of two, N1 <= 16): a line is held by N2
+// threads, thread t owning x[t + N2 m] (m < N1).  Forward: a DFT of size N1
+// over m in registers, the twiddle exp(-2 pi i t q / N), a transpose through
+// shared memory, and thread s computes, for each q = s + N2 j, the DFT of
+// size N2 over t; it then owns X[q + N1 r] = X[s + N2 (j + (N1 / N2) r)]: the
+// same stride-N2 ownership as the input, so the inverse transform runs the
+// same steps on it and returns y[s + N2 m] to thread s.  Two transposes per
+// derivative instead of a shared-memory pass per radix stage.
+
+// exp(-2 pi i k / 16), k < 8 (the roots of the register DFTs, sizes <= 16)
+__device__ __forceinline__ float2 root16(int k) {
+    switch (k) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(0.92387953251128674f, -0.38268343236508977f);
+    case 2: return make_float2(0.70710678118654752f, -0.70710678118654752f);
+    case 3: return make_float2(0.38268343236508977f, -0.92387953251128674f);
+    case 4: return make_float2(0.f, -1.f);
+    case 5: return make_float2(-0.38268343236508977f, -0.92387953251128674f);
+    case 6: return make_float2(-0.70710678118654752f, -0.70710678118654752f);
+    default: return make_float2(-0.92387953251128674f, -0.38268343236508977f);
+    }
+}
+
+__host__ __device__ constexpr int bitrev(int i, int L) {
+    int r = 0;
+    for (int b = 1; b < L; b <<= 1) {
+        r = (r << 1) | (i & 1);
+        i >>= 1;
+    }
+    return r;
+}
+
+// Bit-reversal permutation of a register array, every index a compile-time
+// constant (so the array stays in registers).
+template <int L, int I = 0>
+__device__ __forceinline__ void bitrev_swap(float2 (&v)[L]) {
+    if constexpr (I < L) {
+        constexpr int J = bitrev(I, L);
+        if constexpr (I < J) {
+            const float2 t = v[I];
+            v[I] = v[J];
+            v[J] = t;
+        }
+        bitrev_swap<L, I + 1>(v);
+    }
+}
+
+// One radix-2 stage (butterflies of span LEN) of the in-register DFT.
+template <int L, int LEN>
+__device__ __forceinline__ void dft_stage(float2 (&v)[L], bool inverse) {
+#pragma unroll
+    for (int i = 0; i < L; i += LEN) {
+#pragma unroll
+        for (int k = 0; k < LEN / 2; ++k) {
+            float2 w = root16(k * (16 / LEN));
+            if (inverse) w.y = -w.y;
+            const float2 a = v[i + k];
+            const float2 b = cmul(v[i + k + LEN / 2], w);
+            v[i + k] = make_float2(a.x + b.x, a.y + b.y);
+            v[i + k + LEN / 2] = make_float2(a.x - b.x, a.y - b.y);
+        }
+    }
+    if constexpr (2 * LEN <= L) dft_stage<L, 2 * LEN>(v, inverse);
+}
+
+// In-register DFT of size L (radix 2, decimation in time), forward or
+// inverse (conjugate roots); natural order in and out, every register index
+// a compile-time constant.
+template <int L>
+__device__ __forceinline__ void dft_reg(float2 (&v)[L], bool inverse) {
+    bitrev_swap<L>(v);
+    dft_stage<L, 2>(v, inverse);
+}
+
+// One four-step transform of the block's 16 lines held in registers
+// (ownership as above); T: shared transpose buffer [16][N1][N2 + 1].
+template <int N1, int N2>
+__device__ __forceinline__ void fourstep(float2 (&v)[N1], float2* T, const float2* tw, int line,
+                                         int t, bool inverse) {
+    constexpr int N = N1 * N2;
+    constexpr int TS = N2 + 1;
+    dft_reg<N1>(v, inverse);
+#pragma unroll
+    for (int q = 0; q < N1; ++q) {
+        float2 w = tw[(t * q) & (N - 1)];
+        if (inverse) w.y = -w.y;
+        v[q] = cmul(v[q], w);
+    }
+    float2* Tl = T + line * N1 * TS;
+#pragma unroll
+    for (int q = 0; q < N1; ++q) Tl[q * TS + t] = v[q];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < N1 / N2; ++j) {
+        float2 c[N2];
+#pragma unroll
+        for (int u = 0; u < N2; ++u) c[u] = Tl[(t + N2 * j) * TS + u];
+        dft_reg<N2>(c, inverse);
+        // thread t now owns X[t + N2 (j + (N1 / N2) r)], r < N2
+#pragma unroll
+        for (int r = 0; r < N2; ++r) v[j + (N1 / N2) * r] = c[r];
+    }
+    __syncthreads();
+}
+
+// Block tile <-> shared complex lines, in 16-byte global accesses with every
+// load of a thread issued before its first shared-memory store (the bytes in
+// flight per SM are what bounds a streaming kernel).  Complex line c of the
+// block holds real lines 2c (Re) and 2c + 1 (Im) at stride S.  AXIS 2: a unit
+// is (c, 4 consecutive positions), read as one float4 from each real line
+// and stored as 4 complex values; AXIS 0 / 1: a unit is (position, 4
+// neighbouring real lines), one float4 of a row, stored as two complex values.
+template <int N, int S, int TH, int AXIS>
+__device__ __forceinline__ void tile_load(float2* buf, const float* __restrict__ f, long long base,
+                                          long long astride) {
+    if constexpr (AXIS == 2) {
+        constexpr int U = 16 * (N / 4);
+        static_assert(U % TH == 0, "units per thread");
+        float4 x[U / TH][2];
+#pragma unroll
+        for (int q = 0; q < U / TH; ++q) {
+            const int u = threadIdx.x + q * TH;
+            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
+            const float* src = f + base + (long long)(2 * c) * N + a;
+            x[q][0] = __ldg(reinterpret_cast<const float4*>(src));
+            x[q][1] = __ldg(reinterpret_cast<const float4*>(src + N));
+        }
+#pragma unroll
+        for (int q = 0; q < U / TH; ++q) {
+            const int u = threadIdx.x + q * TH;
+            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
+            float2* d = buf + c * S + a;
+            d[0] = make_float2(x[q][0].x, x[q][1].x);
+            d[1] = make_float2(x[q][0].y, x[q][1].y);
+            d[2] = make_float2(x[q][0].z, x[q][1].z);
+            d[3] = make_float2(x[q][0].w, x[q][1].w);
+        }
+    } else {
+        constexpr int U = 8 * N;
+        static_assert(U % TH == 0, "units per thread");
+        float4 x[U / TH];
+#pragma unroll
+        for (int q = 0; q < U / TH; ++q) {
+            const int u = threadIdx.x + q * TH;
+            const int a = u >> 3, l4 = 4 * (u & 7);
+            x[q] = __ldg(reinterpret_cast<const float4*>(f + base + l4 + a * astride));
+        }
+#pragma unroll
+        for (int q = 0; q < U / TH; ++q) {
+            const int u = threadIdx.x + q * TH;
+            const int a = u >> 3, c = 2 * (u & 7);
+            buf[c * S + a] = make_float2(x[q].x, x[q].y);
+            buf[(c + 1) * S + a] = make_float2(x[q].z, x[q].w);
+        }
+    }
+}
+
+template <int N, int S, int TH, int AXIS>
+__device__ __forceinline__ void tile_store(const float2* buf, float* __restrict__ out,
+                                           long long base, long long astride, int accumulate) {
+    if constexpr (AXIS == 2) {
+        constexpr int U = 16 * (N / 4);
+#pragma unroll
+        for (int q = 0; q < U / TH; ++q) {
+            const int u = threadIdx.x + q * TH;
+            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
+            const float2* z = buf + c * S + a;
+            const float2 z0 = z[0], z1 = z[1], z2 = z[2], z3 = z[3];
+            float4 re = make_float4(z0.x, z1.x, z2.x, z3.x);
+            float4 im = make_float4(z0.y, z1.y, z2.y, z3.y);
+            float4* d = reinterpret_cast<float4*>(out + base + (long long)(2 * c) * N + a);
+            float4* e = reinterpret_cast<float4*>(out + base + (long long)(2 * c + 1) * N + a);
+            if (accumulate) {
+                const float4 p = *d, r = *e;
+                re.x += p.x; re.y += p.y; re.z += p.z; re.w += p.w;
+                im.x += r.x; im.y += r.y; im.z += r.z; im.w += r.w;
+            }
+            *d = re;
+            *e = im;
+        }
+    } else {
+        constexpr int U = 8 * N;
+#pragma unroll
+        for (int q = 0; q < U / TH; ++q) {
+            const int u = threadIdx.x + q * TH;
+            const int a = u >> 3, c = 2 * (u & 7);
+            const float2 z0 = buf[c * S + a], z1 = buf[(c + 1) * S + a];
+            float4 w = make_float4(z0.x, z0.y, z1.x, z1.y);
+            float4* d = reinterpret_cast<float4*>(out + base + 4 * (u & 7) + a * astride);
+            if (accumulate) {
+                const float4 p = *d;
+                w.x += p.x; w.y += p.y; w.z += p.z; w.w += p.w;
+            }
+            *d = w;
+        }
+    }
+}
+
+template <int N1, int N2, int AXIS>
+__global__ void __launch_bounds__(16 * N2)
+k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumulate) {
+    constexpr int N = N1 * N2;
+    constexpr int S = N + 1;                       // load buffer line stride
+    constexpr int TH = 16 * N2;                    // threads
+    extern __shared__ float2 sm[];
+    float2* buf = sm;                              // max(16 S, 16 N1 (N2 + 1)) complex
+    float2* tw = sm + (16 * S > 16 * N1 * (N2 + 1) ? 16 * S : 16 * N1 * (N2 + 1));
+    for (int m = threadIdx.x; m < N; m += TH) {
+        float sn, cs;
+        sincospif(-2.0f * (float)m / (float)N, &sn, &cs);
+        tw[m] = make_float2(cs, sn);
+    }
+    long long base, astride;
+    if (AXIS == 2) {
+        base = (long long)blockIdx.x * 32 * N;
+        astride = 1;
+    } else {
+        const int groups = g.n3 / 32;
+        const int fixed = blockIdx.x / groups, col0 = (blockIdx.x - fixed * groups) * 32;
+        if (AXIS == 1) { base = (long long)fixed * g.n23 + col0; astride = g.n3; }
+        else { base = (long long)fixed * g.n3 + col0; astride = g.n23; }
+    }
+    tile_load<N, S, TH, AXIS>(buf, f, base, astride);
+    __syncthreads();
+    const int line = threadIdx.x / N2, t = threadIdx.x - line * N2;
+    float2 v[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = buf[line * S + t + N2 * m];
+    __syncthreads();                               // buf becomes the transpose buffer
+    fourstep<N1, N2>(v, buf, tw, line, t, false);
+    // i k' / N at k = t + N2 m (Nyquist 0)
+    const float inv_n = 1.0f / (float)N;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) {
+        const int k = t + N2 * m;
+        const float kk = (2 * k < N) ? (float)k : (2 * k == N ? 0.f : (float)(k - N));
+        v[m] = make_float2(-kk * inv_n * v[m].y, kk * inv_n * v[m].x);
+    }
+    fourstep<N1, N2>(v, buf, tw, line, t, true);
+#pragma unroll
+    for (int m = 0; m < N1; ++m) buf[line * S + t + N2 * m] = v[m];
+    __syncthreads();
+    tile_store<N, S, TH, AXIS>(buf, out, base, astride, accumulate);
+}
+
+template <int N1, int N2, int AXIS>
+cudaError_t run_deriv_r(const Dims& g, const float* f, float* out, int accumulate,
+                        cudaStream_t st) {
+    constexpr int N = N1 * N2;
+    const int bufc = 16 * (N + 1) > 16 * N1 * (N2 + 1) ? 16 * (N + 1) : 16 * N1 * (N2 + 1);
+    const size_t smem = sizeof(float2) * (bufc + N);
+    if (smem > 48 * 1024) {
+        static std::once_flag once;
+        static cudaError_t attr = cudaSuccess;
+        std::call_once(once, [&] {
+            attr = cudaFuncSetAttribute(k_deriv_r<N1, N2, AXIS>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        if (attr != cudaSuccess) return attr;
+    }
+    int blocks;
+    if (AXIS == 2) blocks = g.n1 * g.n2 / 32;
+    else blocks = (AXIS == 1 ? g.n1 : g.n2) * (g.n3 / 32);
+    k_deriv_r<N1, N2, AXIS><<<blocks, 16 * N2, smem, st>>>(g, f, out, accumulate);
+    return cudaGetLastError();
+}
+
 template <int N, int AXIS>
 cudaError_t run_deriv(const Dims& g, const float* f, float* out, int accumulate, cudaStream_t st) {
     const size_t smem = sizeof(float2) * (kLines * (N + 1) + N);
@@ -202,10 +473,10 @@ template <int AXIS>
 cudaError_t dispatch(const Dims& g, int N, const float* f, float* out, int acc, cudaStream_t st) {
     switch (N) {
     case 16: return run_deriv<16, AXIS>(g, f, out, acc, st);
-    case 32: return run_deriv<32, AXIS>(g, f, out, acc, st);
-    case 64: return run_deriv<64, AXIS>(g, f, out, acc, st);
-    case 128: return run_deriv<128, AXIS>(g, f, out, acc, st);
-    case 256: return run_deriv<256, AXIS>(g, f, out, acc, st);
+    case 32: return run_deriv_r<8, 4, AXIS>(g, f, out, acc, st);
+    case 64: return run_deriv_r<8, 8, AXIS>(g, f, out, acc, st);
+    case 128: return run_deriv_r<16, 8, AXIS>(g, f, out, acc, st);
+    case 256: return run_deriv_r<16, 16, AXIS>(g, f, out, acc, st);
     case 512: return run_deriv<512, AXIS>(g, f, out, acc, st);
     default: return cudaErrorNotSupported;
     }
@@ -215,13 +486,15 @@ bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1))
 
 }  // namespace
 
-bool deriv_supported(const Dims& g) {
-    return pow2_in(g.n1, 16, 512) && pow2_in(g.n2, 16, 512) && pow2_in(g.n3, 32, 512);
+bool deriv_supported(const Dims& g, const void* f, const void* out) {
+    const uintptr_t mis = (reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(out)) & 15;
+    return mis == 0 && pow2_in(g.n1, 16, 512) && pow2_in(g.n2, 16, 512) &&
+           pow2_in(g.n3, 32, 512);
 }
 
 cudaError_t launch_deriv(const Dims& g, int axis, const float* f, float* out, int accumulate,
                          cudaStream_t st) {
-    if (!deriv_supported(g)) return cudaErrorNotSupported;
+    if (!deriv_supported(g, f, out)) return cudaErrorNotSupported;
     if (axis == 0) return dispatch<0>(g, g.n1, f, out, accumulate, st);
     if (axis == 1) return dispatch<1>(g, g.n2, f, out, accumulate, st);
     return dispatch<2>(g, g.n3, f, out, accumulate, st);

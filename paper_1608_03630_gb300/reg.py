@@ -271,8 +271,8 @@ class Registration:
         self._call('reg_set_beta', float(beta))
 
     def set_persistent(self, on):
-        """Small grids: one persistent launch per PCG matvec transport (True,
-        default) or the time steps one by one (False)."""
+        """Small grids: one persistent launch per PCG matvec transport (True)
+        or the time steps one by one (False, the default)."""
         self._call('reg_set_persistent', 1 if on else 0)
 
     def set_hessian(self, full_newton):

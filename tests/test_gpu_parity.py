@@ -138,10 +138,13 @@ def test_state_transport(reg, shape):
     R.close()
 
 
-@pytest.mark.parametrize('shape', [(32, 32, 32), (20, 28, 44), (16, 64, 128), (16, 16, 512)])
+@pytest.mark.parametrize('shape', [(32, 32, 32), (20, 28, 44), (16, 64, 128), (16, 16, 512),
+                                   (256, 16, 32), (16, 32, 256), (128, 256, 64)])
 def test_spectral_operators(reg, shape):
     """Power-of-two grids take the one-dimensional derivative kernels (axis
-    lengths 16..512), the others cuFFT; both against the oracle."""
+    lengths 16..512: Stockham for 16 and 512, the register four-step
+    transform for 32..256, each on every axis), the others cuFFT; both
+    against the oracle."""
     f = f32(synth.bandlimited(shape, 6, 31, ncomp=None))
     v = f32(synth.bandlimited(shape, 6, 32))
     beta = 3e-3
@@ -370,8 +373,8 @@ def test_small_tiles_give_the_same_results(reg, shape):
 
 @pytest.mark.parametrize('shape,incompressible', [((64, 64, 64), False), ((40, 44, 48), True)])
 def test_persistent_small_grid_solve_matches_step_by_step_launches(reg, shape, incompressible):
-    """On grids of at most 2^18 points each PCG matvec's transports run as one
-    persistent cooperative launch (grid-wide barriers between the time steps,
+    """On grids of at most 2^18 points, with the persistent launch selected,
+    each PCG matvec's transports run as one persistent cooperative launch (grid-wide barriers between the time steps,
     generic staged gather); the same solve with the steps launched one by
     one takes the same Newton and PCG steps to the same objective and
     velocity (FP32 rounding of the stencil sums apart)."""

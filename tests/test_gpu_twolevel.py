@@ -87,7 +87,12 @@ def test_two_level_solve_reaches_the_same_stop_with_fewer_matvecs(reg):
         R.close()
     for beta in (1e-3, 1e-5):
         one, two = res[beta, 0], res[beta, 2]
-        assert abs(two['J'] - one['J']) < 2e-3 * one['J'], (beta, one['J'], two['J'])
+        # both stop at ||g|| <= 1e-2 ||g_0||; under the quadratic model the
+        # gap to the minimum is g^T H^-1 g / 2 against g_0^T H^-1 g_0 / 2 at
+        # v = 0, a small fraction of the decrease J_0 - J (1e-4 when g and
+        # g_0 point alike, more when g is left in low-curvature modes)
+        gap = 1e-2 * (one['J0'] - one['J'])
+        assert abs(two['J'] - one['J']) < gap, (beta, one['J0'], one['J'], two['J'])
         assert two['coarse_matvecs'] > 0 and one['coarse_matvecs'] == 0
     # at the small beta the coarse grid carries the ill-conditioned low modes
     assert res[1e-5, 2]['matvecs'] < res[1e-5, 0]['matvecs'], (res[1e-5, 0], res[1e-5, 2])
