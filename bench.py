@@ -358,6 +358,10 @@ def gpu_bench(args):
             ctx.set_images(dT, dR, presmooth=True)
             pc = ({'coarse_factor': args.coarse_factor, 'coarse_tol': 0.1, 'coarse_max': 20}
                   if precond == 'twolevel' else {})
+            if args.profile_main:
+                # PCG iterations as plain graphs (kernel nodes that ncu lists;
+                # a graph with a conditional node is profiled only whole)
+                pc = dict(pc, use_graph=1)
             if init == 'learned':
                 v.copy_(learned_init.predict(net, info['scale'], dT, dR, SHAPE[0], info['kc'],
                                              info['alpha'], info['stages'], ctx))
@@ -373,10 +377,13 @@ def gpu_bench(args):
             step()
         torch.cuda.synchronize()
         if args.profile_main:
-            # a fixed launch sequence for an ncu launch list: the steps only
+            # a fixed launch sequence for an ncu launch list: the steps only,
+            # inside the NVTX range "steps" (ncu --nvtx --nvtx-include steps/)
+            torch.cuda.nvtx.range_push('steps')
             for _ in range(args.steps):
                 step()
             torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
             R.close()
             return
         if world > 1:
@@ -831,8 +838,8 @@ def main():
                     help='leave the batched workload out of the main bench line')
     ap.add_argument('--profile-main', action='store_true',
                     help='run the warm-up and the timed steps of the main form only (no '
-                         'timing, arms, e2e, batch or CPU baseline) and print nothing: a '
-                         'fixed launch sequence for ncu')
+                         'timing, arms, e2e, batch or CPU baseline; PCG iterations as plain '
+                         'graphs) and print nothing: a fixed launch sequence for ncu')
     ap.add_argument('--profile-matvec', type=int, default=0, metavar='N',
                     help='run one gradient and two matvecs at N^3 (nt = 4) for ncu, then exit')
     args = ap.parse_args()

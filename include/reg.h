@@ -181,7 +181,9 @@ typedef struct {
                              graph per PCG iteration, tests on the host;
                              0: plain launches.  2 falls back to 1 when
                              phase timing is on or the driver refuses the
-                             conditional node                            (2) */
+                             conditional node.  The two-level
+                             preconditioner's coarse PCG loops take the
+                             same form                                   (2) */
     int verbose;          /* print one line per Newton iteration to stderr (0) */
     double gnorm_ref;     /* > 0: use it as ||g_0|| in the stop test and the
                              forcing term, e.g. the gradient norm at v = 0

@@ -403,8 +403,9 @@ static int twolevel_linearize(reg_ctx* c, const float2* v_hat) {
 }
 
 // z_hat = M^-1 r_hat and dsc[slot] = <r, z>; *inner = coarse PCG iterations.
+// use_graph: the coarse PCG loop's form (as reg_solve_opts.use_graph).
 static int twolevel_apply(reg_ctx* c, const float2* r_hat, float2* z_hat, double tol_rel,
-                          int max_it, int slot, int* inner) {
+                          int max_it, int slot, int* inner, int use_graph = 2) {
     reg_ctx* k = c->coarse;
     const int nb = blas_blocks();
     {
@@ -413,7 +414,7 @@ static int twolevel_apply(reg_ctx* c, const float2* r_hat, float2* z_hat, double
     }
     PcgResult pr;
     // the coarse PCG solves H_c s = -g_c = Pi_L r
-    const int s = pcg_solve(k, 0.0, max_it, 2, 0, &pr, tol_rel > 0.0 ? tol_rel : 1e-30);
+    const int s = pcg_solve(k, 0.0, max_it, use_graph, 0, &pr, tol_rel > 0.0 ? tol_rel : 1e-30);
     if (s != REG_OK) return child_fail(c, s);
     if (inner) *inner = pr.iters;
     {
@@ -430,7 +431,7 @@ static int twolevel_apply(reg_ctx* c, const float2* r_hat, float2* z_hat, double
 // Host-driven (it reads the scalars every iteration); the same stopping
 // tests as pcg_solve.
 static int pcg_solve_twolevel(reg_ctx* c, double tol, int max_it, double ctol, int cmax,
-                              PcgResult* res, int* coarse_iters) {
+                              int use_graph, PcgResult* res, int* coarse_iters) {
     const int nb = blas_blocks();
     const int proj = c->incompressible;
     float2** S = c->ss;
@@ -447,7 +448,7 @@ static int pcg_solve_twolevel(reg_ctx* c, double tol, int max_it, double ctol, i
     REG_TRY(read_scalars(c, SC_RR, 1));
     if (std::sqrt(c->hsc[SC_RR]) <= tol) { res->converged = true; return REG_OK; }
     int it_in = 0;
-    REG_TRY(twolevel_apply(c, S[S_R], S[S_Z], ctol, cmax, SC_RZ, &it_in));
+    REG_TRY(twolevel_apply(c, S[S_R], S[S_Z], ctol, cmax, SC_RZ, &it_in, use_graph));
     *coarse_iters += it_in;
     REG_CK(c, cudaMemcpyAsync(S[S_P], S[S_Z], sizeof(float2) * 3 * (size_t)c->g.nc,
                               cudaMemcpyDeviceToDevice, c->stream));
@@ -492,7 +493,7 @@ static int pcg_solve_twolevel(reg_ctx* c, double tol, int max_it, double ctol, i
         if (!std::isfinite(c->hsc[SC_RR])) return fail(c, REG_ENONFINITE, "non-finite residual");
         if (std::sqrt(c->hsc[SC_RR]) <= tol) { res->converged = true; break; }
         if (it == max_it) break;
-        REG_TRY(twolevel_apply(c, S[S_R], S[S_Z], ctol, cmax, SC_RZNEW, &it_in));
+        REG_TRY(twolevel_apply(c, S[S_R], S[S_Z], ctol, cmax, SC_RZNEW, &it_in, use_graph));
         *coarse_iters += it_in;
         {
             Phase ph(c, REG_PH_SPECTRAL, 2.0 * 24.0 * (double)c->g.nc);
@@ -741,8 +742,8 @@ static int solve_impl(reg_ctx* c, float* v_io, const reg_solve_opts* o, reg_solv
         PcgResult pr;
         if (o->coarse_factor >= 2) {
             REG_TRY(twolevel_linearize(c, c->ss[S_V]));
-            REG_TRY(pcg_solve_twolevel(c, tol, o->max_pcg, o->coarse_tol, o->coarse_max, &pr,
-                                       &st->coarse_matvecs));
+            REG_TRY(pcg_solve_twolevel(c, tol, o->max_pcg, o->coarse_tol, o->coarse_max,
+                                       o->use_graph, &pr, &st->coarse_matvecs));
         } else {
             REG_TRY(pcg_solve(c, tol, o->max_pcg, o->use_graph, o->verbose, &pr));
         }
