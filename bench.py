@@ -348,6 +348,8 @@ def gpu_bench(args):
         net, info = learned_init.load(WEIGHTS) if learned else (None, None)
         R = reg.Registration(SHAPE, NT, BETA, KIND, False, precision=args.precision,
                              stream=stream)
+        if args.coarse_tile:
+            R.set_coarse_tile(*args.coarse_tile)
 
         def solve_from_images(ctx, init, precond):
             """One registration from images on the device: the network's
@@ -415,6 +417,7 @@ def gpu_bench(args):
         phased_ms = ev2.elapsed_time(ev3)
         timing = R.get_timing()
         coarse_timing = R.get_coarse_timing()
+        coarse_tile = R.get_coarse_tile()
         R.set_timing(False)
         clk = clocks.stop()
         if world > 1:
@@ -549,6 +552,7 @@ def gpu_bench(args):
         'phase_ms_per_step': {k: v['ms'] / args.steps for k, v in timing.items()},
         'coarse_phase_ms_per_step': {k: v['ms'] / args.steps for k, v in coarse_timing.items()
                                      if v['launches']},
+        'coarse_tile': list(coarse_tile),
         'roofline': {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': peak,
                      'unit': 'GB/s', 'frac': achieved / peak, 'peak_source': peak_kind,
                      'bytes_per_launch': d['bytes'] / max(1, d['launches']),
@@ -840,6 +844,10 @@ def main():
                     help='run the warm-up and the timed steps of the main form only (no '
                          'timing, arms, e2e, batch or CPU baseline; PCG iterations as plain '
                          'graphs) and print nothing: a fixed launch sequence for ncu')
+    ap.add_argument('--coarse-tile', type=int, nargs=2, default=None, metavar=('K', 'WY'),
+                    help='fix the coarse grid tile instead of autotuning it (a profiler '
+                         'distorts the autotuner\'s timings: give a profiled run the tile '
+                         'of the plain run, its "coarse_tile")')
     ap.add_argument('--profile-matvec', type=int, default=0, metavar='N',
                     help='run one gradient and two matvecs at N^3 (nt = 4) for ncu, then exit')
     args = ap.parse_args()

@@ -564,6 +564,18 @@ int reg_get_timing(reg_ctx* ctx, reg_timing* out);
  * (its context follows reg_set_timing of ctx); zeros without one. */
 int reg_get_coarse_timing(reg_ctx* ctx, reg_timing* out);
 
+/* The interpolation tile (k, wy) of the two-level preconditioner's coarse
+ * grid.  By default (k = wy = 0) it is autotuned (reg_autotune) each time the
+ * coarse grid is linearised; a tile that reg_set_tile accepts is used as
+ * given instead (for instance to keep a profiler's launch sequence that of
+ * a plain run, whose autotuning the profiler's per-launch overhead would
+ * distort).  REG_EINVAL for other values.  Takes effect at the next
+ * linearisation. */
+int reg_set_coarse_tile(reg_ctx* ctx, int k, int wy);
+
+/* The tile the coarse grid runs with now; 0, 0 without a coarse grid. */
+int reg_get_coarse_tile(const reg_ctx* ctx, int* k, int* wy);
+
 #ifdef __cplusplus
 }
 #endif

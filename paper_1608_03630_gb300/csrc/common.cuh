@@ -49,6 +49,55 @@ __device__ __forceinline__ void lagrange4(float t, float w[4]) {
     w[3] = p * fmaf(t, 1.f / 6.f, 1.f / 6.f);
 }
 
+// Finish of a reduction kernel's per-block FP64 partial sums inside the same
+// launch (no separate launch_finalize): every block, once its partials are
+// visible, draws a ticket from an atomic counter; the block that draws the
+// last one (no block waits for another) sums each slot t's partials in the
+// order launch_finalize uses (thread-strided, warp shuffles, then the warps in
+// order), writes sc[out[t]] = sum * scale, then sc[copy_to] = sc[copy_from]
+// when copy_to >= 0, and resets the counter for the next launch.  The
+// counter belongs to one context, whose launches on its stream do not
+// overlap.
+struct Fin {
+    unsigned int* count;   // null: no finish (the partials are left for launch_finalize)
+    double* sc;
+    double scale;
+    int out[3];
+    int copy_from, copy_to;
+};
+
+template <int NS>
+__device__ __forceinline__ void finish_partials(const double* partials, int nblk, const Fin& f) {
+    __shared__ unsigned int ticket;
+    __shared__ double red[32];
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    __threadfence();   // this block's partials before its ticket
+    __syncthreads();
+    if (tid == 0) ticket = atomicAdd(f.count, 1u);
+    __syncthreads();
+    if (ticket != (unsigned int)nblk - 1u) return;
+    __threadfence();
+    for (int t = 0; t < NS; ++t) {
+        double acc = 0.0;
+        for (int i = tid; i < nblk; i += nthr) acc += __ldcg(partials + (long long)t * nblk + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if ((tid & 31) == 0) red[tid >> 5] = acc;
+        __syncthreads();
+        if (tid == 0) {
+            double s = 0.0;
+            for (int i = 0; i < nthr / 32; ++i) s += red[i];
+            f.sc[f.out[t]] = s * f.scale;
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (f.copy_to >= 0) f.sc[f.copy_to] = f.sc[f.copy_from];
+        *f.count = 0u;
+    }
+}
+
 // Packed FP32 pairs (Blackwell f32x2 ALU): two independent IEEE FP32
 // multiply-adds per instruction.
 typedef unsigned long long f32x2;
@@ -183,7 +232,7 @@ cudaError_t launch_adjoint_acc(const Dims& g, Tile t, const float* lam_in, const
                                float* b, const float* lam_first, const float* grad_first,
                                float w_first, const float* dotp, double* partials,
                                int max_partials, int* nblk_out, cudaStream_t st,
-                               const float* add = nullptr);
+                               const float* add = nullptr, const Fin* fin = nullptr);
 // One Gauss-Newton matvec's transports (incremental state from v~, the
 // incremental adjoint with the time integral b~, partial sums of <dotp, b~>)
 // in one persistent cooperative launch for small grids (grid-wide barriers
@@ -268,14 +317,17 @@ cudaError_t launch_spec_energy(const Dims& g, const float2* v, int kind, double*
 cudaError_t launch_sp_init(const Dims& g, const float2* gh, float2* r, float2* s, float2* p,
                            float2* pc, double beta, double shift, int kind, int project,
                            double* partials, int nblk, cudaStream_t st);
+// fin (may be null): finish the partials in the same launch (Fin).
 cudaError_t launch_sp_update(const Dims& g, float2* s, float2* r, const float2* p,
                              const float2* B, double* sc, int irz, int ipap, int ipb, int ipq,
                              double beta, double shift, int kind, int project,
-                             double* partials, int nblk, cudaStream_t st);
+                             double* partials, int nblk, cudaStream_t st,
+                             const Fin* fin = nullptr);
 cudaError_t launch_sp_direction(const Dims& g, const float2* r, float2* p, float2* pc,
                                 const double* sc, int irznew, int irz, int zero_beta,
                                 double beta, double shift, int kind, int project,
-                                double* partials, int nblk, cudaStream_t st);
+                                double* partials, int nblk, cudaStream_t st,
+                                const Fin* fin = nullptr);
 cudaError_t launch_sp_gradient(const Dims& g, const float2* v, const float2* B, float2* gout,
                                double beta, int kind, int project, double* partials, int nblk,
                                cudaStream_t st);

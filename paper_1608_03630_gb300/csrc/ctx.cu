@@ -330,6 +330,19 @@ int op_objective(reg_ctx* c, const float* v, int slot_J) {
 // Eq. inc-adj): the equation carries the known source s_j = div(lam_j v~)
 // with lam_j the adjoint levels of the linearisation point (lam_lin); each
 // step then adds dt/2 (1 + dt dv) I[s_{j+1}](X) + dt/2 s_j(x).
+Fin finish_into(reg_ctx* c, double scale, int slot0, int slot1, int copy_from, int copy_to) {
+    Fin f;
+    f.count = c->gsync + 2;
+    f.sc = c->dsc;
+    f.scale = scale;
+    f.out[0] = slot0;
+    f.out[1] = slot1;
+    f.out[2] = 0;
+    f.copy_from = copy_from;
+    f.copy_to = copy_to;
+    return f;
+}
+
 static int adjoint_solve(reg_ctx* c, int phase, float* levels, bool keep_all,
                          const float* src_vt, float* out, const float* dotp, int slot) {
     const long long n = c->g.n;
@@ -366,6 +379,8 @@ static int adjoint_solve(reg_ctx* c, int phase, float* levels, bool keep_all,
         double bytes = (comp ? 20.0 : 16.0) + (store ? 4.0 : 0.0) + 24.0 +
                        (first ? 16.0 : 12.0) + (last && dotp ? 12.0 : 0.0) +
                        (src_vt ? 4.0 : 0.0);
+        // the last step finishes <dotp, b> into dsc[slot] itself
+        const Fin fin = finish_into(c, kTwoPi * kTwoPi * kTwoPi / n, slot);
         Phase p(c, phase, bytes * n);
         REG_CK(c, launch_adjoint_acc(c->g, tile_with(c, c->halo_adj), levels + (j + 1) * n,
                                      c->d_adj, comp ? c->coef : nullptr,
@@ -373,12 +388,7 @@ static int adjoint_solve(reg_ctx* c, int phase, float* levels, bool keep_all,
                                      out, first ? levels + nt * n : nullptr,
                                      first ? grad_level(c, nt) : nullptr, 0.5f * dt,
                                      last ? dotp : nullptr, c->partials, c->npartials, &nb,
-                                     c->stream, src_vt ? add : nullptr));
-    }
-    if (dotp) {
-        Phase p(c, REG_PH_BLAS, 0.0);
-        REG_CK(c, launch_finalize(c->partials, nb, kTwoPi * kTwoPi * kTwoPi / n, c->dsc + slot,
-                                  c->stream));
+                                     c->stream, src_vt ? add : nullptr, &fin));
     }
     return REG_OK;
 }
@@ -704,6 +714,7 @@ int reg_create(int n1, int n2, int n3, int nt, double beta, int reg_kind, int in
         return fail(nullptr, REG_ENOMEM, "cannot allocate the grad rho cache");
     }
     cudaMemset(c->dsc, 0, sizeof(double) * 32);
+    cudaMemset(c->gsync, 0, sizeof(unsigned int) * 4);   // barrier, error flag, finish ticket
     int dims[3] = {n1, n2, n3};
     cufftResult r;
     r = inject_fires(REG_INJECT_CUFFT_PLAN)
@@ -1133,6 +1144,27 @@ int reg_get_coarse_timing(reg_ctx* c, reg_timing* out) {
     }
     const int s = reg_get_timing(c->coarse, out);
     if (s != REG_OK) return fail(c, s, "coarse grid: " + c->coarse->err);
+    return REG_OK;
+}
+
+int reg_set_coarse_tile(reg_ctx* c, int k, int wy) {
+    CHECK_CTX(c);
+    if (k == 0 && wy == 0) {
+        c->coarse_tile_k = c->coarse_tile_wy = 0;
+        return REG_OK;
+    }
+    const bool kok = (k == 1 || k == 2) ? wy * k >= 4 : (k >= 4 && k <= 64 && !(k & 3));
+    if (!kok || !(wy == 1 || wy == 2 || wy == 4 || wy == 8 || wy == 16))
+        return fail(c, REG_EINVAL, "coarse tile: 0, 0 or a tile reg_set_tile accepts");
+    c->coarse_tile_k = k;
+    c->coarse_tile_wy = wy;
+    return REG_OK;
+}
+
+int reg_get_coarse_tile(const reg_ctx* c, int* k, int* wy) {
+    if (!c || !k || !wy) return REG_EINVAL;
+    *k = c->coarse ? c->coarse->tile.k : 0;
+    *wy = c->coarse ? c->coarse->tile.wy : 0;
     return REG_OK;
 }
 

@@ -61,7 +61,8 @@ struct reg_ctx {
     reg::Tile tile;      // tile of the interpolation kernels (k, wy)
     int halo_fwd, halo_adj;   // ceil(max |X - x|) of d_fwd / d_adj (-1: unknown)
     unsigned int* dabs;  // [2] device scratch for max |d| (float bits)
-    unsigned int* gsync; // [2] persistent kernel: barrier counter, error flag
+    unsigned int* gsync; // [4] persistent kernel: barrier counter, error flag; [2] the
+                         // ticket counter of reductions finished in their own launch
     bool persistent;     // small grids: one persistent launch per matvec transport
 
     // Hessian: REG_HESS_GAUSS_NEWTON (default) or REG_HESS_FULL_NEWTON; the
@@ -81,6 +82,7 @@ struct reg_ctx {
     // holding the restricted images, linearised at the restricted velocity
     reg_ctx* coarse;
     int coarse_factor;
+    int coarse_tile_k, coarse_tile_wy;   // the coarse grid's tile; 0: autotuned
     long long img_version, coarse_img_version;   // restrict the images again when they change
 
     // timing
@@ -160,6 +162,11 @@ int op_matvec(reg_ctx* c, const float* vt, float* out);
 // dotp, dsc[slot] = <dotp, b~>_h.
 int op_matvec_transport(reg_ctx* c, const float* vt, const float* dotp, int slot);
 int op_precond(reg_ctx* c, const float* r, float* z);
+// The in-launch finish of a reduction (Fin) on c's ticket counter and device
+// scalars: slot t's sum times scale into dsc[slot_t], then dsc[copy_to] =
+// dsc[copy_from] when copy_to >= 0.
+Fin finish_into(reg_ctx* c, double scale, int slot0, int slot1 = 0, int copy_from = 0,
+                int copy_to = -1);
 int op_leray(reg_ctx* c, const float* v, float* out);
 int read_scalars(reg_ctx* c, int first, int count);   // dsc -> hsc, synchronises
 int bind_stream(reg_ctx* c, cudaStream_t s);         // launch stream + cuFFT plans

@@ -71,23 +71,22 @@ static int pcg_iteration(reg_ctx* c) {
     REG_TRY(op_fft_c2r(c, S[S_PC], p, 3));
     REG_TRY(op_matvec_transport(c, p, p, SC_PB));
     REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
+    // the reductions finish inside their kernels (Fin): RR and RZNEW in the
+    // update, PAP and then RZ = RZNEW in the direction
     {
+        const Fin fin = finish_into(c, kTwoPi3, SC_RR, SC_RZNEW);
         Phase ph(c, REG_PH_SPECTRAL, 6.0 * 24.0 * (double)c->g.nc);
         REG_CK(c, launch_sp_update(c->g, S[S_S], S[S_R], S[S_P], c->spec[1], c->dsc, SC_RZ, SC_PAP,
                                    SC_PB, SC_PQ, c->beta, c->pshift, c->kind, proj, c->partials,
-                                   nb, c->stream));
+                                   nb, c->stream, &fin));
     }
-    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
-    REG_TRY(finalize_to(c, 1, nb, kTwoPi3, SC_RZNEW));
     {
+        const Fin fin = finish_into(c, kTwoPi3, SC_PAP, 0, SC_RZNEW, SC_RZ);
         Phase ph(c, REG_PH_SPECTRAL, 4.0 * 24.0 * (double)c->g.nc);
         REG_CK(c, launch_sp_direction(c->g, S[S_R], S[S_P], S[S_PC], c->dsc, SC_RZNEW, SC_RZ, 0,
                                       c->beta, c->pshift, c->kind, proj, c->partials, nb,
-                                      c->stream));
+                                      c->stream, &fin));
     }
-    REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_PAP));
-    REG_CK(c, cudaMemcpyAsync(c->dsc + SC_RZ, c->dsc + SC_RZNEW, sizeof(double),
-                              cudaMemcpyDeviceToDevice, c->stream));
     return REG_OK;
 }
 
@@ -398,7 +397,9 @@ static int twolevel_linearize(reg_ctx* c, const float2* v_hat) {
     float* vc = k->sv[R_V];
     REG_TRY(child_fail(c, to_physical(k, k->ss[S_V], vc)));
     REG_TRY(child_fail(c, op_linearize(k, vc, false, k->ss[S_V])));
-    // the coarse grid's launches are small: its own tile (cached per grid and halo)
+    // the coarse grid's launches are small: its own tile, set by
+    // reg_set_coarse_tile or autotuned (cached per grid and halo)
+    if (c->coarse_tile_k > 0) return child_fail(c, reg_set_tile(k, c->coarse_tile_k, c->coarse_tile_wy));
     return child_fail(c, reg_autotune(k, nullptr, nullptr));
 }
 

@@ -245,7 +245,8 @@ k_sp_init(Dims g, const float2* __restrict__ gh, float2* __restrict__ r, float2*
 __global__ void __launch_bounds__(kThreads)
 k_sp_update(Dims g, float2* __restrict__ s, float2* __restrict__ r, const float2* __restrict__ p,
             const float2* __restrict__ B, double* sc, int irz, int ipap, int ipb, int ipq,
-            float beta, float shift, int kind, int project, float inv_n, double* partials) {
+            float beta, float shift, int kind, int project, float inv_n, double* partials,
+            Fin fin) {
     const long long nc = g.nc;
     const double pq = sc[ipap] + sc[ipb];
     const float alpha = pq > 0.0 ? (float)(sc[irz] / pq) : 0.f;
@@ -279,14 +280,16 @@ k_sp_update(Dims g, float2* __restrict__ s, float2* __restrict__ r, const float2
         acc[1] += (double)(mprec(A, beta, shift) * e);
     }
     store_partials<2>(acc, partials);
+    if (fin.count) finish_partials<2>(partials, gridDim.x, fin);
 }
 
 // b = sc[irznew] / sc[irz] (0 with zero_beta); p = M P r + b p; pc = p (or, with
 // to_s, s = M P r only); partials: beta A |p|^2.
 __global__ void __launch_bounds__(kThreads)
 k_sp_direction(Dims g, const float2* __restrict__ r, float2* __restrict__ p,
-               float2* __restrict__ pc, const double* __restrict__ sc, int irznew, int irz,
-               int zero_beta, float beta, float shift, int kind, int project, double* partials) {
+               float2* __restrict__ pc, const double* sc, int irznew, int irz,
+               int zero_beta, float beta, float shift, int kind, int project, double* partials,
+               Fin fin) {
     const long long nc = g.nc;
     const double den = sc[irz];
     const float bk = (zero_beta || den == 0.0) ? 0.f : (float)(sc[irznew] / den);
@@ -310,6 +313,7 @@ k_sp_direction(Dims g, const float2* __restrict__ r, float2* __restrict__ p,
         acc[0] += (double)(beta * A * herm_sq(w, z[0], z[1], z[2]));
     }
     store_partials<1>(acc, partials);
+    if (fin.count) finish_partials<1>(partials, gridDim.x, fin);
 }
 
 // g = beta A v + P B / n; partials: |g|^2, A |v|^2.
@@ -471,20 +475,23 @@ cudaError_t launch_sp_init(const Dims& g, const float2* gh, float2* r, float2* s
 cudaError_t launch_sp_update(const Dims& g, float2* s, float2* r, const float2* p,
                              const float2* B, double* sc, int irz, int ipap, int ipb, int ipq,
                              double beta, double shift, int kind, int project,
-                             double* partials, int nblk, cudaStream_t st) {
+                             double* partials, int nblk, cudaStream_t st, const Fin* fin) {
+    const Fin f = fin ? *fin : Fin{};
     k_sp_update<<<nblk, kThreads, 0, st>>>(g, s, r, p, B, sc, irz, ipap, ipb, ipq, (float)beta,
                                            (float)shift, kind, project, 1.0f / (float)g.n,
-                                           partials);
+                                           partials, f);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sp_direction(const Dims& g, const float2* r, float2* p, float2* pc,
                                 const double* sc, int irznew, int irz, int zero_beta,
                                 double beta, double shift, int kind, int project,
-                                double* partials, int nblk, cudaStream_t st) {
+                                double* partials, int nblk, cudaStream_t st,
+                                const Fin* fin) {
+    const Fin f = fin ? *fin : Fin{};
     k_sp_direction<<<nblk, kThreads, 0, st>>>(g, r, p, pc, sc, irznew, irz, zero_beta,
                                               (float)beta, (float)shift, kind, project,
-                                              partials);
+                                              partials, f);
     return cudaGetLastError();
 }
 

@@ -252,6 +252,7 @@ struct EpiAdjAccT {
     const float* dotp;       // last step only (else null)
     double* partials;
     const float* add;        // kAdd only: [n] added to lam_j
+    Fin fin;                 // last step: finish <dotp, b> in the launch (count may be null)
     struct Pre { float c, g0, g1, g2, b0, b1, b2, a; };
     __device__ Pre pre(int idx) const {
         Pre p;
@@ -290,6 +291,7 @@ struct EpiAdjAccT {
         const double s = block_sum(acc);
         if (threadIdx.x == 0 && threadIdx.y == 0)
             partials[blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z)] = s;
+        if (fin.count) finish_partials<1>(partials, gridDim.x * gridDim.y * gridDim.z, fin);
     }
 };
 using EpiAdjAcc = EpiAdjAccT<false>;
@@ -788,23 +790,49 @@ k_tile(Dims g, int K, int H, int E1, int E2, int E3, int P3, const float* __rest
     epi.done(acc);
 }
 
-// Box elements [a0, a1) x [b0, b1) x [c0, c1) (plane, row, column of a box
-// with E2 rows of pitch P3 whose element (0, 0, 0) is grid point (o1, o2, o3))
-// loaded from their periodic images, one element per thread at a time.
-template <int E2, int P3>
-__device__ void load_wrapped(float* box, const float* __restrict__ f, const Dims& g, int o1, int o2,
-                             int o3, int a0, int a1, int b0, int b1, int c0, int c1, int tid,
-                             int nthr) {
-    const int na = a1 - a0, nb = b1 - b0, nc = c1 - c0;
-    if (na <= 0 || nb <= 0 || nc <= 0) return;
-    for (int e = tid; e < na * nb * nc; e += nthr) {
-        const int c = c0 + e % nc, r = e / nc;
-        const int b = b0 + r % nb, a = a0 + r / nb;
-        box[(a * E2 + b) * P3 + c] =
-            __ldg(f + (long long)wrap_near(o1 + a, g.n1) * g.n23 +
-                  wrap_near(o2 + b, g.n2) * g.n3 + wrap_near(o3 + c, g.n3));
+// The elements of a box that lie outside the grid, as six disjoint regions
+// (planes outside; rows outside of inside planes; columns outside of inside
+// rows) of the box's column range [C0, C1), given the in-grid index ranges
+// [a_lo, a_hi) x [b_lo, b_hi) x [c_lo, c_hi).  One ordinal e in [0, count())
+// enumerates them, so that a thread can load its share before the box's copy
+// has landed and store it afterwards.
+template <int E2, int C0, int C1>
+struct Faces {
+    int E1, a_lo, a_hi, b_lo, b_hi, c_lo, c_hi;
+    __device__ int count() const {
+        constexpr int NC = C1 - C0;
+        const int A = a_hi - a_lo, B = b_hi - b_lo;
+        return (a_lo + E1 - a_hi) * E2 * NC + A * (b_lo + E2 - b_hi) * NC +
+               A * B * (c_lo - C0 + C1 - c_hi);
     }
-}
+    // box element (a, b, c) of ordinal e < count()
+    __device__ void element(int e, int& a, int& b, int& c) const {
+        constexpr int NC = C1 - C0;
+        const int A = a_hi - a_lo, B = b_hi - b_lo;
+        auto decode = [&](int l, int a0, int b0, int nb, int c0, int nc) {
+            c = c0 + l % nc;
+            const int r = l / nc;
+            b = b0 + r % nb;
+            a = a0 + r / nb;
+        };
+        int n = a_lo * E2 * NC;
+        if (e < n) return decode(e, 0, 0, E2, C0, NC);
+        e -= n;
+        n = (E1 - a_hi) * E2 * NC;
+        if (e < n) return decode(e, a_hi, 0, E2, C0, NC);
+        e -= n;
+        n = A * b_lo * NC;
+        if (e < n) return decode(e, a_lo, 0, b_lo, C0, NC);
+        e -= n;
+        n = A * (E2 - b_hi) * NC;
+        if (e < n) return decode(e, a_lo, b_hi, E2 - b_hi, C0, NC);
+        e -= n;
+        n = A * B * (c_lo - C0);
+        if (e < n) return decode(e, a_lo, b_lo, B, C0, c_lo - C0);
+        e -= n;
+        decode(e, a_lo, b_lo, B, c_hi, C1 - c_hi);
+    }
+};
 
 // The same kernel with the halo H and the block height WY fixed at compile
 // time: every one of the 64 shared-memory offsets of a point is then an
@@ -817,6 +845,8 @@ __device__ void load_wrapped(float* box, const float* __restrict__ f, const Dims
 // from their periodic images.  Without one, every thread issues 4-byte
 // cp.async copies with the wrap resolved per row.  A block whose wait for the
 // copy gives up (bounded, about a second) writes NaN for its points.
+constexpr int kWrapAhead = 4;   // periodic-image loads per thread issued before the copy lands
+
 template <class Epi, int H, int WY>
 __global__ void __launch_bounds__(32 * WY, 1024 / (32 * WY))
 k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict__ d, Epi epi,
@@ -854,26 +884,44 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
     }
     bool staged = true;
     if (tma) {
-        const long long limit = inject_timeout ? kInjectWaitCycles : kStageWaitCycles;
-        staged = mbar_wait_bounded(bar, 0, limit);
-        if (!staged) mbar_wait_bounded(bar, 0, limit);   // let a late copy land before exit
-        // in-grid index ranges of the box along each axis
+        // the copy reads zeros outside the grid: those elements come from
+        // their periodic images, in disjoint parts (planes outside; rows
+        // outside of inside planes; columns outside of inside rows).  A
+        // thread's first kWrapAhead of them are loaded while the copy is in
+        // flight and stored once it has landed, the rest after it.
+        const int nthr = 32 * WY;
         const int a_lo = min(max(-o1, 0), E1), a_hi = max(min(g.n1 - o1, E1), a_lo);
         const int b_lo = min(max(-o2, 0), E2), b_hi = max(min(g.n2 - o2, E2), b_lo);
         const int c_lo = min(max(-o3, C0), C1), c_hi = max(min(g.n3 - o3, C1), c_lo);
-        if (a_lo > 0 || a_hi < E1 || b_lo > 0 || b_hi < E2 || c_lo > C0 || c_hi < C1) {
-            // elements with a coordinate outside the grid, in disjoint parts:
-            // planes outside; rows outside of inside planes; columns outside
-            // of inside rows
-            const int nthr = 32 * WY;
-            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, 0, a_lo, 0, E2, C0, C1, tid, nthr);
-            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_hi, E1, 0, E2, C0, C1, tid, nthr);
-            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_lo, a_hi, 0, b_lo, C0, C1, tid, nthr);
-            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_lo, a_hi, b_hi, E2, C0, C1, tid, nthr);
-            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_lo, a_hi, b_lo, b_hi, C0, c_lo, tid,
-                                 nthr);
-            load_wrapped<E2, P3>(box, f, g, o1, o2, o3, a_lo, a_hi, b_lo, b_hi, c_hi, C1, tid,
-                                 nthr);
+        const Faces<E2, C0, C1> fc{E1, a_lo, a_hi, b_lo, b_hi, c_lo, c_hi};
+        const int total = fc.count();
+        auto image = [&](int a, int b, int c) {
+            return __ldg(f + (long long)wrap_near(o1 + a, g.n1) * g.n23 +
+                         wrap_near(o2 + b, g.n2) * g.n3 + wrap_near(o3 + c, g.n3));
+        };
+        float wv[kWrapAhead];
+        int wi[kWrapAhead];
+#pragma unroll
+        for (int q = 0; q < kWrapAhead; ++q) {
+            const int e = tid + q * nthr;
+            wi[q] = -1;
+            if (e < total) {
+                int a, b, c;
+                fc.element(e, a, b, c);
+                wi[q] = (a * E2 + b) * P3 + c;
+                wv[q] = image(a, b, c);
+            }
+        }
+        const long long limit = inject_timeout ? kInjectWaitCycles : kStageWaitCycles;
+        staged = mbar_wait_bounded(bar, 0, limit);
+        if (!staged) mbar_wait_bounded(bar, 0, limit);   // let a late copy land before exit
+#pragma unroll
+        for (int q = 0; q < kWrapAhead; ++q)
+            if (wi[q] >= 0) box[wi[q]] = wv[q];
+        for (int e = tid + kWrapAhead * nthr; e < total; e += nthr) {
+            int a, b, c;
+            fc.element(e, a, b, c);
+            box[(a * E2 + b) * P3 + c] = image(a, b, c);
         }
     } else {
         int col[2];
@@ -1310,18 +1358,19 @@ cudaError_t launch_adjoint_acc(const Dims& g, Tile t, const float* lam_in, const
                                float* b, const float* lam_first, const float* grad_first,
                                float w_first, const float* dotp, double* partials,
                                int max_partials, int* nblk_out, cudaStream_t st,
-                               const float* add) {
+                               const float* add, const Fin* fin) {
     const int nb = march_blocks(g, t);
     if (dotp && nb > max_partials) return cudaErrorInvalidValue;
     if (nblk_out) *nblk_out = nb;
+    const Fin f = (fin && dotp) ? *fin : Fin{};
     if (add)
         return run_march(g, t, lam_in, d,
                          EpiAdjAccT<true>{lam_out, c, grad, b, g.n, w, lam_first, grad_first,
-                                          w_first, dotp, partials, add},
+                                          w_first, dotp, partials, add, f},
                          st);
     return run_march(g, t, lam_in, d,
                      EpiAdjAcc{lam_out, c, grad, b, g.n, w, lam_first, grad_first, w_first, dotp,
-                               partials, nullptr},
+                               partials, nullptr, f},
                      st);
 }
 

@@ -111,6 +111,8 @@ _SIGS = {
     'reg_debug_inject': [_I, _I],
     'reg_get_timing': [_P, ctypes.POINTER(Timing)],
     'reg_get_coarse_timing': [_P, ctypes.POINTER(Timing)],
+    'reg_get_coarse_tile': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
+    'reg_set_coarse_tile': [_P, _I, _I],
     'reg_autotune': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_batch_create': [_I, _P, _I, _D, _I, _I, _I, ctypes.POINTER(_P)],
     'reg_batch_destroy': [_P],
@@ -478,6 +480,18 @@ class Registration:
         t = Timing()
         self._call('reg_get_coarse_timing', ctypes.byref(t))
         return t.as_dict()
+
+    def set_coarse_tile(self, k, wy):
+        """The coarse grid's tile: (0, 0) autotuned (default), else as given
+        (reg_set_coarse_tile)."""
+        self._call('reg_set_coarse_tile', int(k), int(wy))
+
+    def get_coarse_tile(self):
+        """(k, wy) of the two-level preconditioner's coarse grid ((0, 0)
+        without one)."""
+        k, wy = ctypes.c_int(), ctypes.c_int()
+        self._call('reg_get_coarse_tile', ctypes.byref(k), ctypes.byref(wy))
+        return k.value, wy.value
 
 
 class Batch:

@@ -96,3 +96,34 @@ def test_two_level_solve_reaches_the_same_stop_with_fewer_matvecs(reg):
         assert two['coarse_matvecs'] > 0 and one['coarse_matvecs'] == 0
     # at the small beta the coarse grid carries the ill-conditioned low modes
     assert res[1e-5, 2]['matvecs'] < res[1e-5, 0]['matvecs'], (res[1e-5, 0], res[1e-5, 2])
+
+
+def test_coarse_tile_fixed_or_autotuned(reg):
+    """The coarse grid's tile is autotuned unless set; a set tile is used as
+    given and gives the same solve up to the FP32 order of the stencil sums."""
+    shape, nt = (64, 64, 64), 4
+    rho_T, rho_R, _ = synth.phantom_problem(shape, 3000)
+    dT = torch.tensor(rho_T, dtype=torch.float32, device='cuda')
+    dR = torch.tensor(rho_R, dtype=torch.float32, device='cuda')
+    out = []
+    for tile in (None, (4, 8)):
+        R = reg.Registration(shape, nt, 1e-3, 'H2', False)
+        assert R.get_coarse_tile() == (0, 0)
+        with pytest.raises(reg.RegError):
+            R.set_coarse_tile(3, 8)
+        if tile:
+            R.set_coarse_tile(*tile)
+        R.set_images(dT, dR, presmooth=True)
+        v = torch.zeros((3,) + shape, device='cuda')
+        s, st = R.solve(v, gtol=1e-2, coarse_factor=2, coarse_tol=0.1, coarse_max=20)
+        assert s == 0
+        got = R.get_coarse_tile()
+        if tile:
+            assert got == tile
+        else:
+            assert got[0] in (1, 2, 4, 8, 16) and got[1] in (4, 8, 16), got
+        out.append((v.cpu().numpy(), st))
+        R.close()
+    (v0, s0), (v1, s1) = out
+    assert s0['gn_iters'] == s1['gn_iters']
+    assert np.linalg.norm(v1 - v0) <= 1e-3 * np.linalg.norm(v0)
