@@ -573,6 +573,15 @@ int reg_get_coarse_timing(reg_ctx* ctx, reg_timing* out);
  * linearisation. */
 int reg_set_coarse_tile(reg_ctx* ctx, int k, int wy);
 
+/* Process-wide: on = 1 (default) launches the staged interpolation steps,
+ * the incremental-state start and the PCG update, direction and loop-control
+ * kernels with programmatic stream serialisation, so that each may be
+ * scheduled while its predecessor on the stream finishes (it waits on the
+ * device for the predecessor's results before touching memory).  on = 0:
+ * ordinary launches.  Same results either way.  Applies to launches and
+ * graph captures made after the call; REG_EINVAL for other values. */
+int reg_set_dependent_launch(int on);
+
 /* The tile the coarse grid runs with now; 0, 0 without a coarse grid. */
 int reg_get_coarse_tile(const reg_ctx* ctx, int* k, int* wy);
 

@@ -49,6 +49,41 @@ __device__ __forceinline__ void lagrange4(float t, float w[4]) {
     w[3] = p * fmaf(t, 1.f / 6.f, 1.f / 6.f);
 }
 
+// Programmatic dependent launch: a kernel launched with launch_dependent()
+// may start while its predecessor on the stream is still running.  It must
+// pass pdl_wait() -- which returns once the predecessor has completed and its
+// memory operations are visible -- before it reads or writes global memory
+// that the predecessor (or anything before it) touches, and it lets its own
+// dependents start (pdl_trigger) only after that wait, so a kernel that
+// starts early can rely on everything before its predecessor being complete.
+// Both are no-ops in a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Process-wide switch of launch_dependent (reg_set_dependent_launch).
+bool dependent_launch_enabled();
+void set_dependent_launch(bool on);
+
+// Launch kern<<<grid, block, smem, st>>>(args...) with programmatic stream
+// serialisation (when enabled): the kernel must call pdl_wait() first.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t st, Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = dependent_launch_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 // Finish of a reduction kernel's per-block FP64 partial sums inside the same
 // launch (no separate launch_finalize): every block, once its partials are
 // visible, draws a ticket from an atomic counter; the block that draws the

@@ -1147,6 +1147,12 @@ int reg_get_coarse_timing(reg_ctx* c, reg_timing* out) {
     return REG_OK;
 }
 
+int reg_set_dependent_launch(int on) {
+    if (on != 0 && on != 1) return REG_EINVAL;
+    set_dependent_launch(on != 0);
+    return REG_OK;
+}
+
 int reg_set_coarse_tile(reg_ctx* c, int k, int wy) {
     CHECK_CTX(c);
     if (k == 0 && wy == 0) {

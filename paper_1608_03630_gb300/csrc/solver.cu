@@ -104,6 +104,7 @@ __global__ void k_pcg_setup(double* dsc, double tol2, int max_it) {
 // The stopping tests of one PCG iteration, in the host loop's order; a zero
 // condition ends the graph's while-loop.  The cap max_it bounds the loop.
 __global__ void k_pcg_control(double* dsc, cudaGraphConditionalHandle h) {
+    pdl_wait();
     const double it = dsc[SC_IT] + 1.0;
     dsc[SC_IT] = it;
     const double pq = dsc[SC_PQ], rr = dsc[SC_RR];
@@ -137,8 +138,9 @@ static bool add_pcg_loop(reg_ctx* c, cudaGraph_t graph) {
                                             cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
         int s = pcg_iteration(c);
         if (s == REG_OK) {
-            k_pcg_control<<<1, 1, 0, c->stream>>>(c->dsc, h);
-            if (cudaGetLastError() != cudaSuccess) s = REG_ECUDA;
+            if (launch_dependent(k_pcg_control, dim3(1), dim3(1), 0, c->stream, c->dsc, h) !=
+                cudaSuccess)
+                s = REG_ECUDA;
         }
         cudaGraph_t captured = nullptr;
         const cudaError_t e = cudaStreamEndCapture(c->stream, &captured);

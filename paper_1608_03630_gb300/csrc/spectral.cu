@@ -247,6 +247,8 @@ k_sp_update(Dims g, float2* __restrict__ s, float2* __restrict__ r, const float2
             const float2* __restrict__ B, double* sc, int irz, int ipap, int ipb, int ipq,
             float beta, float shift, int kind, int project, float inv_n, double* partials,
             Fin fin) {
+    pdl_wait();
+    pdl_trigger();
     const long long nc = g.nc;
     const double pq = sc[ipap] + sc[ipb];
     const float alpha = pq > 0.0 ? (float)(sc[irz] / pq) : 0.f;
@@ -290,6 +292,8 @@ k_sp_direction(Dims g, const float2* __restrict__ r, float2* __restrict__ p,
                float2* __restrict__ pc, const double* sc, int irznew, int irz,
                int zero_beta, float beta, float shift, int kind, int project, double* partials,
                Fin fin) {
+    pdl_wait();
+    pdl_trigger();
     const long long nc = g.nc;
     const double den = sc[irz];
     const float bk = (zero_beta || den == 0.0) ? 0.f : (float)(sc[irznew] / den);
@@ -477,10 +481,9 @@ cudaError_t launch_sp_update(const Dims& g, float2* s, float2* r, const float2* 
                              double beta, double shift, int kind, int project,
                              double* partials, int nblk, cudaStream_t st, const Fin* fin) {
     const Fin f = fin ? *fin : Fin{};
-    k_sp_update<<<nblk, kThreads, 0, st>>>(g, s, r, p, B, sc, irz, ipap, ipb, ipq, (float)beta,
-                                           (float)shift, kind, project, 1.0f / (float)g.n,
-                                           partials, f);
-    return cudaGetLastError();
+    return launch_dependent(k_sp_update, dim3(nblk), dim3(kThreads), 0, st, g, s, r, p, B, sc,
+                            irz, ipap, ipb, ipq, (float)beta, (float)shift, kind, project,
+                            1.0f / (float)g.n, partials, f);
 }
 
 cudaError_t launch_sp_direction(const Dims& g, const float2* r, float2* p, float2* pc,
@@ -489,10 +492,9 @@ cudaError_t launch_sp_direction(const Dims& g, const float2* r, float2* p, float
                                 double* partials, int nblk, cudaStream_t st,
                                 const Fin* fin) {
     const Fin f = fin ? *fin : Fin{};
-    k_sp_direction<<<nblk, kThreads, 0, st>>>(g, r, p, pc, sc, irznew, irz, zero_beta,
-                                              (float)beta, (float)shift, kind, project,
-                                              partials, f);
-    return cudaGetLastError();
+    return launch_dependent(k_sp_direction, dim3(nblk), dim3(kThreads), 0, st, g, r, p, pc, sc,
+                            irznew, irz, zero_beta, (float)beta, (float)shift, kind, project,
+                            partials, f);
 }
 
 cudaError_t launch_sp_gradient(const Dims& g, const float2* v, const float2* B, float2* gout,

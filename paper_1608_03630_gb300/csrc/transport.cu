@@ -869,6 +869,8 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
     const int kend = min(K, g.n1 - i1b);
     uint64_t* bar = reinterpret_cast<uint64_t*>(box + E1 * E23);
     const bool tma = use_tma && (smem_u32(box) & 127u) == 0;
+    pdl_wait();      // the previous step's level is this step's input
+    pdl_trigger();
     if (tma) {
         if (tid == 0) mbar_init(bar, 1);
         __syncthreads();
@@ -1056,9 +1058,8 @@ cudaError_t run_tile_fixed(const Dims& g, Tile t, const float* f, const float* d
     CUtensorMap map;
     const int use_tma = t.tma && box_tensor_map(&map, g, f, E1, E2) ? 1 : 0;
     const int inject = use_tma && g_inject_stage.exchange(0) ? 1 : 0;
-    k_tile_fixed<Epi, H, WY><<<march_grid(g, t), dim3(32, WY), smem, st>>>(g, t.k, f, d, epi, map,
-                                                                            use_tma, inject);
-    return cudaGetLastError();
+    return launch_dependent(k_tile_fixed<Epi, H, WY>, march_grid(g, t), dim3(32, WY), smem, st,
+                            g, t.k, f, d, epi, map, use_tma, inject);
 }
 
 // Tricubic value at displacement (e1, e2, e3) (grid units) of the point of
@@ -1243,6 +1244,8 @@ __global__ void k_absmax(const float* __restrict__ d, long long count, unsigned 
 __global__ void __launch_bounds__(kThreads)
 k_incstate_init(Dims g, const float* __restrict__ vt, const float* __restrict__ g0, float dt,
                 float* __restrict__ u0) {
+    pdl_wait();
+    pdl_trigger();
     const int idx = blockIdx.x * kThreads + threadIdx.x;
     if (idx >= g.n) return;
     const long long n = g.n;
@@ -1294,6 +1297,12 @@ __global__ void k_from_bf16(const __nv_bfloat16* __restrict__ in, float* __restr
 }  // namespace
 
 void arm_stage_timeout(int on) { g_inject_stage.store(on ? 1 : 0); }
+
+namespace {
+std::atomic<bool> g_dependent_launch{true};
+}
+bool dependent_launch_enabled() { return g_dependent_launch.load(std::memory_order_relaxed); }
+void set_dependent_launch(bool on) { g_dependent_launch.store(on); }
 
 cudaError_t launch_absmax(const float* d, long long count, unsigned int* out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned int), st);
@@ -1481,8 +1490,8 @@ cudaError_t launch_incstate_step(const Dims& g, Tile t, const float* u_in, const
 
 cudaError_t launch_incstate_init(const Dims& g, const float* vt, const float* grad0, float dt,
                                  float* u0, cudaStream_t st) {
-    k_incstate_init<<<nblocks(g.n), kThreads, 0, st>>>(g, vt, grad0, dt, u0);
-    return cudaGetLastError();
+    return launch_dependent(k_incstate_init, dim3(nblocks(g.n)), dim3(kThreads), 0, st, g, vt,
+                            grad0, dt, u0);
 }
 
 

@@ -113,6 +113,7 @@ _SIGS = {
     'reg_get_coarse_timing': [_P, ctypes.POINTER(Timing)],
     'reg_get_coarse_tile': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_set_coarse_tile': [_P, _I, _I],
+    'reg_set_dependent_launch': [_I],
     'reg_autotune': [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)],
     'reg_batch_create': [_I, _P, _I, _D, _I, _I, _I, ctypes.POINTER(_P)],
     'reg_batch_destroy': [_P],
@@ -188,6 +189,14 @@ def _ptr(t, shape=None, what='tensor'):
     if shape is not None and tuple(t.shape) != tuple(shape):
         raise ValueError('%s has shape %s, expected %s' % (what, tuple(t.shape), tuple(shape)))
     return ctypes.c_void_p(t.data_ptr())
+
+
+def set_dependent_launch(on):
+    """Process-wide: programmatic dependent launches of the PCG-path kernels
+    (True, the default) or ordinary launches (reg_set_dependent_launch)."""
+    s = lib().reg_set_dependent_launch(1 if on else 0)
+    if s != 0:
+        raise RegError(s, 'reg_set_dependent_launch failed')
 
 
 def state_transport_noalloc(rho0, d_fwd, rho1, nt, stream=None):
