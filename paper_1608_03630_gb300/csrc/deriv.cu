@@ -381,7 +381,7 @@ __device__ __forceinline__ void tile_store(const float2* buf, float* __restrict_
 }
 
 template <int N1, int N2, int AXIS>
-__global__ void __launch_bounds__(16 * N2)
+__global__ void __launch_bounds__(16 * N2, 3)
 k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumulate) {
     constexpr int N = N1 * N2;
     constexpr int S = N + 1;                       // load buffer line stride

@@ -76,6 +76,16 @@ def test_null_context_is_rejected(lib):
     assert lib.reg_solve(None, None, None, None) == 1
     assert lib.reg_set_staging(None, 1) == 1
     assert lib.reg_unet_set_mma(None, 1) == 1
+    assert lib.reg_set_coarse_tile(None, 2, 8) == 1
+    assert lib.reg_get_coarse_tile(None, None, None) == 1
+
+
+def test_dependent_launch_switch(lib):
+    """The process-wide launch switch takes 0 or 1 and touches no GPU."""
+    assert lib.reg_set_dependent_launch(2) == 1
+    assert lib.reg_set_dependent_launch(-1) == 1
+    assert lib.reg_set_dependent_launch(0) == 0
+    assert lib.reg_set_dependent_launch(1) == 0
 
 
 def test_fault_injection_arguments(lib):

@@ -127,3 +127,32 @@ def test_coarse_tile_fixed_or_autotuned(reg):
     (v0, s0), (v1, s1) = out
     assert s0['gn_iters'] == s1['gn_iters']
     assert np.linalg.norm(v1 - v0) <= 1e-3 * np.linalg.norm(v0)
+
+
+def test_dependent_launches_change_nothing(reg):
+    """With programmatic dependent launches (the default) every kernel still
+    waits on the device for its predecessor's results: a two-level solve
+    (fine and coarse PCG graphs) gives the same iterates bit for bit as with
+    ordinary launches."""
+    shape, nt = (64, 64, 64), 4
+    rho_T, rho_R, _ = synth.phantom_problem(shape, 3100)
+    dT = torch.tensor(rho_T, dtype=torch.float32, device='cuda')
+    dR = torch.tensor(rho_R, dtype=torch.float32, device='cuda')
+    out = []
+    try:
+        for on in (False, True):
+            reg.set_dependent_launch(on)
+            R = reg.Registration(shape, nt, 1e-3, 'H2', False)
+            R.set_coarse_tile(2, 8)
+            R.set_images(dT, dR, presmooth=True)
+            v = torch.zeros((3,) + shape, device='cuda')
+            s, st = R.solve(v, gtol=1e-2, coarse_factor=2, coarse_tol=0.1, coarse_max=20)
+            assert s == 0
+            out.append((v.cpu().numpy(), st))
+            R.close()
+    finally:
+        reg.set_dependent_launch(True)
+    (v0, s0), (v1, s1) = out
+    assert s0['pcg_iters'] == s1['pcg_iters'] and s0['coarse_matvecs'] == s1['coarse_matvecs']
+    assert np.array_equal(v0, v1)
+    assert reg.lib().reg_set_dependent_launch(2) == 1   # REG_EINVAL
