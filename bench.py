@@ -441,6 +441,23 @@ def gpu_bench(args):
         torch.cuda.synchronize()
         e2e_s = e4.elapsed_time(e5) / 1e3 / args.steps
 
+        # the Gauss-Newton Hessian matvec alone, as PCG applies it: normalised
+        # coefficients in and out (inverse transform of p, the 2 nt
+        # transports with the time integral, forward transform, assembly),
+        # at the last linearisation point of the solve
+        p_hat = 1e-3 * torch.randn(R.sshape, dtype=torch.complex64, device='cuda')
+        q_hat = torch.empty_like(p_hat)
+        for _ in range(3):
+            R.hessian_matvec_spectral(p_hat, out=q_hat)
+        torch.cuda.synchronize()
+        e6, e7 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e6.record(stream)
+        for _ in range(20):
+            R.hessian_matvec_spectral(p_hat, out=q_hat)
+        e7.record(stream)
+        torch.cuda.synchronize()
+        matvec_ms = e6.elapsed_time(e7) / 20
+
         # the other forms of the method, the faster of two timed solves each after a warm-up,
         # to the same stopping test (the plain FP32 solver is the target's
         # comparison)
@@ -546,6 +563,8 @@ def gpu_bench(args):
         'speedup_vs_plain_fp32': (arms['plain_fp32']['time_to_solution_s'] / value
                                   if 'plain_fp32' in arms else 1.0),
         'matvecs_per_s': matvecs / (elapsed_ms / 1e3),
+        'matvec_256': {'ms': matvec_ms, 'per_s': 1e3 / matvec_ms, 'nt': NT,
+                       'form': 'Gauss-Newton, coefficients in and out, %s' % args.precision},
         'phased_ms_per_step': phased_ms / args.steps,
         'interp_gbs': ib / (ims / 1e3) / 1e9 if ims > 0 else None,
         'spectral_gbs': sb / (sms / 1e3) / 1e9 if sms > 0 else None,

@@ -491,6 +491,17 @@ __device__ __forceinline__ void tma_load_box(float* dst, const CUtensorMap* map,
         : "memory");
 }
 
+// Box of a 4-D tensor map at element coordinates (x3, x2, x1, component).
+__device__ __forceinline__ void tma_load_box4(float* dst, const CUtensorMap* map, uint64_t* bar,
+                                              int x, int y, int z, int w) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(w),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
 // ------------------------------------------- shared-memory staged kernel
 // The block's output tile is 32 (x3) x wy (x2) x k (x1) points.  With every
 // |floor(d)| <= H, the stencils of the tile lie in the box of
@@ -1167,6 +1178,204 @@ k_departure_tile(Dims g, int K, const float* __restrict__ v, float dth1, float d
     }
 }
 
+// Tricubic values of the three velocity components at displacement (e1, e2,
+// e3) of local point (kloc, r2, r3) from their staged boxes (component c at
+// box + c * BOX, pitch 64): one set of weights for the three gathers, each in
+// the operation order of box_interp.
+template <int H, int WY, int E1>
+__device__ __forceinline__ void box_interp3(const float* box, int kloc, int r2, int r3, float e1,
+                                            float e2, float e3, float (&out)[3]) {
+    constexpr int E2 = WY + 3 + 2 * H;
+    constexpr int P3 = 64;
+    constexpr int E23 = E2 * P3;
+    constexpr int BOX = E1 * E23;
+    const float fl1 = floorf(e1), fl2 = floorf(e2), fl3 = floorf(e3);
+    float w1[4], w2[4], w3[4];
+    lagrange4(e1 - fl1, w1);
+    lagrange4(e2 - fl2, w2);
+    lagrange4(e3 - fl3, w3);
+    const int l1 = min(max(kloc + H + (int)fl1, 0), E1 - 4);
+    const int l2 = min(max(r2 + (int)fl2, 0), E2 - 4);
+    const int l3 = min(max(r3 + (int)fl3, 0), P3 - 4);
+    const f32x2 w2a = pk(w2[0], w2[1]), w2b = pk(w2[2], w2[3]);
+    f32x2 ww3[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) ww3[c] = pk(w3[c], w3[c]);
+#pragma unroll
+    for (int comp = 0; comp < 3; ++comp) {
+        const float* base = box + comp * BOX + (l1 * E2 + l2) * P3 + l3;
+        float r[4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const float* pl = base + a * E23;
+            f32x2 s01 = mul2(ww3[0], pk(pl[0], pl[P3]));
+            f32x2 s23 = mul2(ww3[0], pk(pl[2 * P3], pl[3 * P3]));
+#pragma unroll
+            for (int c = 1; c < 4; ++c) {
+                s01 = fma2(ww3[c], pk(pl[c], pl[P3 + c]), s01);
+                s23 = fma2(ww3[c], pk(pl[2 * P3 + c], pl[3 * P3 + c]), s23);
+            }
+            const float2 t2 = upk(fma2(w2b, s23, mul2(w2a, s01)));
+            r[a] = t2.x + t2.y;
+        }
+        float val = w1[0] * r[0];
+        val = fmaf(w1[1], r[1], val);
+        val = fmaf(w1[2], r[2], val);
+        out[comp] = fmaf(w1[3], r[3], val);
+    }
+}
+
+// RK2 points of v and -v (Eq. sml-trajectory) from ONE tensor copy of the
+// three velocity components' boxes ([3][E1][E2][64] floats, a 4-D tensor map
+// over the component-major field; the copy reads zeros outside the grid and
+// the block reloads those elements from their periodic images, the loads
+// issued while the copy is in flight).  Each foot's weights serve the three
+// components, and the point's own velocity comes from the box.  Tile: 4
+// points along x1, 8 rows, 32 columns; |u| <= H.  A block whose wait for the
+// copy gives up (bounded) writes NaN.  Same values as k_departure_tile.
+constexpr int kDepK = 4;
+
+template <int H>
+__global__ void __launch_bounds__(256)
+k_departure_fixed(Dims g, const float* __restrict__ v, float dth1, float dth2, float dth3,
+                  float* __restrict__ d_fwd, float* __restrict__ d_adj,
+                  const __grid_constant__ CUtensorMap map, int inject_timeout) {
+    constexpr int K = kDepK, WY = 8;
+    constexpr int E1 = K + 3 + 2 * H, E2 = WY + 3 + 2 * H, P3 = 64;
+    constexpr int C0 = 3 - H, C1 = 38 + H;
+    constexpr int E23 = E2 * P3, BOX = E1 * E23;
+    extern __shared__ __align__(128) float box[];   // [3][E1][E2][P3], then the mbarrier
+    const int lane = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + lane;
+    const int i3 = blockIdx.x * 32 + lane, i2 = blockIdx.y * WY + ty, i1b = blockIdx.z * K;
+    const int o1 = i1b - 1 - H, o2 = blockIdx.y * WY - 1 - H, o3 = blockIdx.x * 32 - 4;
+    const bool active = i3 < g.n3 && i2 < g.n2;
+    const int kend = min(K, g.n1 - i1b);
+    const long long n = g.n;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(box + 3 * BOX);
+    // the tensor copy wants a 128-byte aligned destination; otherwise every
+    // element is loaded as a periodic image (the whole box counts as outside)
+    const bool tma = (smem_u32(box) & 127u) == 0;
+    if (tma) {
+        if (tid == 0) mbar_init(bar, 1);
+        __syncthreads();
+        if (tid == 0) {
+            mbar_expect_tx(bar, (unsigned)(sizeof(float) * 3 * BOX));
+            if (!inject_timeout) tma_load_box4(box, &map, bar, o3, o2, o1, 0);
+        }
+    }
+    const int a_lo = tma ? min(max(-o1, 0), E1) : 0;
+    const int a_hi = tma ? max(min(g.n1 - o1, E1), a_lo) : 0;
+    const int b_lo = min(max(-o2, 0), E2), b_hi = max(min(g.n2 - o2, E2), b_lo);
+    const int c_lo = min(max(-o3, C0), C1), c_hi = max(min(g.n3 - o3, C1), c_lo);
+    const Faces<E2, C0, C1> fc{E1, a_lo, a_hi, b_lo, b_hi, c_lo, c_hi};
+    const int per = fc.count(), total = 3 * per;   // every component's images
+    auto image = [&](int e, int& at) {
+        const int comp = e / per;
+        int a, b, c;
+        fc.element(e - comp * per, a, b, c);
+        at = comp * BOX + (a * E2 + b) * P3 + c;
+        return __ldg(v + comp * n + (long long)wrap_near(o1 + a, g.n1) * g.n23 +
+                     wrap_near(o2 + b, g.n2) * g.n3 + wrap_near(o3 + c, g.n3));
+    };
+    float wv[kWrapAhead];
+    int wi[kWrapAhead];
+#pragma unroll
+    for (int q = 0; q < kWrapAhead; ++q) {
+        const int e = tid + q * 256;
+        wi[q] = -1;
+        if (e < total) wv[q] = image(e, wi[q]);
+    }
+    bool staged = true;
+    if (tma) {
+        const long long limit = inject_timeout ? kInjectWaitCycles : kStageWaitCycles;
+        staged = mbar_wait_bounded(bar, 0, limit);
+        if (!staged) mbar_wait_bounded(bar, 0, limit);   // let a late copy land before exit
+    }
+#pragma unroll
+    for (int q = 0; q < kWrapAhead; ++q)
+        if (wi[q] >= 0) box[wi[q]] = wv[q];
+    for (int e = tid + kWrapAhead * 256; e < total; e += 256) {
+        int at;
+        const float x = image(e, at);
+        box[at] = x;
+    }
+    __syncthreads();
+    if (!active) return;
+    const int r2 = ty + H, r3 = lane + 3;   // i2 - 1 - o2, i3 - 1 - o3
+    const float dth[3] = {dth1, dth2, dth3};
+    for (int k = 0; k < kend; ++k) {
+        const int idx = ((i1b + k) * g.n2 + i2) * g.n3 + i3;
+        const int ctr = ((k + 1 + H) * E2 + ty + 1 + H) * P3 + lane + 4;
+        const float u[3] = {box[ctr] * dth1, box[BOX + ctr] * dth2, box[2 * BOX + ctr] * dth3};
+        float a[3];
+        // forward: X* = x - u, X = x - (u + dt v(X*)) / 2
+        box_interp3<H, WY, E1>(box, k, r2, r3, -u[0], -u[1], -u[2], a);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float af = a[c] * dth[c];
+            d_fwd[c * n + idx] = staged ? -0.5f * (u[c] + af) : __int_as_float(0x7fffffff);
+        }
+        if (d_adj) {
+            // adjoint (velocity -v): X* = x + u, X = x + (u + dt v(X*)) / 2
+            box_interp3<H, WY, E1>(box, k, r2, r3, u[0], u[1], u[2], a);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float aa = a[c] * dth[c];
+                d_adj[c * n + idx] = staged ? 0.5f * (u[c] + aa) : __int_as_float(0x7fffffff);
+            }
+        }
+    }
+}
+
+// Tensor map of the velocity (3 x n1 x n2 x n3, x3 fastest) with a box of
+// 64 x E2 x E1 x 3 elements; false unless rows are whole 16-byte units, v is
+// 16-byte aligned and the grid is at least one box large.
+bool velocity_tensor_map(CUtensorMap* map, const Dims& g, const float* v, int E1, int E2) {
+    std::memset(map, 0, sizeof(*map));
+    if (g.n3 % 4 || g.n3 < 64 || g.n2 < E2 || g.n1 < E1 || E1 > 256 || E2 > 256 ||
+        (reinterpret_cast<uintptr_t>(v) & 15))
+        return false;
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dim[4] = {(cuuint64_t)g.n3, (cuuint64_t)g.n2, (cuuint64_t)g.n1, 3};
+    const cuuint64_t stride[3] = {sizeof(float) * (cuuint64_t)g.n3,
+                                  sizeof(float) * (cuuint64_t)g.n23,
+                                  sizeof(float) * (cuuint64_t)g.n};
+    const cuuint32_t boxd[4] = {64, (cuuint32_t)E2, (cuuint32_t)E1, 3};
+    const cuuint32_t estride[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float*>(v), dim, stride, boxd,
+               estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+// The TMA-staged departure kernel when its tensor map can be made; false
+// (nothing launched) otherwise.
+template <int H>
+bool run_departure_fixed(const Dims& g, const float* v, float dth1, float dth2, float dth3,
+                         float* d_fwd, float* d_adj, cudaStream_t st, cudaError_t* err) {
+    constexpr int E1 = kDepK + 3 + 2 * H, E2 = 8 + 3 + 2 * H;
+    const size_t smem = sizeof(float) * 3 * (size_t)E1 * E2 * 64 + 16;
+    CUtensorMap map;
+    if (!velocity_tensor_map(&map, g, v, E1, E2)) return false;
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [&] {
+        attr = cudaFuncSetAttribute(k_departure_fixed<H>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    });
+    if (attr != cudaSuccess) {
+        *err = attr;
+        return true;
+    }
+    const int inject = g_inject_stage.exchange(0) ? 1 : 0;
+    const dim3 grid((g.n3 + 31) / 32, (g.n2 + 7) / 8, (g.n1 + kDepK - 1) / kDepK);
+    k_departure_fixed<H><<<grid, dim3(32, 8), smem, st>>>(g, v, dth1, dth2, dth3, d_fwd, d_adj,
+                                                          map, inject);
+    *err = cudaGetLastError();
+    return true;
+}
+
 template <int H>
 cudaError_t run_departure_tile(const Dims& g, Tile t, const float* v, float dth1, float dth2,
                                float dth3, float* d_fwd, float* d_adj, cudaStream_t st) {
@@ -1334,6 +1543,15 @@ cudaError_t launch_departure(const Dims& g, Tile t, const float* v, float dt, fl
                              float* d_adj, cudaStream_t st) {
     const float two_pi = 6.283185307179586f;
     const float dth1 = dt * g.n1 / two_pi, dth2 = dt * g.n2 / two_pi, dth3 = dt * g.n3 / two_pi;
+    if (t.halo >= 0 && t.halo <= 3 && t.tma) {
+        // one tensor copy of the three components' boxes per block
+        cudaError_t e = cudaSuccess;
+        bool done;
+        if (t.halo <= 1) done = run_departure_fixed<1>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e);
+        else if (t.halo == 2) done = run_departure_fixed<2>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e);
+        else done = run_departure_fixed<3>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e);
+        if (done) return e;
+    }
     if (t.halo >= 0 && t.halo <= 3 && t.wy == 8 && tile_staged(t)) {
         if (t.halo <= 1) return run_departure_tile<1>(g, t, v, dth1, dth2, dth3, d_fwd, d_adj, st);
         if (t.halo == 2) return run_departure_tile<2>(g, t, v, dth1, dth2, dth3, d_fwd, d_adj, st);

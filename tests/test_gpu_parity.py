@@ -78,6 +78,28 @@ def test_departure_points(reg, shape, amp):
     R.close()
 
 
+@pytest.mark.parametrize('shape', [(20, 24, 68), (16, 40, 64), (36, 20, 128)])
+@pytest.mark.parametrize('amp', [0.3, 0.6, 1.0])
+def test_departure_points_staged_by_one_tensor_copy(reg, shape, amp):
+    """Rows of 64 or more points: one tensor copy stages the three velocity
+    components' boxes of a block (halo 1 to 3 for these amplitudes, faces
+    reloaded from their periodic images); the points equal the oracle's to
+    2e-5 and, bit for bit, those of the per-thread staged kernel (same
+    arithmetic in the same order)."""
+    nt = 4
+    v = f32(amp * synth.bandlimited(shape, 3, 7))
+    R = reg.Registration(shape, nt, 1e-2)
+    df, da = [host(t) for t in R.departure(dev(v))]
+    R.set_staging(False)
+    df0, da0 = [host(t) for t in R.departure(dev(v))]
+    R.close()
+    ef = otr.departure(v, 1.0 / nt)
+    ea = otr.departure(-v, 1.0 / nt)
+    assert np.abs(df - ef).max() < 2e-5 * max(1.0, np.abs(ef).max())
+    assert np.abs(da - ea).max() < 2e-5 * max(1.0, np.abs(ea).max())
+    assert np.array_equal(df, df0) and np.array_equal(da, da0)
+
+
 @pytest.mark.parametrize('shape', SHAPES)
 @pytest.mark.parametrize('nf', [1, 2, 3])
 def test_interpolation_with_large_displacements(reg, shape, nf):
