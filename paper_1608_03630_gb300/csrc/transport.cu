@@ -202,6 +202,7 @@ __device__ __forceinline__ float march_interp(Window& W, const float* __restrict
 // threads of the block, for reductions).
 
 struct EpiStore {            // out = val
+    static constexpr bool kPreFixed = true;
     float* out;
     struct Pre {};
     __device__ Pre pre(int) const { return {}; }
@@ -210,6 +211,7 @@ struct EpiStore {            // out = val
 };
 
 struct EpiStateFinal {       // out = val; lam = rho_R - val; sum (val - rho_R)^2
+    static constexpr bool kPreFixed = true;
     float* out;
     const float* rho_R;
     float* lam;              // may be null
@@ -240,6 +242,7 @@ struct EpiStateFinal {       // out = val; lam = rho_R - val; sum (val - rho_R)^
 // more.
 template <bool kAdd>
 struct EpiAdjAccT {
+    static constexpr bool kPreFixed = false;   // b: the previous step's output
     float* out;
     const float* c;          // may be null (c = 1)
     const float* grad;       // grad rho_j [3n]
@@ -302,6 +305,7 @@ using EpiAdjAcc = EpiAdjAccT<false>;
 // (dv = div v; 0 when divergence free).  This epilogue writes the last two
 // terms, val = I[s_old](X).
 struct EpiSrcAdd {
+    static constexpr bool kPreFixed = false;   // s_new: written just before
     float* out;
     const float* divv;       // may be null
     const float* s_new;
@@ -318,6 +322,7 @@ struct EpiSrcAdd {
 };
 
 struct EpiCoef {             // c = 1 + dt/2 (dX + dv + dt dX dv), val = dX
+    static constexpr bool kPreFixed = false;   // div v: written just before
     float* out;
     const float* divv;
     float dt;
@@ -330,6 +335,7 @@ struct EpiCoef {             // c = 1 + dt/2 (dX + dv + dt dX dv), val = dX
 };
 
 struct EpiIncState {         // u_{j+1} = val + dt f_{j+1}; final: lam~ = -(val + dt/2 f_nt)
+    static constexpr bool kPreFixed = true;    // v~, grad rho_{j+1}: not the previous step's
     float* out;
     const float* vt;
     const float* gj1;
@@ -880,6 +886,17 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
     const int kend = min(K, g.n1 - i1b);
     uint64_t* bar = reinterpret_cast<uint64_t*>(box + E1 * E23);
     const bool tma = use_tma && (smem_u32(box) & 127u) == 0;
+    // the first two points' inputs: before the wait for the previous step
+    // where none of them is that step's output (the displacements never
+    // are; Epi::kPreFixed says whether the epilogue's are)
+    Ahead<Epi> ah[2];
+    auto prefetch = [&]() {
+        if (active) {
+            if (0 < kend) fetch(ah[0], d, g, epi, i1b, i2, i3);
+            if (1 < kend) fetch(ah[1], d, g, epi, i1b + 1, i2, i3);
+        }
+    };
+    if constexpr (Epi::kPreFixed) prefetch();
     pdl_wait();      // the previous step's level is this step's input
     pdl_trigger();
     if (tma) {
@@ -890,11 +907,7 @@ k_tile_fixed(Dims g, int K, const float* __restrict__ f, const float* __restrict
             if (!inject_timeout) tma_load_box(box, &box_map, bar, o3, o2, o1);
         }
     }
-    Ahead<Epi> ah[2];
-    if (active) {
-        if (0 < kend) fetch(ah[0], d, g, epi, i1b, i2, i3);
-        if (1 < kend) fetch(ah[1], d, g, epi, i1b + 1, i2, i3);
-    }
+    if constexpr (!Epi::kPreFixed) prefetch();
     bool staged = true;
     if (tma) {
         // the copy reads zeros outside the grid: those elements come from
