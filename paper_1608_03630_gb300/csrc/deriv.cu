@@ -294,49 +294,59 @@ __device__ __forceinline__ void fourstep(float2 (&v)[N1], float2* T, const float
 // is (c, 4 consecutive positions), read as one float4 from each real line
 // and stored as 4 complex values; AXIS 0 / 1: a unit is (position, 4
 // neighbouring real lines), one float4 of a row, stored as two complex values.
+template <int N, int TH, int AXIS>
+struct TileRegs {   // one thread's share of a block tile, between load and store
+    static constexpr int U = AXIS == 2 ? 16 * (N / 4) : 8 * N;
+    static_assert(U % TH == 0, "units per thread");
+    float4 x[U / TH][AXIS == 2 ? 2 : 1];
+};
+
+template <int N, int TH, int AXIS>
+__device__ __forceinline__ void tile_fetch(TileRegs<N, TH, AXIS>& r, const float* __restrict__ f,
+                                           long long base, long long astride) {
+    constexpr int Q = TileRegs<N, TH, AXIS>::U / TH;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int u = threadIdx.x + q * TH;
+        if constexpr (AXIS == 2) {
+            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
+            const float* src = f + base + (long long)(2 * c) * N + a;
+            r.x[q][0] = __ldg(reinterpret_cast<const float4*>(src));
+            r.x[q][1] = __ldg(reinterpret_cast<const float4*>(src + N));
+        } else {
+            const int a = u >> 3, l4 = 4 * (u & 7);
+            r.x[q][0] = __ldg(reinterpret_cast<const float4*>(f + base + l4 + a * astride));
+        }
+    }
+}
+
+template <int N, int S, int TH, int AXIS>
+__device__ __forceinline__ void tile_put(float2* buf, const TileRegs<N, TH, AXIS>& r) {
+    constexpr int Q = TileRegs<N, TH, AXIS>::U / TH;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int u = threadIdx.x + q * TH;
+        if constexpr (AXIS == 2) {
+            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
+            float2* d = buf + c * S + a;
+            d[0] = make_float2(r.x[q][0].x, r.x[q][1].x);
+            d[1] = make_float2(r.x[q][0].y, r.x[q][1].y);
+            d[2] = make_float2(r.x[q][0].z, r.x[q][1].z);
+            d[3] = make_float2(r.x[q][0].w, r.x[q][1].w);
+        } else {
+            const int a = u >> 3, c = 2 * (u & 7);
+            buf[c * S + a] = make_float2(r.x[q][0].x, r.x[q][0].y);
+            buf[(c + 1) * S + a] = make_float2(r.x[q][0].z, r.x[q][0].w);
+        }
+    }
+}
+
 template <int N, int S, int TH, int AXIS>
 __device__ __forceinline__ void tile_load(float2* buf, const float* __restrict__ f, long long base,
                                           long long astride) {
-    if constexpr (AXIS == 2) {
-        constexpr int U = 16 * (N / 4);
-        static_assert(U % TH == 0, "units per thread");
-        float4 x[U / TH][2];
-#pragma unroll
-        for (int q = 0; q < U / TH; ++q) {
-            const int u = threadIdx.x + q * TH;
-            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
-            const float* src = f + base + (long long)(2 * c) * N + a;
-            x[q][0] = __ldg(reinterpret_cast<const float4*>(src));
-            x[q][1] = __ldg(reinterpret_cast<const float4*>(src + N));
-        }
-#pragma unroll
-        for (int q = 0; q < U / TH; ++q) {
-            const int u = threadIdx.x + q * TH;
-            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
-            float2* d = buf + c * S + a;
-            d[0] = make_float2(x[q][0].x, x[q][1].x);
-            d[1] = make_float2(x[q][0].y, x[q][1].y);
-            d[2] = make_float2(x[q][0].z, x[q][1].z);
-            d[3] = make_float2(x[q][0].w, x[q][1].w);
-        }
-    } else {
-        constexpr int U = 8 * N;
-        static_assert(U % TH == 0, "units per thread");
-        float4 x[U / TH];
-#pragma unroll
-        for (int q = 0; q < U / TH; ++q) {
-            const int u = threadIdx.x + q * TH;
-            const int a = u >> 3, l4 = 4 * (u & 7);
-            x[q] = __ldg(reinterpret_cast<const float4*>(f + base + l4 + a * astride));
-        }
-#pragma unroll
-        for (int q = 0; q < U / TH; ++q) {
-            const int u = threadIdx.x + q * TH;
-            const int a = u >> 3, c = 2 * (u & 7);
-            buf[c * S + a] = make_float2(x[q].x, x[q].y);
-            buf[(c + 1) * S + a] = make_float2(x[q].z, x[q].w);
-        }
-    }
+    TileRegs<N, TH, AXIS> r;
+    tile_fetch<N, TH, AXIS>(r, f, base, astride);
+    tile_put<N, S, TH, AXIS>(buf, r);
 }
 
 template <int N, int S, int TH, int AXIS>
@@ -404,13 +414,23 @@ k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accu
         if (AXIS == 1) { base = (long long)fixed * g.n23 + col0; astride = g.n3; }
         else { base = (long long)fixed * g.n3 + col0; astride = g.n23; }
     }
-    tile_load<N, S, TH, AXIS>(buf, f, base, astride);
-    __syncthreads();
     const int line = threadIdx.x / N2, t = threadIdx.x - line * N2;
     float2 v[N1];
+    if constexpr (AXIS == 2) {
+        // rows are contiguous: each thread loads its stride-N2 elements of
+        // the two real rows of its complex line straight into registers
+        // (a warp reads 64-byte row segments); no staging pass
+        const float* r0 = f + base + (long long)(2 * line) * N + t;
 #pragma unroll
-    for (int m = 0; m < N1; ++m) v[m] = buf[line * S + t + N2 * m];
-    __syncthreads();                               // buf becomes the transpose buffer
+        for (int m = 0; m < N1; ++m) v[m] = make_float2(__ldg(r0 + N2 * m), __ldg(r0 + N + N2 * m));
+        __syncthreads();                           // the twiddle table
+    } else {
+        tile_load<N, S, TH, AXIS>(buf, f, base, astride);
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < N1; ++m) v[m] = buf[line * S + t + N2 * m];
+        __syncthreads();                           // buf becomes the transpose buffer
+    }
     fourstep<N1, N2>(v, buf, tw, line, t, false);
     // i k' / N at k = t + N2 m (Nyquist 0)
     const float inv_n = 1.0f / (float)N;
@@ -421,11 +441,26 @@ k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accu
         v[m] = make_float2(-kk * inv_n * v[m].y, kk * inv_n * v[m].x);
     }
     fourstep<N1, N2>(v, buf, tw, line, t, true);
+    if constexpr (AXIS == 2) {
+        float* o0 = out + base + (long long)(2 * line) * N + t;
 #pragma unroll
-    for (int m = 0; m < N1; ++m) buf[line * S + t + N2 * m] = v[m];
-    __syncthreads();
-    tile_store<N, S, TH, AXIS>(buf, out, base, astride, accumulate);
+        for (int m = 0; m < N1; ++m) {
+            float re = v[m].x, im = v[m].y;
+            if (accumulate) {
+                re += o0[N2 * m];
+                im += o0[N + N2 * m];
+            }
+            o0[N2 * m] = re;
+            o0[N + N2 * m] = im;
+        }
+    } else {
+#pragma unroll
+        for (int m = 0; m < N1; ++m) buf[line * S + t + N2 * m] = v[m];
+        __syncthreads();
+        tile_store<N, S, TH, AXIS>(buf, out, base, astride, accumulate);
+    }
 }
+
 
 template <int N1, int N2, int AXIS>
 cudaError_t run_deriv_r(const Dims& g, const float* f, float* out, int accumulate,
