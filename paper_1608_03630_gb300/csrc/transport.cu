@@ -329,7 +329,10 @@ struct EpiCoef {             // c = 1 + dt/2 (dX + dv + dt dX dv), val = dX
     struct Pre { float dv; };
     __device__ Pre pre(int idx) const { return {__ldg(divv + idx)}; }
     __device__ void post(int idx, float val, const Pre& p, double&) const {
-        out[idx] = 1.f + 0.5f * dt * (val + p.dv + dt * val * p.dv);
+        // explicit fused operations: the same rounding at every inlined
+        // call site of the point routine (the compiler's contraction choices
+        // may differ between sites)
+        out[idx] = fmaf(0.5f * dt, fmaf(dt * val, p.dv, val + p.dv), 1.f);
     }
     __device__ void done(double) const {}
 };
@@ -348,7 +351,8 @@ struct EpiIncState {         // u_{j+1} = val + dt f_{j+1}; final: lam~ = -(val 
                 ld(gj1, idx), ld(gj1, n + idx), ld(gj1, 2 * n + idx)};
     }
     __device__ void post(int idx, float val, const Pre& p, double&) const {
-        const float f = -(p.v0 * p.g0 + p.v1 * p.g1 + p.v2 * p.g2);
+        // explicit fused operations (see EpiCoef)
+        const float f = -fmaf(p.v2, p.g2, fmaf(p.v1, p.g1, p.v0 * p.g0));
         out[idx] = final_step ? -fmaf(0.5f * dt, f, val) : fmaf(dt, f, val);
     }
     __device__ void done(double) const {}
@@ -1180,12 +1184,12 @@ k_departure_tile(Dims g, int K, const float* __restrict__ v, float dth1, float d
             const float u3 = __ldg(v + 2 * n + idx) * dth3;
             const float uc = comp == 0 ? u1 : (comp == 1 ? u2 : u3);
             // forward: X* = x - u, X = x - (u + dt v(X*)) / 2
-            const float af = box_interp<H, WY>(box, E1, k, r2, r3, -u1, -u2, -u3) * dthc;
-            d_fwd[comp * n + idx] = -0.5f * (uc + af);
+            const float af = box_interp<H, WY>(box, E1, k, r2, r3, -u1, -u2, -u3);
+            d_fwd[comp * n + idx] = -0.5f * fmaf(af, dthc, uc);
             if (d_adj) {
                 // adjoint (velocity -v): X* = x + u, X = x + (u + dt v(X*)) / 2
-                const float aa = box_interp<H, WY>(box, E1, k, r2, r3, u1, u2, u3) * dthc;
-                d_adj[comp * n + idx] = 0.5f * (uc + aa);
+                const float aa = box_interp<H, WY>(box, E1, k, r2, r3, u1, u2, u3);
+                d_adj[comp * n + idx] = 0.5f * fmaf(aa, dthc, uc);
             }
         }
     }
@@ -1324,18 +1328,14 @@ k_departure_fixed(Dims g, const float* __restrict__ v, float dth1, float dth2, f
         // forward: X* = x - u, X = x - (u + dt v(X*)) / 2
         box_interp3<H, WY, E1>(box, k, r2, r3, -u[0], -u[1], -u[2], a);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float af = a[c] * dth[c];
-            d_fwd[c * n + idx] = staged ? -0.5f * (u[c] + af) : __int_as_float(0x7fffffff);
-        }
+        for (int c = 0; c < 3; ++c)
+            d_fwd[c * n + idx] = staged ? -0.5f * fmaf(a[c], dth[c], u[c]) : __int_as_float(0x7fffffff);
         if (d_adj) {
             // adjoint (velocity -v): X* = x + u, X = x + (u + dt v(X*)) / 2
             box_interp3<H, WY, E1>(box, k, r2, r3, u[0], u[1], u[2], a);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float aa = a[c] * dth[c];
-                d_adj[c * n + idx] = staged ? 0.5f * (u[c] + aa) : __int_as_float(0x7fffffff);
-            }
+            for (int c = 0; c < 3; ++c)
+                d_adj[c * n + idx] = staged ? 0.5f * fmaf(a[c], dth[c], u[c]) : __int_as_float(0x7fffffff);
         }
     }
 }
@@ -1471,8 +1471,8 @@ k_incstate_init(Dims g, const float* __restrict__ vt, const float* __restrict__ 
     const int idx = blockIdx.x * kThreads + threadIdx.x;
     if (idx >= g.n) return;
     const long long n = g.n;
-    const float f0 = -(vt[idx] * ld(g0, idx) + vt[n + idx] * ld(g0, n + idx) +
-                       vt[2 * n + idx] * ld(g0, 2 * n + idx));
+    const float f0 = -fmaf(vt[2 * n + idx], ld(g0, 2 * n + idx),
+                           fmaf(vt[n + idx], ld(g0, n + idx), vt[idx] * ld(g0, idx)));
     u0[idx] = 0.5f * dt * f0;
 }
 
@@ -1485,8 +1485,8 @@ k_inc_state_level(Dims g, const float* __restrict__ u, const float* __restrict__
     const int idx = blockIdx.x * kThreads + threadIdx.x;
     if (idx >= g.n) return;
     const long long n = g.n;
-    const float vg = vt[idx] * ld(gj, idx) + vt[n + idx] * ld(gj, n + idx) +
-                     vt[2 * n + idx] * ld(gj, 2 * n + idx);
+    const float vg = fmaf(vt[2 * n + idx], ld(gj, 2 * n + idx),
+                          fmaf(vt[n + idx], ld(gj, n + idx), vt[idx] * ld(gj, idx)));
     out[idx] = fmaf(0.5f * dt, vg, u[idx]);
 }
 
@@ -1565,10 +1565,14 @@ cudaError_t launch_departure(const Dims& g, Tile t, const float* v, float dt, fl
         else done = run_departure_fixed<3>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e);
         if (done) return e;
     }
-    if (t.halo >= 0 && t.halo <= 3 && t.wy == 8 && tile_staged(t)) {
-        if (t.halo <= 1) return run_departure_tile<1>(g, t, v, dth1, dth2, dth3, d_fwd, d_adj, st);
-        if (t.halo == 2) return run_departure_tile<2>(g, t, v, dth1, dth2, dth3, d_fwd, d_adj, st);
-        return run_departure_tile<3>(g, t, v, dth1, dth2, dth3, d_fwd, d_adj, st);
+    // the per-thread staged kernel tiles rows by 8 whatever the transports'
+    // tile (the same arithmetic as the tensor-copy kernel: equal points)
+    Tile td = t;
+    td.wy = 8;
+    if (td.halo >= 0 && td.halo <= 3 && tile_staged(td)) {
+        if (td.halo <= 1) return run_departure_tile<1>(g, td, v, dth1, dth2, dth3, d_fwd, d_adj, st);
+        if (td.halo == 2) return run_departure_tile<2>(g, td, v, dth1, dth2, dth3, d_fwd, d_adj, st);
+        return run_departure_tile<3>(g, td, v, dth1, dth2, dth3, d_fwd, d_adj, st);
     }
     k_departure<<<nblocks(g.n), kThreads, 0, st>>>(g, v, dth1, dth2, dth3, d_fwd, d_adj);
     return cudaGetLastError();

@@ -364,10 +364,11 @@ def test_tensor_copy_and_per_thread_staging_agree_bit_for_bit(reg, shape, wy):
 def test_small_tiles_give_the_same_results(reg, shape):
     """Tiles of 1 or 2 points per thread (more warps on small grids) of the
     fixed-halo staged kernels with 8-row blocks run the same per-point
-    arithmetic as the default tile: identical fields, the objective up to the
-    order of its block sums.  16-row blocks take the unstaged semi-Lagrangian
-    points and 4-row blocks the generic staged kernel, which sum their
-    stencils in another order: equal to FP32 rounding."""
+    arithmetic as the default tile (every fused operation explicit, so no
+    call site rounds differently): identical fields, the objective up to the
+    order of its block sums.  4-row blocks take the generic staged kernel,
+    which sums its stencils in another order, and 16-row blocks another
+    instantiation: equal to FP32 rounding."""
     rho_T, rho_R, v = _problem_case(shape, 'H2', False, 1e-3, 4, True)
     w = dev(synth.bandlimited(shape, 3, 1301))
     out = []
