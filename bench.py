@@ -358,7 +358,8 @@ def gpu_bench(args):
             regularisation operator ('spectral', the paper's) or the
             two-level coarse-grid operator ('twolevel')."""
             ctx.set_images(dT, dR, presmooth=True)
-            pc = ({'coarse_factor': args.coarse_factor, 'coarse_tol': 0.1, 'coarse_max': 20}
+            pc = ({'coarse_factor': args.coarse_factor, 'coarse_tol': args.coarse_tol,
+                   'coarse_max': args.coarse_max}
                   if precond == 'twolevel' else {})
             if args.profile_main:
                 # PCG iterations as plain graphs (kernel nodes that ncu lists;
@@ -549,8 +550,9 @@ def gpu_bench(args):
                    'grid': list(SHAPE), 'nt': NT, 'beta': BETA, 'regularisation': KIND,
                    'gtol': '1e-2 of ||g(v=0)||', 'precision': args.precision,
                    'precond': ('two-level: coarse grid n/%d Gauss-Newton Hessian (inner PCG '
-                               'to 0.1, <= 20 iterations) + (beta A)^-1 on the other modes, '
-                               'flexible PCG' % args.coarse_factor
+                               'to %g, <= %d iterations) + (beta A)^-1 on the other modes, '
+                               'flexible PCG' % (args.coarse_factor, args.coarse_tol,
+                                                 args.coarse_max)
                                if args.precond == 'twolevel' else '(beta A)^-1 spectral'),
                    'parallelism': ('independent pairs, one per rank' if world > 1
                                    else 'one GPU'),
@@ -846,6 +848,10 @@ def main():
     ap.add_argument('--precond', default='twolevel', choices=['twolevel', 'spectral'],
                     help='two-level coarse-grid preconditioner or the paper\'s (beta A)^-1')
     ap.add_argument('--coarse-factor', type=int, default=4)
+    ap.add_argument('--coarse-tol', type=float, default=0.1,
+                    help='two-level preconditioner: relative tolerance of the inner PCG')
+    ap.add_argument('--coarse-max', type=int, default=20,
+                    help='two-level preconditioner: iteration cap of the inner PCG')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='phantom256',
                     choices=['phantom256', 'batched', 'beta_sweep', 'twolevel_sweep',
