@@ -753,8 +753,9 @@ def beta_sweep(args):
             if beta < 1e-1:
                 row['continuation'] = timed(gtol=1e-2, beta_start=1e-1, beta_factor=10.0)
             for cf in args.coarse_factors:
-                row['twolevel_%d' % cf] = timed(gtol=1e-2, coarse_factor=cf, coarse_tol=0.1,
-                                                coarse_max=20)
+                row['twolevel_%d' % cf] = timed(gtol=1e-2, coarse_factor=cf,
+                                                coarse_tol=args.coarse_tol,
+                                                coarse_max=args.coarse_max)
             rows.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
         R.close()
@@ -782,7 +783,10 @@ def twolevel_sweep(args):
     rho_T, rho_R = make_inputs(shape)
     settings = [(4, 0, 0.1, 20), (4, 4, 0.1, 20), (4, 2, 0.1, 20), (8, 0, 0.1, 20),
                 (8, 4, 0.1, 20), (4, 0, 0.25, 10), (4, 0, 0.05, 40), (4, 4, 0.25, 10),
-                (2, 4, 0.1, 20)]
+                (2, 4, 0.1, 20), (4, 0, 0.2, 12), (4, 0, 0.15, 15)]
+    if args.sweep_settings:
+        settings = [tuple(float(x) if '.' in x else int(x) for x in c.split(','))
+                    for c in args.sweep_settings]
     stream = torch.cuda.Stream()
     rows = []
     with torch.cuda.stream(stream):
@@ -848,9 +852,9 @@ def main():
     ap.add_argument('--precond', default='twolevel', choices=['twolevel', 'spectral'],
                     help='two-level coarse-grid preconditioner or the paper\'s (beta A)^-1')
     ap.add_argument('--coarse-factor', type=int, default=4)
-    ap.add_argument('--coarse-tol', type=float, default=0.1,
+    ap.add_argument('--coarse-tol', type=float, default=0.2,
                     help='two-level preconditioner: relative tolerance of the inner PCG')
-    ap.add_argument('--coarse-max', type=int, default=20,
+    ap.add_argument('--coarse-max', type=int, default=12,
                     help='two-level preconditioner: iteration cap of the inner PCG')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='phantom256',
@@ -858,6 +862,9 @@ def main():
                              'cpu_oracle'])
     ap.add_argument('--sweep-n', type=int, default=256)
     ap.add_argument('--betas', type=float, nargs='+', default=[1e-1, 1e-2, 1e-3, 1e-4, 1e-5])
+    ap.add_argument('--sweep-settings', nargs='*', default=None, metavar='F,NT,TOL,MAX',
+                    help='twolevel_sweep: coarse factor, coarse nt (0: the fine one), inner '
+                         'tolerance and cap of each setting')
     ap.add_argument('--coarse-factors', type=int, nargs='*', default=[2, 4])
     ap.add_argument('--pairs', type=int, default=48)
     ap.add_argument('--batch-threads', action='store_true',

@@ -216,8 +216,8 @@ typedef struct {
                              remedy for the beta dependence of (beta A)^-1
                              (Table 5).  Each n_j / coarse_factor must be
                              an integer >= 8.  0 or 1: off               (0) */
-    double coarse_tol;    /* inner PCG relative residual tolerance       (0.1) */
-    int coarse_max;       /* inner PCG iteration cap                      (10) */
+    double coarse_tol;    /* inner PCG relative residual tolerance       (0.2) */
+    int coarse_max;       /* inner PCG iteration cap                      (12) */
     int coarse_nt;        /* semi-Lagrangian steps of the coarse Hessian,
                              1..64; 0: the context's nt                   (0) */
 } reg_solve_opts;

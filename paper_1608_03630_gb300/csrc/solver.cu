@@ -966,8 +966,8 @@ int reg_solve_opts_default(reg_solve_opts* o) {
     o->beta_start = 0.0;
     o->beta_factor = 10.0;
     o->coarse_factor = 0;
-    o->coarse_tol = 0.1;
-    o->coarse_max = 10;
+    o->coarse_tol = 0.2;
+    o->coarse_max = 12;
     o->coarse_nt = 0;
     return REG_OK;
 }
