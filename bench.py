@@ -359,7 +359,7 @@ def gpu_bench(args):
             two-level coarse-grid operator ('twolevel')."""
             ctx.set_images(dT, dR, presmooth=True)
             pc = ({'coarse_factor': args.coarse_factor, 'coarse_tol': args.coarse_tol,
-                   'coarse_max': args.coarse_max}
+                   'coarse_max': args.coarse_max, 'coarse_nt': args.coarse_nt}
                   if precond == 'twolevel' else {})
             if args.profile_main:
                 # PCG iterations as plain graphs (kernel nodes that ncu lists;
@@ -549,10 +549,11 @@ def gpu_bench(args):
                                if args.precision == 'mixed_bf16' else 'fp32'),
                    'grid': list(SHAPE), 'nt': NT, 'beta': BETA, 'regularisation': KIND,
                    'gtol': '1e-2 of ||g(v=0)||', 'precision': args.precision,
-                   'precond': ('two-level: coarse grid n/%d Gauss-Newton Hessian (inner PCG '
-                               'to %g, <= %d iterations) + (beta A)^-1 on the other modes, '
-                               'flexible PCG' % (args.coarse_factor, args.coarse_tol,
-                                                 args.coarse_max)
+                   'precond': ('two-level: coarse grid n/%d Gauss-Newton Hessian with nt=%d '
+                               '(inner PCG to %g, <= %d iterations) + (beta A)^-1 on the '
+                               'other modes, flexible PCG'
+                               % (args.coarse_factor, args.coarse_nt or NT, args.coarse_tol,
+                                  args.coarse_max)
                                if args.precond == 'twolevel' else '(beta A)^-1 spectral'),
                    'parallelism': ('independent pairs, one per rank' if world > 1
                                    else 'one GPU'),
@@ -755,7 +756,8 @@ def beta_sweep(args):
             for cf in args.coarse_factors:
                 row['twolevel_%d' % cf] = timed(gtol=1e-2, coarse_factor=cf,
                                                 coarse_tol=args.coarse_tol,
-                                                coarse_max=args.coarse_max)
+                                                coarse_max=args.coarse_max,
+                                                coarse_nt=args.coarse_nt)
             rows.append(row)
             print(json.dumps(row), file=sys.stderr, flush=True)
         R.close()
@@ -856,6 +858,9 @@ def main():
                     help='two-level preconditioner: relative tolerance of the inner PCG')
     ap.add_argument('--coarse-max', type=int, default=12,
                     help='two-level preconditioner: iteration cap of the inner PCG')
+    ap.add_argument('--coarse-nt', type=int, default=NT // 2,
+                    help='two-level preconditioner: time steps of the coarse Hessian '
+                         '(0: the fine n_t)')
     ap.add_argument('--no-cpu-baseline', action='store_true')
     ap.add_argument('--workload', default='phantom256',
                     choices=['phantom256', 'batched', 'beta_sweep', 'twolevel_sweep',

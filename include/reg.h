@@ -219,7 +219,11 @@ typedef struct {
     double coarse_tol;    /* inner PCG relative residual tolerance       (0.2) */
     int coarse_max;       /* inner PCG iteration cap                      (12) */
     int coarse_nt;        /* semi-Lagrangian steps of the coarse Hessian,
-                             1..64; 0: the context's nt                   (0) */
+                             1..64; 0: the context's nt. On a coarse grid
+                             n/4 a point moves a quarter of the cells per
+                             step: half the fine nt measured faster at the
+                             same outer iteration counts (256^3, nt = 8:
+                             4 instead of 8)                              (0) */
 } reg_solve_opts;
 
 typedef struct {

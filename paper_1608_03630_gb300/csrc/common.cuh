@@ -369,6 +369,10 @@ cudaError_t launch_sp_gradient(const Dims& g, const float2* v, const float2* B, 
 cudaError_t launch_sp_axpy(const Dims& g, float2* out, float2* copy, const float2* x,
                            const float2* y, float a, int kind, int project, double* partials,
                            int nblk, cudaStream_t st);
+// s += a p, r -= a q and the partial sums of herm |r|^2 in one pass.
+cudaError_t launch_sp_fcg_update(const Dims& g, float2* s, float2* r, const float2* p,
+                                 const float2* q, float a, double* partials, int nblk,
+                                 cudaStream_t st);
 cudaError_t launch_sp_dot(const Dims& g, const float2* a, const float2* b, double* partials,
                           int nblk, cudaStream_t st);
 cudaError_t launch_sp_normalise(const Dims& g, const float2* in, float2* out, int project,

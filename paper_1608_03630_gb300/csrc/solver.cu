@@ -484,12 +484,9 @@ static int pcg_solve_twolevel(reg_ctx* c, double tol, int max_it, double ctol, i
         }
         const float alpha = (float)(rz / pq);
         {
-            Phase ph(c, REG_PH_SPECTRAL, 2.0 * 3.0 * 24.0 * (double)c->g.nc);
-            REG_CK(c, launch_sp_axpy(c->g, S[S_S], nullptr, S[S_S], S[S_P], alpha, c->kind, 0,
-                                     c->partials, nb, c->stream));
-            REG_CK(c, launch_sp_axpy(c->g, S[S_R], nullptr, S[S_R], S[S_Q], -alpha, c->kind, 0,
-                                     c->partials, nb, c->stream));
-            REG_CK(c, launch_sp_dot(c->g, S[S_R], S[S_R], c->partials, nb, c->stream));
+            Phase ph(c, REG_PH_SPECTRAL, 6.0 * 24.0 * (double)c->g.nc);
+            REG_CK(c, launch_sp_fcg_update(c->g, S[S_S], S[S_R], S[S_P], S[S_Q], alpha,
+                                           c->partials, nb, c->stream));
         }
         REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_RR));
         REG_TRY(read_scalars(c, SC_RR, 1));

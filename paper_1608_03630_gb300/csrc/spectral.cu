@@ -394,6 +394,38 @@ k_sp_dot(Dims g, const float2* __restrict__ a, const float2* __restrict__ b, dou
     store_partials<1>(acc, partials);
 }
 
+// Flexible PCG step: s += a p, r -= a q, partials: herm |r|^2 -- the two
+// updates and the residual norm of k_sp_axpy and k_sp_dot in one pass (the
+// same operations, so the same values).
+__global__ void __launch_bounds__(kThreads)
+k_sp_fcg_update(Dims g, float2* __restrict__ s, float2* __restrict__ r,
+                const float2* __restrict__ p, const float2* __restrict__ q, float a,
+                double* partials) {
+    const long long nc = g.nc;
+    double acc[1] = {0.0};
+    SPEC_LOOP {
+        const Wave w = wave(g, idx);
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float2 sv = s[k * nc + idx];
+            const float2 pv = p[k * nc + idx];
+            sv.x = fmaf(a, pv.x, sv.x);
+            sv.y = fmaf(a, pv.y, sv.y);
+            s[k * nc + idx] = sv;
+            float2 rv = r[k * nc + idx];
+            const float2 qv = q[k * nc + idx];
+            rv.x = fmaf(-a, qv.x, rv.x);
+            rv.y = fmaf(-a, qv.y, rv.y);
+            r[k * nc + idx] = rv;
+            sum = fmaf(rv.x, rv.x, sum);
+            sum = fmaf(rv.y, rv.y, sum);
+        }
+        acc[0] += (double)(w.herm * sum);
+    }
+    store_partials<1>(acc, partials);
+}
+
 // out = in / n (normalise a raw R2C spectrum), optional Leray projection.
 __global__ void __launch_bounds__(kThreads)
 k_sp_normalise(Dims g, const float2* in, float2* out, int project, float inv_n) {
@@ -509,6 +541,13 @@ cudaError_t launch_sp_axpy(const Dims& g, float2* out, float2* copy, const float
                            const float2* y, float a, int kind, int project, double* partials,
                            int nblk, cudaStream_t st) {
     k_sp_axpy<<<nblk, kThreads, 0, st>>>(g, out, copy, x, y, a, kind, project, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sp_fcg_update(const Dims& g, float2* s, float2* r, const float2* p,
+                                 const float2* q, float a, double* partials, int nblk,
+                                 cudaStream_t st) {
+    k_sp_fcg_update<<<nblk, kThreads, 0, st>>>(g, s, r, p, q, a, partials);
     return cudaGetLastError();
 }
 

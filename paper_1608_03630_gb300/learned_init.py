@@ -265,7 +265,7 @@ ARMS = (('plain', 'zero', 'fp32'), ('learned_fp32', 'learned', 'fp32'),
 def twolevel_arms(factor):
     """The arms again with the two-level preconditioner (coarse grid n /
     factor): solver options as the fourth element of an arm."""
-    opts = {'coarse_factor': factor, 'coarse_tol': 0.2, 'coarse_max': 12}
+    opts = {'coarse_factor': factor, 'coarse_tol': 0.2, 'coarse_max': 12, 'coarse_nt': 4}
     return tuple((name + '_twolevel', init, prec, opts) for name, init, prec in ARMS)
 
 
