@@ -575,6 +575,11 @@ def gpu_bench(args):
         'coarse_phase_ms_per_step': {k: v['ms'] / args.steps for k, v in coarse_timing.items()
                                      if v['launches']},
         'coarse_tile': list(coarse_tile),
+        # every fine-grid phase against the same peak: algorithmic bytes of
+        # its launches / their summed event time (the staged steps are bound
+        # by their shared-memory gathers; the fraction is of HBM bandwidth)
+        'phase_hbm_frac': {k: round(v['bytes'] / (v['ms'] / 1e3) / 1e9 / peak, 3)
+                           for k, v in timing.items() if v['ms'] > 0 and v['bytes'] > 0},
         'roofline': {'bound': 'hbm', 'kernel': dom, 'achieved': achieved, 'peak': peak,
                      'unit': 'GB/s', 'frac': achieved / peak, 'peak_source': peak_kind,
                      'bytes_per_launch': d['bytes'] / max(1, d['launches']),

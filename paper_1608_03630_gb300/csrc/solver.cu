@@ -500,8 +500,9 @@ static int pcg_solve_twolevel(reg_ctx* c, double tol, int max_it, double ctol, i
             REG_CK(c, launch_sp_dot(c->g, S[S_Z], S[S_Q], c->partials, nb, c->stream));
         }
         REG_TRY(finalize_to(c, 0, nb, kTwoPi3, SC_TMP));
-        REG_TRY(read_scalars(c, SC_RZNEW, 1));
-        REG_TRY(read_scalars(c, SC_TMP, 1));
+        // RZNEW and TMP in one wait (slots SC_TMP .. SC_RZNEW)
+        static_assert(SC_TMP < SC_RZNEW, "scalar slots");
+        REG_TRY(read_scalars(c, SC_TMP, SC_RZNEW - SC_TMP + 1));
         const float bk = (float)(-(double)alpha * c->hsc[SC_TMP] / rz);
         {
             Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
