@@ -396,8 +396,9 @@ int reg_set_persistent(reg_ctx* ctx, int on);
  *                         next objective or gradient returns REG_ENONFINITE
  *                         and the context stays usable;
  *  REG_INJECT_STAGE_TIMEOUT  the next launch of a staged interpolation
- *                         kernel that stages its box by TMA issues no
- *                         copy and waits for it at most ~1e-4 s of SM
+ *                         or departure-point kernel that stages its box(es)
+ *                         by TMA issues no copy and waits for it at most
+ *                         ~1e-4 s of SM
  *                         clock (instead of ~1 s): every block's bounded
  *                         mbarrier wait runs out, the block writes NaN for
  *                         its points (nothing is in flight), and the call
@@ -415,8 +416,11 @@ int reg_debug_inject(int what, int after);
  * at least one box large (n3 >= 64, n2 >= wy + 3 + 2h, n1 >= k + 3 + 2h for
  * halo h); blocks at a face of the periodic domain reload the elements outside
  * the grid from their periodic images.  Elsewhere, and with tma = 0, every
- * thread issues 4-byte cp.async copies.  The box content, and so every result,
- * is the same either way.  REG_EINVAL unless tma is 0 or 1. */
+ * thread issues 4-byte cp.async copies.  The departure points likewise: one
+ * 4-D tensor copy of the three velocity components' boxes per block (n3 >=
+ * 64, n2 >= 11 + 2h, n1 >= 7 + 2h), else the per-thread copies.  The box
+ * content, and so every result, is the same either way.  REG_EINVAL unless
+ * tma is 0 or 1. */
 int reg_set_staging(reg_ctx* ctx, int tma);
 
 /* Autotuner: time the interpolation kernels of the current linearisation
