@@ -238,7 +238,7 @@ def cpu_oracle_sample(precision_note, counts):
     one objective at 64^3 (nt = 8, same phantom recipe) on one core, scaled to
     256^3 by grid points (x64) and combined with the operation counts of the
     GPU solve (coarse-grid matvecs of the two-level preconditioner by their
-    share of the points).  All cores: the same sample in one process per
+    share of the points and time steps).  All cores: the same sample in one process per
     core at once, the solve time divided by the processes (the throughput of
     the box running independent oracle solves)."""
     import multiprocessing as mp
@@ -533,7 +533,9 @@ def gpu_bench(args):
     counts = {'gradient_evals': last['gradient_evals'], 'matvecs': last['matvecs'],
               'objective_evals': last['objective_evals'],
               'coarse_matvecs': last['coarse_matvecs'],
-              'coarse_points_ratio': (1.0 / args.coarse_factor ** 3
+              # a coarse matvec's work against a fine one's: points x time steps
+              'coarse_points_ratio': ((1.0 / args.coarse_factor ** 3) *
+                                      (args.coarse_nt or NT) / float(NT)
                                       if args.precond == 'twolevel' else 0.0)}
     form = '%s guess, %s, %s preconditioner' % (args.init, args.precision, args.precond)
     line = {
