@@ -67,6 +67,10 @@ def test_status_strings_and_default_options(lib):
     o = reg.Registration.default_opts()
     assert o.gtol == 1e-2 and o.max_gn == 50 and o.max_pcg == 500
     assert o.armijo_c == 1e-4 and o.armijo_shrink == 0.5
+    # two-level preconditioner: off unless coarse_factor is set; inner PCG
+    # to 0.2 relative, at most 12 iterations; the fine nt on the coarse grid
+    assert o.coarse_factor == 0 and o.coarse_tol == 0.2 and o.coarse_max == 12
+    assert o.coarse_nt == 0 and o.use_graph == 2
 
 
 def test_null_context_is_rejected(lib):
