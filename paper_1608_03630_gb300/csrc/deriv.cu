@@ -287,118 +287,79 @@ __device__ __forceinline__ void fourstep(float2 (&v)[N1], float2* T, const float
     __syncthreads();
 }
 
-// Block tile <-> shared complex lines, in 16-byte global accesses with every
-// load of a thread issued before its first shared-memory store (the bytes in
-// flight per SM are what bounds a streaming kernel).  Complex line c of the
-// block holds real lines 2c (Re) and 2c + 1 (Im) at stride S.  AXIS 2: a unit
-// is (c, 4 consecutive positions), read as one float4 from each real line
-// and stored as 4 complex values; AXIS 0 / 1: a unit is (position, 4
-// neighbouring real lines), one float4 of a row, stored as two complex values.
-template <int N, int TH, int AXIS>
+// Column tile (lines along x1 or x2: RL = 2 LC neighbouring x3 columns) <->
+// shared complex lines, in 16-byte global accesses with every load of a
+// thread issued before its first shared-memory store (the bytes in flight
+// per SM are what bounds a streaming kernel).  Complex line c of the block
+// holds real lines 2c (Re) and 2c + 1 (Im) at stride S.  A unit is (position,
+// 4 neighbouring real lines): one float4 of a row, stored as two complex
+// values.  (Rows along x3 need no staging: the kernel loads them straight
+// into registers.)
+template <int N, int LC, int TH>
 struct TileRegs {   // one thread's share of a block tile, between load and store
-    static constexpr int U = AXIS == 2 ? 16 * (N / 4) : 8 * N;
+    static constexpr int G = LC / 2;        // float4 units per position
+    static constexpr int U = G * N;
     static_assert(U % TH == 0, "units per thread");
-    float4 x[U / TH][AXIS == 2 ? 2 : 1];
+    float4 x[U / TH];
 };
 
-template <int N, int TH, int AXIS>
-__device__ __forceinline__ void tile_fetch(TileRegs<N, TH, AXIS>& r, const float* __restrict__ f,
+template <int N, int LC, int TH>
+__device__ __forceinline__ void tile_fetch(TileRegs<N, LC, TH>& r, const float* __restrict__ f,
                                            long long base, long long astride) {
-    constexpr int Q = TileRegs<N, TH, AXIS>::U / TH;
+    constexpr int G = TileRegs<N, LC, TH>::G;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
+    for (int q = 0; q < TileRegs<N, LC, TH>::U / TH; ++q) {
         const int u = threadIdx.x + q * TH;
-        if constexpr (AXIS == 2) {
-            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
-            const float* src = f + base + (long long)(2 * c) * N + a;
-            r.x[q][0] = __ldg(reinterpret_cast<const float4*>(src));
-            r.x[q][1] = __ldg(reinterpret_cast<const float4*>(src + N));
-        } else {
-            const int a = u >> 3, l4 = 4 * (u & 7);
-            r.x[q][0] = __ldg(reinterpret_cast<const float4*>(f + base + l4 + a * astride));
-        }
+        const int a = u / G, l4 = 4 * (u % G);
+        r.x[q] = __ldg(reinterpret_cast<const float4*>(f + base + l4 + a * astride));
     }
 }
 
-template <int N, int S, int TH, int AXIS>
-__device__ __forceinline__ void tile_put(float2* buf, const TileRegs<N, TH, AXIS>& r) {
-    constexpr int Q = TileRegs<N, TH, AXIS>::U / TH;
+template <int N, int LC, int S, int TH>
+__device__ __forceinline__ void tile_put(float2* buf, const TileRegs<N, LC, TH>& r) {
+    constexpr int G = TileRegs<N, LC, TH>::G;
 #pragma unroll
-    for (int q = 0; q < Q; ++q) {
+    for (int q = 0; q < TileRegs<N, LC, TH>::U / TH; ++q) {
         const int u = threadIdx.x + q * TH;
-        if constexpr (AXIS == 2) {
-            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
-            float2* d = buf + c * S + a;
-            d[0] = make_float2(r.x[q][0].x, r.x[q][1].x);
-            d[1] = make_float2(r.x[q][0].y, r.x[q][1].y);
-            d[2] = make_float2(r.x[q][0].z, r.x[q][1].z);
-            d[3] = make_float2(r.x[q][0].w, r.x[q][1].w);
-        } else {
-            const int a = u >> 3, c = 2 * (u & 7);
-            buf[c * S + a] = make_float2(r.x[q][0].x, r.x[q][0].y);
-            buf[(c + 1) * S + a] = make_float2(r.x[q][0].z, r.x[q][0].w);
-        }
+        const int a = u / G, c = 2 * (u % G);
+        buf[c * S + a] = make_float2(r.x[q].x, r.x[q].y);
+        buf[(c + 1) * S + a] = make_float2(r.x[q].z, r.x[q].w);
     }
 }
 
-template <int N, int S, int TH, int AXIS>
-__device__ __forceinline__ void tile_load(float2* buf, const float* __restrict__ f, long long base,
-                                          long long astride) {
-    TileRegs<N, TH, AXIS> r;
-    tile_fetch<N, TH, AXIS>(r, f, base, astride);
-    tile_put<N, S, TH, AXIS>(buf, r);
-}
-
-template <int N, int S, int TH, int AXIS>
+template <int N, int LC, int S, int TH>
 __device__ __forceinline__ void tile_store(const float2* buf, float* __restrict__ out,
                                            long long base, long long astride, int accumulate) {
-    if constexpr (AXIS == 2) {
-        constexpr int U = 16 * (N / 4);
+    constexpr int G = LC / 2;
 #pragma unroll
-        for (int q = 0; q < U / TH; ++q) {
-            const int u = threadIdx.x + q * TH;
-            const int c = u / (N / 4), a = 4 * (u - c * (N / 4));
-            const float2* z = buf + c * S + a;
-            const float2 z0 = z[0], z1 = z[1], z2 = z[2], z3 = z[3];
-            float4 re = make_float4(z0.x, z1.x, z2.x, z3.x);
-            float4 im = make_float4(z0.y, z1.y, z2.y, z3.y);
-            float4* d = reinterpret_cast<float4*>(out + base + (long long)(2 * c) * N + a);
-            float4* e = reinterpret_cast<float4*>(out + base + (long long)(2 * c + 1) * N + a);
-            if (accumulate) {
-                const float4 p = *d, r = *e;
-                re.x += p.x; re.y += p.y; re.z += p.z; re.w += p.w;
-                im.x += r.x; im.y += r.y; im.z += r.z; im.w += r.w;
-            }
-            *d = re;
-            *e = im;
+    for (int q = 0; q < G * N / TH; ++q) {
+        const int u = threadIdx.x + q * TH;
+        const int a = u / G, c = 2 * (u % G);
+        const float2 z0 = buf[c * S + a], z1 = buf[(c + 1) * S + a];
+        float4 w = make_float4(z0.x, z0.y, z1.x, z1.y);
+        float4* d = reinterpret_cast<float4*>(out + base + 4 * (u % G) + a * astride);
+        if (accumulate) {
+            const float4 p = *d;
+            w.x += p.x; w.y += p.y; w.z += p.z; w.w += p.w;
         }
-    } else {
-        constexpr int U = 8 * N;
-#pragma unroll
-        for (int q = 0; q < U / TH; ++q) {
-            const int u = threadIdx.x + q * TH;
-            const int a = u >> 3, c = 2 * (u & 7);
-            const float2 z0 = buf[c * S + a], z1 = buf[(c + 1) * S + a];
-            float4 w = make_float4(z0.x, z0.y, z1.x, z1.y);
-            float4* d = reinterpret_cast<float4*>(out + base + 4 * (u & 7) + a * astride);
-            if (accumulate) {
-                const float4 p = *d;
-                w.x += p.x; w.y += p.y; w.z += p.z; w.w += p.w;
-            }
-            *d = w;
-        }
+        *d = w;
     }
 }
 
-template <int N1, int N2, int AXIS>
-__global__ void __launch_bounds__(16 * N2, 3)
+// Complex lines per block of the four-step kernel (2 LC real lines: rows
+// along x3, or neighbouring x3 columns along x1 / x2).
+constexpr int kDerivLines = 16;
+
+template <int N1, int N2, int AXIS, int LC>
+__global__ void __launch_bounds__(LC * N2, 48 / LC)
 k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumulate) {
     constexpr int N = N1 * N2;
     constexpr int S = N + 1;                       // load buffer line stride
-    constexpr int TH = 16 * N2;                    // threads
+    constexpr int TH = LC * N2;                    // threads
+    constexpr int RL = 2 * LC;                     // real lines per block
     extern __shared__ float2 sm[];
-    float2* buf = sm;                              // max(16 S, 16 N1 (N2 + 1)) complex
-    float2* tw = sm + (16 * S > 16 * N1 * (N2 + 1) ? 16 * S : 16 * N1 * (N2 + 1));
+    float2* buf = sm;                              // max(LC S, LC N1 (N2 + 1)) complex
+    float2* tw = sm + (LC * S > LC * N1 * (N2 + 1) ? LC * S : LC * N1 * (N2 + 1));
     for (int m = threadIdx.x; m < N; m += TH) {
         float sn, cs;
         sincospif(-2.0f * (float)m / (float)N, &sn, &cs);
@@ -406,11 +367,11 @@ k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accu
     }
     long long base, astride;
     if (AXIS == 2) {
-        base = (long long)blockIdx.x * 32 * N;
+        base = (long long)blockIdx.x * RL * N;
         astride = 1;
     } else {
-        const int groups = g.n3 / 32;
-        const int fixed = blockIdx.x / groups, col0 = (blockIdx.x - fixed * groups) * 32;
+        const int groups = g.n3 / RL;
+        const int fixed = blockIdx.x / groups, col0 = (blockIdx.x - fixed * groups) * RL;
         if (AXIS == 1) { base = (long long)fixed * g.n23 + col0; astride = g.n3; }
         else { base = (long long)fixed * g.n3 + col0; astride = g.n23; }
     }
@@ -425,7 +386,9 @@ k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accu
         for (int m = 0; m < N1; ++m) v[m] = make_float2(__ldg(r0 + N2 * m), __ldg(r0 + N + N2 * m));
         __syncthreads();                           // the twiddle table
     } else {
-        tile_load<N, S, TH, AXIS>(buf, f, base, astride);
+        TileRegs<N, LC, TH> r;
+        tile_fetch<N, LC, TH>(r, f, base, astride);
+        tile_put<N, LC, S, TH>(buf, r);
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < N1; ++m) v[m] = buf[line * S + t + N2 * m];
@@ -457,30 +420,30 @@ k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accu
 #pragma unroll
         for (int m = 0; m < N1; ++m) buf[line * S + t + N2 * m] = v[m];
         __syncthreads();
-        tile_store<N, S, TH, AXIS>(buf, out, base, astride, accumulate);
+        tile_store<N, LC, S, TH>(buf, out, base, astride, accumulate);
     }
 }
-
 
 template <int N1, int N2, int AXIS>
 cudaError_t run_deriv_r(const Dims& g, const float* f, float* out, int accumulate,
                         cudaStream_t st) {
+    constexpr int LC = kDerivLines;
     constexpr int N = N1 * N2;
-    const int bufc = 16 * (N + 1) > 16 * N1 * (N2 + 1) ? 16 * (N + 1) : 16 * N1 * (N2 + 1);
+    const int bufc = LC * (N + 1) > LC * N1 * (N2 + 1) ? LC * (N + 1) : LC * N1 * (N2 + 1);
     const size_t smem = sizeof(float2) * (bufc + N);
     if (smem > 48 * 1024) {
         static std::once_flag once;
         static cudaError_t attr = cudaSuccess;
         std::call_once(once, [&] {
-            attr = cudaFuncSetAttribute(k_deriv_r<N1, N2, AXIS>,
+            attr = cudaFuncSetAttribute(k_deriv_r<N1, N2, AXIS, LC>,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         });
         if (attr != cudaSuccess) return attr;
     }
     int blocks;
-    if (AXIS == 2) blocks = g.n1 * g.n2 / 32;
-    else blocks = (AXIS == 1 ? g.n1 : g.n2) * (g.n3 / 32);
-    k_deriv_r<N1, N2, AXIS><<<blocks, 16 * N2, smem, st>>>(g, f, out, accumulate);
+    if (AXIS == 2) blocks = g.n1 * g.n2 / (2 * LC);
+    else blocks = (AXIS == 1 ? g.n1 : g.n2) * (g.n3 / (2 * LC));
+    k_deriv_r<N1, N2, AXIS, LC><<<blocks, LC * N2, smem, st>>>(g, f, out, accumulate);
     return cudaGetLastError();
 }
 
