@@ -240,9 +240,13 @@ cudaError_t launch_absmax(const float* d, long long count, unsigned int* out, cu
 
 // transport.cu
 // t.halo (>= ceil of the predictor's largest displacement, grid units) and
-// the tile select the shared-memory staged kernel when it applies.
+// the tile select the shared-memory staged kernel when it applies.  dmax
+// (may be null; 2 words): where the tensor-copy kernel runs with d_adj, it
+// also leaves max |d_fwd| and max |d_adj| there as launch_absmax would, and
+// sets *maxed (else *maxed = false and dmax is untouched).
 cudaError_t launch_departure(const Dims& g, Tile t, const float* v, float dt, float* d_fwd,
-                             float* d_adj, cudaStream_t st);
+                             float* d_adj, cudaStream_t st, unsigned int* dmax = nullptr,
+                             bool* maxed = nullptr);
 // out = I[f](x + d) for one scalar field.
 cudaError_t launch_interp(const Dims& g, Tile t, const float* f, const float* d, float* out,
                           cudaStream_t st);

@@ -105,7 +105,7 @@ void release_graph_timing(reg_ctx* c) {
 
 // ------------------------------------------------------------- operations
 
-int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj) {
+int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj, bool* maxed) {
     // the predictor's displacement dt v_j n_j / (2 pi) (grid units) is below
     // max |v| dt max_j n_j / (2 pi): its ceiling is the staged kernel's halo
     const int nmax = std::max(c->g.n1, std::max(c->g.n2, c->g.n3));
@@ -113,7 +113,16 @@ int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj) {
     REG_TRY(op_halo(c, v, &halo, (float)(nmax / (c->nt * 6.283185307179586))));
     Phase p(c, REG_PH_DEPARTURE, (double)c->g.n * (d_adj ? 36.0 : 24.0));
     REG_CK(c, launch_departure(c->g, tile_with(c, halo), v, (float)(1.0 / c->nt), d_fwd, d_adj,
-                               c->stream));
+                               c->stream, maxed ? c->dabs : nullptr, maxed));
+    return REG_OK;
+}
+
+// ceil(max |d|) from the bits of a float maximum (as op_halo).
+static int halo_of(reg_ctx* c, unsigned int bits, int* halo) {
+    float m;
+    memcpy(&m, &bits, sizeof m);
+    if (!std::isfinite(m)) return fail(c, REG_ENONFINITE, "non-finite displacement");
+    *halo = m < 1e6f ? (int)std::ceil(m) : 1000000;
     return REG_OK;
 }
 
@@ -396,9 +405,20 @@ static int adjoint_solve(reg_ctx* c, int phase, float* levels, bool keep_all,
 // The points of v and -v, their halos and the state history of v (with
 // lam(1) and the mismatch) in the linearisation buffers.
 static int state_of(reg_ctx* c, const float* v) {
-    REG_TRY(op_departure(c, v, c->d_fwd, c->d_adj));
-    REG_TRY(op_halo(c, c->d_fwd, &c->halo_fwd));
-    REG_TRY(op_halo(c, c->d_adj, &c->halo_adj));
+    // the tensor-copy departure kernel leaves both fields' maxima in dabs:
+    // one wait for the two halos instead of two reductions and two waits
+    bool maxed = false;
+    REG_TRY(op_departure(c, v, c->d_fwd, c->d_adj, &maxed));
+    if (maxed) {
+        unsigned int bits[2] = {0u, 0u};
+        REG_CK(c, cudaMemcpyAsync(bits, c->dabs, sizeof bits, cudaMemcpyDeviceToHost, c->stream));
+        REG_CK(c, cudaStreamSynchronize(c->stream));
+        REG_TRY(halo_of(c, bits[0], &c->halo_fwd));
+        REG_TRY(halo_of(c, bits[1], &c->halo_adj));
+    } else {
+        REG_TRY(op_halo(c, c->d_fwd, &c->halo_fwd));
+        REG_TRY(op_halo(c, c->d_adj, &c->halo_adj));
+    }
     return state_solve(c, c->d_fwd, c->halo_fwd, c->rho_hist, true,
                        c->lam_hist + (long long)c->nt * c->g.n);
 }

@@ -133,7 +133,9 @@ int harvest_graph_timing(reg_ctx* c);
 void release_graph_timing(reg_ctx* c);
 
 // Internal operations (device pointers; all on c->stream).
-int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj);
+// maxed (may be null): when the kernel also left max |d_fwd|, max |d_adj| in
+// c->dabs[0..1] (float bits), *maxed = true.
+int op_departure(reg_ctx* c, const float* v, float* d_fwd, float* d_adj, bool* maxed = nullptr);
 int op_fft_r2c(reg_ctx* c, const float* in, float2* out, int ncomp);
 int op_fft_c2r(reg_ctx* c, float2* in, float* out, int ncomp);
 int op_spectral(reg_ctx* c, SpecOp op, const SpecArgs& a, int ncomp_bytes_fields);

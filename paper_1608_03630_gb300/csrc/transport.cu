@@ -1256,7 +1256,8 @@ template <int H>
 __global__ void __launch_bounds__(256)
 k_departure_fixed(Dims g, const float* __restrict__ v, float dth1, float dth2, float dth3,
                   float* __restrict__ d_fwd, float* __restrict__ d_adj,
-                  const __grid_constant__ CUtensorMap map, int inject_timeout) {
+                  const __grid_constant__ CUtensorMap map, int inject_timeout,
+                  unsigned int* __restrict__ dmax) {
     constexpr int K = kDepK, WY = 8;
     constexpr int E1 = K + 3 + 2 * H, E2 = WY + 3 + 2 * H, P3 = 64;
     constexpr int C0 = 3 - H, C1 = 38 + H;
@@ -1317,10 +1318,10 @@ k_departure_fixed(Dims g, const float* __restrict__ v, float dth1, float dth2, f
         box[at] = x;
     }
     __syncthreads();
-    if (!active) return;
     const int r2 = ty + H, r3 = lane + 3;   // i2 - 1 - o2, i3 - 1 - o3
     const float dth[3] = {dth1, dth2, dth3};
-    for (int k = 0; k < kend; ++k) {
+    float mf = 0.f, ma = 0.f;   // max |d_fwd|, max |d_adj| of the thread's points
+    for (int k = 0; active && k < kend; ++k) {
         const int idx = ((i1b + k) * g.n2 + i2) * g.n3 + i3;
         const int ctr = ((k + 1 + H) * E2 + ty + 1 + H) * P3 + lane + 4;
         const float u[3] = {box[ctr] * dth1, box[BOX + ctr] * dth2, box[2 * BOX + ctr] * dth3};
@@ -1328,14 +1329,41 @@ k_departure_fixed(Dims g, const float* __restrict__ v, float dth1, float dth2, f
         // forward: X* = x - u, X = x - (u + dt v(X*)) / 2
         box_interp3<H, WY, E1>(box, k, r2, r3, -u[0], -u[1], -u[2], a);
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            d_fwd[c * n + idx] = staged ? -0.5f * fmaf(a[c], dth[c], u[c]) : __int_as_float(0x7fffffff);
+        for (int c = 0; c < 3; ++c) {
+            const float x = staged ? -0.5f * fmaf(a[c], dth[c], u[c]) : __int_as_float(0x7fffffff);
+            d_fwd[c * n + idx] = x;
+            mf = fmaxf(mf, fabsf(x));
+        }
         if (d_adj) {
             // adjoint (velocity -v): X* = x + u, X = x + (u + dt v(X*)) / 2
             box_interp3<H, WY, E1>(box, k, r2, r3, u[0], u[1], u[2], a);
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                d_adj[c * n + idx] = staged ? 0.5f * fmaf(a[c], dth[c], u[c]) : __int_as_float(0x7fffffff);
+            for (int c = 0; c < 3; ++c) {
+                const float x = staged ? 0.5f * fmaf(a[c], dth[c], u[c]) : __int_as_float(0x7fffffff);
+                d_adj[c * n + idx] = x;
+                ma = fmaxf(ma, fabsf(x));
+            }
+        }
+    }
+    if (dmax) {
+        // the largest |d| of each field, as k_absmax finds it (fmaxf of the
+        // absolute values; the bits of non-negative floats order as unsigned
+        // integers): a warp, then the block, then one atomic per block
+        __shared__ float red[2][8];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mf = fmaxf(mf, __shfl_xor_sync(0xffffffffu, mf, o));
+            ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        }
+        if (lane == 0) {
+            red[0][ty] = mf;
+            red[1][ty] = ma;
+        }
+        __syncthreads();
+        if (tid < 2) {
+            float m = 0.f;
+            for (int w = 0; w < 8; ++w) m = fmaxf(m, red[tid][w]);
+            atomicMax(dmax + tid, __float_as_uint(m));
         }
     }
 }
@@ -1366,7 +1394,8 @@ bool velocity_tensor_map(CUtensorMap* map, const Dims& g, const float* v, int E1
 // (nothing launched) otherwise.
 template <int H>
 bool run_departure_fixed(const Dims& g, const float* v, float dth1, float dth2, float dth3,
-                         float* d_fwd, float* d_adj, cudaStream_t st, cudaError_t* err) {
+                         float* d_fwd, float* d_adj, cudaStream_t st, cudaError_t* err,
+                         unsigned int* dmax) {
     constexpr int E1 = kDepK + 3 + 2 * H, E2 = 8 + 3 + 2 * H;
     const size_t smem = sizeof(float) * 3 * (size_t)E1 * E2 * 64 + 16;
     CUtensorMap map;
@@ -1383,8 +1412,12 @@ bool run_departure_fixed(const Dims& g, const float* v, float dth1, float dth2, 
     }
     const int inject = g_inject_stage.exchange(0) ? 1 : 0;
     const dim3 grid((g.n3 + 31) / 32, (g.n2 + 7) / 8, (g.n1 + kDepK - 1) / kDepK);
+    if (dmax) {
+        *err = cudaMemsetAsync(dmax, 0, 2 * sizeof(unsigned int), st);
+        if (*err != cudaSuccess) return true;
+    }
     k_departure_fixed<H><<<grid, dim3(32, 8), smem, st>>>(g, v, dth1, dth2, dth3, d_fwd, d_adj,
-                                                          map, inject);
+                                                          map, inject, dmax);
     *err = cudaGetLastError();
     return true;
 }
@@ -1553,17 +1586,22 @@ int march_blocks(const Dims& g, Tile t) {
 }
 
 cudaError_t launch_departure(const Dims& g, Tile t, const float* v, float dt, float* d_fwd,
-                             float* d_adj, cudaStream_t st) {
+                             float* d_adj, cudaStream_t st, unsigned int* dmax, bool* maxed) {
+    if (maxed) *maxed = false;
     const float two_pi = 6.283185307179586f;
     const float dth1 = dt * g.n1 / two_pi, dth2 = dt * g.n2 / two_pi, dth3 = dt * g.n3 / two_pi;
     if (t.halo >= 0 && t.halo <= 3 && t.tma) {
         // one tensor copy of the three components' boxes per block
         cudaError_t e = cudaSuccess;
         bool done;
-        if (t.halo <= 1) done = run_departure_fixed<1>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e);
-        else if (t.halo == 2) done = run_departure_fixed<2>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e);
-        else done = run_departure_fixed<3>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e);
-        if (done) return e;
+        unsigned int* m = d_adj ? dmax : nullptr;
+        if (t.halo <= 1) done = run_departure_fixed<1>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e, m);
+        else if (t.halo == 2) done = run_departure_fixed<2>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e, m);
+        else done = run_departure_fixed<3>(g, v, dth1, dth2, dth3, d_fwd, d_adj, st, &e, m);
+        if (done) {
+            if (maxed && m && e == cudaSuccess) *maxed = true;
+            return e;
+        }
     }
     // the per-thread staged kernel tiles rows by 8 whatever the transports'
     // tile (the same arithmetic as the tensor-copy kernel: equal points)
