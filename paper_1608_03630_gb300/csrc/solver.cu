@@ -453,11 +453,15 @@ static int pcg_solve_twolevel(reg_ctx* c, double tol, int max_it, double ctol, i
     int it_in = 0;
     REG_TRY(twolevel_apply(c, S[S_R], S[S_Z], ctol, cmax, SC_RZ, &it_in, use_graph));
     *coarse_iters += it_in;
+    // p = z, and spec[0] = p: the inverse transform destroys its input, so
+    // it always works on spec[0], which the direction update refreshes
     REG_CK(c, cudaMemcpyAsync(S[S_P], S[S_Z], sizeof(float2) * 3 * (size_t)c->g.nc,
+                              cudaMemcpyDeviceToDevice, c->stream));
+    REG_CK(c, cudaMemcpyAsync(c->spec[0], S[S_Z], sizeof(float2) * 3 * (size_t)c->g.nc,
                               cudaMemcpyDeviceToDevice, c->stream));
     for (int it = 1; it <= max_it; ++it) {
         // q = H p on the coefficients
-        REG_TRY(to_physical(c, S[S_P], c->sv[R_P]));
+        REG_TRY(op_fft_c2r(c, c->spec[0], c->sv[R_P], 3));
         REG_TRY(op_matvec_transport(c, c->sv[R_P], nullptr, 0));
         REG_TRY(op_fft_r2c(c, c->bacc, c->spec[1], 3));
         {
@@ -506,7 +510,7 @@ static int pcg_solve_twolevel(reg_ctx* c, double tol, int max_it, double ctol, i
         const float bk = (float)(-(double)alpha * c->hsc[SC_TMP] / rz);
         {
             Phase ph(c, REG_PH_SPECTRAL, 3.0 * 24.0 * (double)c->g.nc);
-            REG_CK(c, launch_sp_axpy(c->g, S[S_P], nullptr, S[S_Z], S[S_P], bk, c->kind, 0,
+            REG_CK(c, launch_sp_axpy(c->g, S[S_P], c->spec[0], S[S_Z], S[S_P], bk, c->kind, 0,
                                      c->partials, nb, c->stream));
         }
         REG_CK(c, cudaMemcpyAsync(c->dsc + SC_RZ, c->dsc + SC_RZNEW, sizeof(double),
