@@ -78,16 +78,21 @@ class TwoLevel:
     linearize(v) sets the coarse Hessian's linearisation point to the
     restriction of v; apply(r) returns M^-1 r.  inner_tol is the inner PCG's
     relative residual tolerance, inner_max its iteration cap (inner_tol = 0
-    runs exactly inner_max iterations unless the residual vanishes).
+    runs exactly inner_max iterations unless the residual vanishes).  nt_c:
+    the coarse Hessian's semi-Lagrangian time steps (None: the fine nt); a
+    coarse grid moves a point across fewer cells per step, so it may take
+    fewer steps -- any nt_c gives an SPD H_c, so M^-1 stays a valid
+    preconditioner for the flexible outer iteration.
     """
 
-    def __init__(self, problem, shape_c, inner_tol=0.1, inner_max=10):
+    def __init__(self, problem, shape_c, inner_tol=0.1, inner_max=10, nt_c=None):
         self.P = problem
         self.shape_c = tuple(shape_c)
         self.inner_tol = float(inner_tol)
         self.inner_max = int(inner_max)
         self.coarse = Problem(restrict(problem.rho_T, shape_c), restrict(problem.rho_R, shape_c),
-                              problem.nt, problem.beta, problem.kind, problem.incompressible)
+                              int(nt_c) if nt_c else problem.nt, problem.beta, problem.kind,
+                              problem.incompressible)
         self.inner_iters = 0
 
     def linearize(self, v):
@@ -113,9 +118,9 @@ class TwoLevelProblem:
     also relinearises the coarse Hessian, precond() applies M^-1.  For
     solver.gauss_newton(..., flexible=True)."""
 
-    def __init__(self, problem, shape_c, inner_tol=0.1, inner_max=10):
+    def __init__(self, problem, shape_c, inner_tol=0.1, inner_max=10, nt_c=None):
         self.base = problem
-        self.two = TwoLevel(problem, shape_c, inner_tol, inner_max)
+        self.two = TwoLevel(problem, shape_c, inner_tol, inner_max, nt_c)
 
     def __getattr__(self, name):
         return getattr(self.base, name)

@@ -43,7 +43,11 @@ def host_c(t):
 
 @pytest.mark.parametrize('kind,incompressible,beta', [('H2', False, 1e-3), ('H1DIV', True, 1e-3)])
 @pytest.mark.parametrize('inner', [1, 3])
-def test_two_level_application_matches_the_oracle(reg, kind, incompressible, beta, inner):
+@pytest.mark.parametrize('coarse_nt', [0, 2])
+def test_two_level_application_matches_the_oracle(reg, kind, incompressible, beta, inner,
+                                                  coarse_nt):
+    """coarse_nt 0: the coarse Hessian takes the fine nt = 4 steps; 2: its
+    own two steps (the form the bench runs, half the fine steps)."""
     shape, coarse, nt = (32, 32, 32), (16, 16, 16), 4
     rho_T, rho_R, _ = [f32(a) for a in synth.sinusoid_problem(shape, 0.5)]
     v = 0.3 * synth.bandlimited(shape, 2, 51)
@@ -53,13 +57,13 @@ def test_two_level_application_matches_the_oracle(reg, kind, incompressible, bet
     v_hat, v = oracle_jobs.rounded_hat(v)
     r_hat, r = oracle_jobs.rounded_hat(r)
     P = opr.Problem(rho_T, rho_R, nt, beta, kind, incompressible)
-    T = opc.TwoLevel(P, coarse, inner_tol=0.0, inner_max=inner)
+    T = opc.TwoLevel(P, coarse, inner_tol=0.0, inner_max=inner, nt_c=coarse_nt or None)
     T.linearize(v)
     z_ref = T.apply(r)
     R = reg.Registration(shape, nt, beta, kind, incompressible)
     R.set_images(torch.tensor(rho_T, dtype=torch.float32, device='cuda'),
                  torch.tensor(rho_R, dtype=torch.float32, device='cuda'))
-    R.twolevel_setup(2, torch.tensor(v_hat, device='cuda'))
+    R.twolevel_setup(2, torch.tensor(v_hat, device='cuda'), coarse_nt=coarse_nt)
     z, its = R.twolevel_apply(torch.tensor(r_hat, device='cuda'), inner_tol=0.0, inner_max=inner)
     R.close()
     assert its == T.inner_iters == inner

@@ -12,6 +12,9 @@
   symmetric) flexible PCG then takes one iteration to the exact Newton step.
 * Flexible PCG with a fixed SPD preconditioner makes the same iterates as
   PCG (the two direction coefficients agree in exact arithmetic).
+* A coarse Hessian with its own time steps (nt_c): with an exact inner solve
+  at v = 0 the operator is symmetric, and it equals the coarse correction
+  assembled by hand from a coarse problem with nt_c steps.
 """
 
 import numpy as np
@@ -111,3 +114,45 @@ def test_closed_form_pin_catches_a_dropped_high_mode_part(monkeypatch):
     expected = osp.preconditioner(r, beta, 'H2', False)
     monkeypatch.setattr(opc._sp, 'preconditioner', lambda rr, *a: 0.0 * rr)
     assert rel(T.apply(r), expected) > 1e-2
+
+
+def test_coarse_time_steps_give_a_symmetric_operator_built_from_that_coarse_problem():
+    """At v = 0 the state does not move and the Gauss-Newton Hessian does not
+    depend on the number of steps (its time integrand is linear in t, which
+    the trapezoid rule integrates exactly), so there the operator must be
+    symmetric; away from v = 0 it must equal the coarse correction assembled
+    by hand from a coarse problem with nt_c steps, and differ from the one
+    with the fine number of steps."""
+    shape, coarse, beta = (16, 16, 16), (8, 8, 8), 1e-3
+    rho_T = synth.bandlimited(shape, 3, 71, ncomp=None)
+    rho_R = synth.bandlimited(shape, 3, 72, ncomp=None)
+    P = opr.Problem(rho_T, rho_R, 4, beta, 'H2', False)
+    a = synth.bandlimited(shape, 5, 73)
+    b = synth.bandlimited(shape, 5, 74)
+    zero = np.zeros((3,) + shape)
+    P.gradient(zero)
+    T2 = opc.TwoLevel(P, coarse, inner_tol=1e-12, inner_max=300, nt_c=2)
+    T2.linearize(zero)
+    assert T2.coarse.nt == 2
+    ma, mb = T2.apply(a), T2.apply(b)
+    # symmetric up to the inner solve's error (residual 1e-12 relative, times
+    # the coarse Hessian's condition number, about 1e4 at beta = 1e-3)
+    assert abs(opr.inner(ma, b) - opr.inner(a, mb)) < 1e-6 * abs(opr.inner(ma, b))
+    # away from v = 0: the same correction from a coarse problem with two
+    # steps, by hand
+    v = 0.8 * synth.bandlimited(shape, 2, 75)
+    P.gradient(v)
+    T2.linearize(v)
+    ma = T2.apply(a)
+    C = opr.Problem(opc.restrict(rho_T, coarse), opc.restrict(rho_R, coarse), 2, beta, 'H2',
+                    False)
+    C.gradient(opc.restrict(v, coarse))
+    rl = opc.restrict(a, coarse)
+    y, _, _ = oso.pcg(C.hessian_matvec, C.precond, rl, 1e-12 * np.sqrt(opr.inner(rl, rl)), 300)
+    expected = opc.prolong(y, shape) + osp.preconditioner(a - opc.low_pass(a, coarse), beta, 'H2',
+                                                          False)
+    assert rel(ma, expected) < 1e-9
+    # and it differs from the operator with the fine number of steps
+    T4 = opc.TwoLevel(P, coarse, inner_tol=1e-12, inner_max=300)
+    T4.linearize(v)
+    assert rel(T4.apply(a), ma) > 1e-4
