@@ -14,13 +14,14 @@
 //
 // Lines of 32..256 points use a register-blocked four-step transform
 // (below); lines of 16 and 512 points a Stockham FFT in shared memory.
-// Stockham: natural order in and out, radix 4 with one
-// radix-2 stage when log2 N is odd, each stage in place in one shared buffer
-// (every thread reads its butterflies' inputs into registers, the block
-// synchronises, then it writes their outputs); twiddles exp(-2 pi i m / N)
-// from a table the block fills with sincospif.  Lines along x3 are rows (contiguous); lines along x1 or x2
-// are 32 neighbouring x3 columns, so every global access is a coalesced
-// 128-byte row segment.
+// Stockham: natural order in and out, radix 4 with one radix-2 stage when
+// log2 N is odd, each stage in place in one shared buffer (every thread
+// reads its butterflies' inputs into registers, the block synchronises, then
+// it writes their outputs); twiddles exp(-2 pi i m / N) from a table the
+// block fills with sincospif.  Lines along x3 are rows (contiguous; the
+// four-step kernel loads its elements of them straight into registers);
+// lines along x1 or x2 are 32 neighbouring x3 columns, staged through shared
+// memory in 16-byte row segments.
 #include <cstdint>
 #include <mutex>
 
