@@ -351,13 +351,17 @@ def gpu_bench(args):
         if args.coarse_tile:
             R.set_coarse_tile(*args.coarse_tile)
 
-        def solve_from_images(ctx, init, precond):
+        def solve_from_images(ctx, init, precond, T=None, Rimg=None, vel=None):
             """One registration from images on the device: the network's
             prediction for the learned guess, then the solve to
             ||g|| <= 1e-2 ||g(0)||, preconditioned by the inverse
             regularisation operator ('spectral', the paper's) or the
-            two-level coarse-grid operator ('twolevel')."""
-            ctx.set_images(dT, dR, presmooth=True)
+            two-level coarse-grid operator ('twolevel'). T, Rimg and vel
+            default to the bench's own image and velocity buffers."""
+            T = dT if T is None else T
+            Rimg = dR if Rimg is None else Rimg
+            vel = v if vel is None else vel
+            ctx.set_images(T, Rimg, presmooth=True)
             pc = ({'coarse_factor': args.coarse_factor, 'coarse_tol': args.coarse_tol,
                    'coarse_max': args.coarse_max, 'coarse_nt': args.coarse_nt}
                   if precond == 'twolevel' else {})
@@ -366,12 +370,12 @@ def gpu_bench(args):
                 # a graph with a conditional node is profiled only whole)
                 pc = dict(pc, use_graph=1)
             if init == 'learned':
-                v.copy_(learned_init.predict(net, info['scale'], dT, dR, SHAPE[0], info['kc'],
-                                             info['alpha'], info['stages'], ctx))
+                vel.copy_(learned_init.predict(net, info['scale'], T, Rimg, SHAPE[0], info['kc'],
+                                               info['alpha'], info['stages'], ctx))
                 # stop at 1e-2 ||g(0)||, ||g(0)|| from its closed form at v = 0
-                return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500, gnorm_ref=-1.0, **pc)
-            v.zero_()
-            return ctx.solve(v, gtol=1e-2, max_gn=50, max_pcg=500, **pc)
+                return ctx.solve(vel, gtol=1e-2, max_gn=50, max_pcg=500, gnorm_ref=-1.0, **pc)
+            vel.zero_()
+            return ctx.solve(vel, gtol=1e-2, max_gn=50, max_pcg=500, **pc)
 
         def step():
             return solve_from_images(R, args.init, args.precond)
@@ -425,19 +429,51 @@ def gpu_bench(args):
             elapsed_ms = max_over_ranks(elapsed_ms, world)
             dist.barrier()
 
-        # end to end through the public API: pinned host images in, the
-        # velocity back to pinned host memory, every step
+        # end to end through the public API: every step uploads its pair
+        # from pinned host memory and downloads its velocity to pinned host
+        # memory. The copies run on a copy stream into double buffers, as a
+        # stream of registrations is served: the upload of pair k+1 and the
+        # download of velocity k-1 overlap the solve of pair k (the first
+        # upload and the last download are exposed).
         hT = torch.from_numpy(rho_T).pin_memory()
         hR = torch.from_numpy(rho_R).pin_memory()
         hv = torch.zeros((3,) + SHAPE).pin_memory()
+        bufT = [dT, torch.empty_like(dT)]
+        bufR = [dR, torch.empty_like(dR)]
+        bufv = [v, torch.empty_like(v)]
+        copy = torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(2)]    # pair uploaded
+        ev_done = [torch.cuda.Event() for _ in range(2)]  # solve finished
+        ev_out = [torch.cuda.Event() for _ in range(2)]   # velocity downloaded
+
+        def upload(b):
+            bufT[b].copy_(hT, non_blocking=True)
+            bufR[b].copy_(hR, non_blocking=True)
+            ev_in[b].record(copy)
+
         torch.cuda.synchronize()
         e4, e5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e4.record(stream)
-        for _ in range(args.steps):
-            dT.copy_(hT, non_blocking=True)
-            dR.copy_(hR, non_blocking=True)
-            solve_from_images(R, args.init, args.precond)
-            hv.copy_(v, non_blocking=True)
+        with torch.cuda.stream(copy):
+            copy.wait_event(e4)
+            upload(0)
+        for k in range(args.steps):
+            b = k % 2
+            if k + 1 < args.steps:
+                # buffer 1-b was last read by solve k-1, whose download the
+                # copy stream already waits for
+                with torch.cuda.stream(copy):
+                    upload(1 - b)
+            stream.wait_event(ev_in[b])
+            if k >= 2:
+                stream.wait_event(ev_out[b])   # velocity k-2 left buffer b
+            solve_from_images(R, args.init, args.precond, bufT[b], bufR[b], bufv[b])
+            ev_done[b].record(stream)
+            with torch.cuda.stream(copy):
+                copy.wait_event(ev_done[b])
+                hv.copy_(bufv[b], non_blocking=True)
+                ev_out[b].record(copy)
+        stream.wait_event(ev_out[(args.steps - 1) % 2])
         e5.record(stream)
         torch.cuda.synchronize()
         e2e_s = e4.elapsed_time(e5) / 1e3 / args.steps
