@@ -240,7 +240,7 @@ def cpu_oracle_sample(precision_note, counts):
     GPU solve (coarse-grid matvecs of the two-level preconditioner by their
     share of the points and time steps).  All cores: the same sample in one process per
     core at once, the solve time divided by the processes (the throughput of
-    the box running independent oracle solves)."""
+    the host running independent oracle solves)."""
     import multiprocessing as mp
     shape = (64, 64, 64)
     tg, tm, to = _oracle_ops(shape)
@@ -496,8 +496,8 @@ def gpu_bench(args):
         matvec_ms = e6.elapsed_time(e7) / 20
 
         # the other forms of the method, the faster of two timed solves each after a warm-up,
-        # to the same stopping test (the plain FP32 solver is the target's
-        # comparison)
+        # to the same stopping test (the plain FP32 solver from v = 0 is the
+        # comparison for the time to solution)
         arms = {}
         ctxs = {args.precision: R}
         for name, init, prec, pcd in (('plain_fp32', 'zero', 'fp32', 'spectral'),

@@ -91,10 +91,10 @@ def sinusoid_case(shape, scale, kind, incompressible, beta, nt, vscale, dir_seed
 
 
 JOBS = {
-    # configs[1]: 128^3, nt = 4, v* x 1.0; compressible H2 beta = 1e-2
+    # the 128^3 sinusoid problem, nt = 4, v* x 1.0; compressible H2 beta = 1e-2
     'c128_h2_a': (sinusoid_case, ((128, 128, 128), 1.0, 'H2', False, 1e-2, 4, 0.5, (1001,))),
     'c128_h2_b': (sinusoid_case, ((128, 128, 128), 1.0, 'H2', False, 1e-2, 4, 0.5, (1002, 1003))),
-    # configs[1], incompressible: Leray projection, H1-div, beta = 1e-3
+    # the same problem, incompressible: Leray projection, H1-div, beta = 1e-3
     'c128_div_a': (sinusoid_case, ((128, 128, 128), 1.0, 'H1DIV', True, 1e-3, 4, 0.5, (1001,))),
     'c128_div_b': (sinusoid_case, ((128, 128, 128), 1.0, 'H1DIV', True, 1e-3, 4, 0.5,
                                    (1002, 1003))),

@@ -299,7 +299,7 @@ def test_full_newton_matvec(reg, shape, kind, incompressible, beta, nt):
 
 
 def test_full_newton_solve_matches_the_oracle(reg):
-    """A Newton solve with the full Hessian (configs[0]'s problem): same
+    """A Newton solve with the full Hessian (the 32^3 sinusoid problem): same
     number of Newton steps (+-1), objective and velocity as the oracle's."""
     shape, nt, beta = (32, 32, 32), 4, 1e-2
     rho_T, rho_R, _ = [f32(a) for a in synth.sinusoid_problem(shape, 0.5)]
