@@ -348,11 +348,13 @@ __device__ __forceinline__ void tile_store(const float2* buf, float* __restrict_
 }
 
 // Complex lines per block of the four-step kernel (2 LC real lines: rows
-// along x3, or neighbouring x3 columns along x1 / x2).
+// along x3, or neighbouring x3 columns along x1 / x2).  With MINB = 3 blocks
+// an SM (48 / LC) the 256-point kernel keeps 80 registers; 8 or 32 lines,
+// and 2 or 4 blocks an SM, measured slower on the column axes at 256^3.
 constexpr int kDerivLines = 16;
 
-template <int N1, int N2, int AXIS, int LC>
-__global__ void __launch_bounds__(LC * N2, 48 / LC)
+template <int N1, int N2, int AXIS, int LC, int MINB = 48 / LC>
+__global__ void __launch_bounds__(LC * N2, MINB)
 k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumulate) {
     constexpr int N = N1 * N2;
     constexpr int S = N + 1;                       // load buffer line stride
