@@ -322,7 +322,8 @@ int reg_state_transport_noalloc(int n1, int n2, int n3, int nt, const float* rho
                                 const float* d_fwd, float* rho1, void* stream);
 
 /* Spectral first derivatives (Sec. III-B1): grad [3n] = grad f (f [n]);
- * div [n] = div v (v [3n]).  Odd derivatives zero the Nyquist mode. */
+ * div [n] = div v (v [3n]).  Odd derivatives zero the Nyquist mode.  Input
+ * and output must not overlap (REG_EINVAL). */
 int reg_spectral_grad(reg_ctx* ctx, const float* f, float* grad);
 int reg_spectral_div(reg_ctx* ctx, const float* v, float* div);
 

@@ -401,6 +401,10 @@ cudaError_t launch_sp_twolevel(const Dims& gf, const Dims& gc, const float2* r, 
 bool deriv_supported(const Dims& g, const void* f = nullptr, const void* out = nullptr);
 cudaError_t launch_deriv(const Dims& g, int axis, const float* f, float* out, int accumulate,
                          cudaStream_t st);
+// out3[a] = d_a f for a = 0, 1, 2 in one launch (components n apart), on cubic
+// grids of 32..256 points a side (deriv_supported's conditions besides);
+// cudaErrorNotSupported elsewhere, with nothing launched.
+cudaError_t launch_grad(const Dims& g, const float* f, float* out3, cudaStream_t st);
 
 // blas.cu
 int blas_blocks();   // number of partial-sum blocks used by reductions

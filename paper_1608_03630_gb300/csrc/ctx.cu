@@ -3,6 +3,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
 #include <new>
 
@@ -159,8 +160,15 @@ static SpecArgs spec_args(reg_ctx* c) {
 
 int op_grad(reg_ctx* c, const float* f, float* out3) {
     if (deriv_supported(c->g, f, out3)) {
-        // one-dimensional transforms per axis: one read and one write each
+        // one-dimensional transforms per axis: one read and one write each,
+        // the three axes in one launch where the grid is cubic
         const long long n = c->g.n;
+        const Dims& g = c->g;
+        if (g.n1 == g.n2 && g.n1 == g.n3 && g.n1 >= 32 && g.n1 <= 256) {
+            Phase p(c, REG_PH_DERIV, 24.0 * n);
+            REG_CK(c, launch_grad(g, f, out3, c->stream));
+            return REG_OK;
+        }
         for (int ax = 0; ax < 3; ++ax) {
             Phase p(c, REG_PH_DERIV, 8.0 * n);
             REG_CK(c, launch_deriv(c->g, ax, f, out3 + ax * n, 0, c->stream));
@@ -1023,10 +1031,18 @@ int reg_state_transport(reg_ctx* c, const float* rho0, const float* d_fwd, float
     return REG_OK;
 }
 
+// [a, a + na) and [b, b + nb) share an element.
+static bool ranges_overlap(const float* a, long long na, const float* b, long long nb) {
+    const uintptr_t a0 = reinterpret_cast<uintptr_t>(a), b0 = reinterpret_cast<uintptr_t>(b);
+    return a0 < b0 + sizeof(float) * nb && b0 < a0 + sizeof(float) * na;
+}
+
 int reg_spectral_grad(reg_ctx* c, const float* f, float* grad) {
     CHECK_CTX(c);
     CHECK_PTR(c, f);
     CHECK_PTR(c, grad);
+    if (ranges_overlap(f, c->g.n, grad, 3LL * c->g.n))
+        return fail(c, REG_EINVAL, "f and grad overlap");
     return op_grad(c, f, grad);
 }
 
@@ -1034,6 +1050,8 @@ int reg_spectral_div(reg_ctx* c, const float* v, float* div) {
     CHECK_CTX(c);
     CHECK_PTR(c, v);
     CHECK_PTR(c, div);
+    if (ranges_overlap(v, 3LL * c->g.n, div, c->g.n))
+        return fail(c, REG_EINVAL, "v and div overlap");
     return op_div(c, v, div);
 }
 

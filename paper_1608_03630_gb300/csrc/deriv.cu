@@ -13,7 +13,9 @@
 // and one write of the field per derivative.
 //
 // Lines of 32..256 points use a register-blocked four-step transform
-// (below); lines of 16 and 512 points a Stockham FFT in shared memory.
+// (below); lines of 16 and 512 points a Stockham FFT in shared memory.  On
+// cubic grids of 32..256 points a side the three derivatives of a gradient
+// run as one launch (k_grad_r), the blocks of the three axes side by side.
 // Stockham: natural order in and out, radix 4 with one radix-2 stage when
 // log2 N is odd, each stage in place in one shared buffer (every thread
 // reads its butterflies' inputs into registers, the block synchronises, then
@@ -353,14 +355,16 @@ __device__ __forceinline__ void tile_store(const float2* buf, float* __restrict_
 // and 2 or 4 blocks an SM, measured slower on the column axes at 256^3.
 constexpr int kDerivLines = 16;
 
-template <int N1, int N2, int AXIS, int LC, int MINB = 48 / LC>
-__global__ void __launch_bounds__(LC * N2, MINB)
-k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumulate) {
+// The lines of block `blk` of one axis (the block's whole work; sm: its
+// dynamic shared memory).
+template <int N1, int N2, int AXIS, int LC>
+__device__ __forceinline__ void deriv_lines(const Dims& g, const float* __restrict__ f,
+                                            float* __restrict__ out, int accumulate, int blk,
+                                            float2* sm) {
     constexpr int N = N1 * N2;
     constexpr int S = N + 1;                       // load buffer line stride
     constexpr int TH = LC * N2;                    // threads
     constexpr int RL = 2 * LC;                     // real lines per block
-    extern __shared__ float2 sm[];
     float2* buf = sm;                              // max(LC S, LC N1 (N2 + 1)) complex
     float2* tw = sm + (LC * S > LC * N1 * (N2 + 1) ? LC * S : LC * N1 * (N2 + 1));
     for (int m = threadIdx.x; m < N; m += TH) {
@@ -370,11 +374,11 @@ k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accu
     }
     long long base, astride;
     if (AXIS == 2) {
-        base = (long long)blockIdx.x * RL * N;
+        base = (long long)blk * RL * N;
         astride = 1;
     } else {
         const int groups = g.n3 / RL;
-        const int fixed = blockIdx.x / groups, col0 = (blockIdx.x - fixed * groups) * RL;
+        const int fixed = blk / groups, col0 = (blk - fixed * groups) * RL;
         if (AXIS == 1) { base = (long long)fixed * g.n23 + col0; astride = g.n3; }
         else { base = (long long)fixed * g.n3 + col0; astride = g.n23; }
     }
@@ -427,6 +431,28 @@ k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accu
     }
 }
 
+template <int N1, int N2, int AXIS, int LC, int MINB = 48 / LC>
+__global__ void __launch_bounds__(LC * N2, MINB)
+k_deriv_r(Dims g, const float* __restrict__ f, float* __restrict__ out, int accumulate) {
+    extern __shared__ float2 sm[];
+    deriv_lines<N1, N2, AXIS, LC>(g, f, out, accumulate, blockIdx.x, sm);
+}
+
+// The three derivatives of a gradient in one launch (cubic grids: every axis
+// has N^2 / (2 LC) blocks, the same count): blocks [0, per) take x1,
+// [per, 2 per) x2, [2 per, 3 per) x3, so the launch has one tail instead of
+// three and the field's second and third reads can come from L2.
+template <int N1, int N2, int LC, int MINB = 48 / LC>
+__global__ void __launch_bounds__(LC * N2, MINB)
+k_grad_r(Dims g, const float* __restrict__ f, float* __restrict__ out3, int per) {
+    extern __shared__ float2 sm[];
+    const int ax = blockIdx.x / per, blk = blockIdx.x - ax * per;
+    float* out = out3 + (long long)ax * g.n;
+    if (ax == 0) deriv_lines<N1, N2, 0, LC>(g, f, out, 0, blk, sm);
+    else if (ax == 1) deriv_lines<N1, N2, 1, LC>(g, f, out, 0, blk, sm);
+    else deriv_lines<N1, N2, 2, LC>(g, f, out, 0, blk, sm);
+}
+
 template <int N1, int N2, int AXIS>
 cudaError_t run_deriv_r(const Dims& g, const float* f, float* out, int accumulate,
                         cudaStream_t st) {
@@ -447,6 +473,26 @@ cudaError_t run_deriv_r(const Dims& g, const float* f, float* out, int accumulat
     if (AXIS == 2) blocks = g.n1 * g.n2 / (2 * LC);
     else blocks = (AXIS == 1 ? g.n1 : g.n2) * (g.n3 / (2 * LC));
     k_deriv_r<N1, N2, AXIS, LC><<<blocks, LC * N2, smem, st>>>(g, f, out, accumulate);
+    return cudaGetLastError();
+}
+
+template <int N1, int N2>
+cudaError_t run_grad_r(const Dims& g, const float* f, float* out3, cudaStream_t st) {
+    constexpr int LC = kDerivLines;
+    constexpr int N = N1 * N2;
+    const int bufc = LC * (N + 1) > LC * N1 * (N2 + 1) ? LC * (N + 1) : LC * N1 * (N2 + 1);
+    const size_t smem = sizeof(float2) * (bufc + N);
+    if (smem > 48 * 1024) {
+        static std::once_flag once;
+        static cudaError_t attr = cudaSuccess;
+        std::call_once(once, [&] {
+            attr = cudaFuncSetAttribute(k_grad_r<N1, N2, LC>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        });
+        if (attr != cudaSuccess) return attr;
+    }
+    const int per = N * N / (2 * LC);              // blocks per axis (n1 = n2 = n3 = N)
+    k_grad_r<N1, N2, LC><<<3 * per, LC * N2, smem, st>>>(g, f, out3, per);
     return cudaGetLastError();
 }
 
@@ -491,6 +537,18 @@ bool deriv_supported(const Dims& g, const void* f, const void* out) {
     const uintptr_t mis = (reinterpret_cast<uintptr_t>(f) | reinterpret_cast<uintptr_t>(out)) & 15;
     return mis == 0 && pow2_in(g.n1, 16, 512) && pow2_in(g.n2, 16, 512) &&
            pow2_in(g.n3, 32, 512);
+}
+
+cudaError_t launch_grad(const Dims& g, const float* f, float* out3, cudaStream_t st) {
+    if (!deriv_supported(g, f, out3) || g.n1 != g.n2 || g.n1 != g.n3)
+        return cudaErrorNotSupported;
+    switch (g.n1) {
+    case 32: return run_grad_r<8, 4>(g, f, out3, st);
+    case 64: return run_grad_r<8, 8>(g, f, out3, st);
+    case 128: return run_grad_r<16, 8>(g, f, out3, st);
+    case 256: return run_grad_r<16, 16>(g, f, out3, st);
+    default: return cudaErrorNotSupported;
+    }
 }
 
 cudaError_t launch_deriv(const Dims& g, int axis, const float* f, float* out, int accumulate,

@@ -194,6 +194,28 @@ def test_spectral_operators(reg, shape):
             R.close()
 
 
+@pytest.mark.parametrize('n', [32, 64, 128, 256])
+def test_gradient_of_cubic_grids_in_one_launch(reg, n):
+    """Cubic grids of 32..256 points a side take the three derivatives of a
+    gradient in one launch (blocks of the three axes side by side): each
+    component against the oracle, bandlimited and white-noise fields."""
+    shape = (n, n, n)
+    R = reg.Registration(shape, 4, 1e-2)
+    for f in (synth.bandlimited(shape, 6, 33, ncomp=None),
+              np.random.default_rng(34).standard_normal(shape)):
+        g = host(R.spectral_grad(dev(f32(f))))
+        ref = osp.gradient(f32(f))
+        for a in range(3):
+            assert rel(g[a], ref[a]) < 1e-5, (n, a, rel(g[a], ref[a]))
+    # one launch reads f while other blocks write grad: overlap is refused
+    g3 = torch.zeros((3,) + shape, device='cuda')
+    for comp in range(3):
+        with pytest.raises(reg.RegError) as e:
+            R._call('reg_spectral_grad', reg._ptr(g3[comp], shape), reg._ptr(g3))
+        assert e.value.status == 1, comp    # REG_EINVAL
+    R.close()
+
+
 def test_inner_product(reg):
     shape = (20, 28, 44)
     a = synth.bandlimited(shape, 4, 41)
