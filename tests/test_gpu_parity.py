@@ -580,6 +580,32 @@ def test_graph_and_eager_pcg_agree(reg):
         assert rel(o[0], out[0][0]) < 1e-6
 
 
+def test_solve_through_host_buffers_equals_the_device_solve(reg):
+    """reg_solve_host (images and velocity in host memory, pageable or
+    pinned; uploads, solve, download) gives the device solve's status, counts
+    and iterate, from v = 0 and from a non-zero guess."""
+    shape = (24, 24, 24)
+    rho_T, rho_R, vs = synth.sinusoid_problem(shape, 0.5)
+    cpu = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float32)
+    for v0 in (np.zeros((3,) + shape), 0.5 * np.asarray(vs)):
+        R = reg.Registration(shape, 4, 1e-3)
+        R.set_images(dev(rho_T), dev(rho_R), presmooth=True)
+        v = dev(v0)
+        s_dev, st_dev = R.solve(v, gtol=1e-2, max_gn=4)
+        R.close()
+        for pinned in (False, True):
+            hT, hR, hv = cpu(rho_T), cpu(rho_R), cpu(v0)
+            if pinned:
+                hT, hR, hv = hT.pin_memory(), hR.pin_memory(), hv.pin_memory()
+            R = reg.Registration(shape, 4, 1e-3)
+            s, st = R.solve_host(hT, hR, hv, presmooth=True, gtol=1e-2, max_gn=4)
+            R.close()
+            assert s == s_dev, (pinned, s, s_dev)
+            assert st['gn_iters'] == st_dev['gn_iters'], pinned
+            assert st['pcg_iters'] == st_dev['pcg_iters'], pinned
+            assert rel(hv.double().numpy(), host(v)) < 1e-6, pinned
+
+
 def test_device_pcg_loop_respects_the_iteration_cap(reg):
     shape = (24, 24, 24)
     rho_T, rho_R, _ = synth.sinusoid_problem(shape, 0.5)
